@@ -1,0 +1,200 @@
+/*
+ * ozk2.h - C ABI of an FP64 matrix-multiplication emulation on FP8 tensor cores
+ * (Ozaki-II scheme with FP8 E4M3 digits; Uchino, Ozaki, Imamura, arXiv:2603.10634),
+ * built for NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are row-major.  A is m x k with leading dimension lda >= max(1, k);
+ *     B is k x n with ldb >= max(1, n); C is m x n with ldc >= max(1, n).
+ *     Leading dimensions are counted in elements.
+ *   - Pointers named A, B, C, D and every array argument are DEVICE pointers on the
+ *     current CUDA device, owned by the caller.  Work is enqueued on `stream`
+ *     (a cudaStream_t; NULL is the legacy default stream) and the call returns
+ *     after enqueueing: results are valid once the stream has reached that point.
+ *   - num_moduli is the paper's N, 1 <= N <= 20, taking the first N moduli of the
+ *     hybrid list (Sec. III-D).  N = 12 reaches P/2 > 2^110 (Sec. III-D) and is the
+ *     usual FP64-level choice; each further modulus adds about 4.5 bits.
+ *   - Argument errors are detected on the host, return OZK2_ERR_INVALID_VALUE and
+ *     touch no memory.  Errors of enqueued work (a CUDA launch failure) return
+ *     OZK2_ERR_CUDA.  Conditions found by the kernels themselves (non-finite input,
+ *     a bounded device wait that gave up) are recorded in a device flag word and
+ *     reported by ozk2_device_status().
+ *   - Not thread-safe: serialise calls that use the library-owned workspace.
+ */
+#ifndef OZK2_H
+#define OZK2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ozk2_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+  OZK2_OK = 0,
+  OZK2_ERR_INVALID_VALUE = 1, /* bad size, leading dimension, pointer or N      */
+  OZK2_ERR_UNSUPPORTED = 2,   /* no sm_103a-class device, or a shape outside the
+                                 supported range                               */
+  OZK2_ERR_ALLOC = 3,         /* workspace allocation failed                     */
+  OZK2_ERR_CUDA = 4,          /* a CUDA runtime / driver call failed             */
+  OZK2_ERR_INTERNAL = 5,      /* inconsistent internal state                     */
+  OZK2_ERR_TIMEOUT = 6,       /* a device-side wait exceeded its bound (kernel
+                                 returned early; results are invalid)            */
+  OZK2_ERR_NONFINITE = 7,     /* informational: NaN/Inf inputs were seen; the
+                                 affected rows/columns of C are NaN              */
+  OZK2_ERR_RANGE = 8          /* a scaled input exceeded the supported exponent
+                                 range (results are invalid)                     */
+} ozk2_status;
+
+/*
+ * ozk2_dgemm - C := A * B in emulated FP64.
+ *
+ * The operation of Sec. II (C ~ AB via A' = trunc(diag(mu) A), B' = trunc(B diag(nu)),
+ * residues modulo p_1..p_N, CRT, inverse scaling) with the FP8 construction of
+ * Sec. III: hybrid moduli (Sec. III-D), square moduli by Eq. 3matmult-notKaratsuba,
+ * the rest by the Karatsuba split (Sec. III-B), accurate-mode scaling by an FP8
+ * bound product (Sec. III-E).  3N + 1 FP8 products run on the tensor cores.
+ *
+ * m, n, k >= 0.  If m == 0 or n == 0 nothing is written; if k == 0, C is set to 0.
+ * k is unrestricted: reductions longer than 2^16 are split into exact blocks.
+ * C must not overlap A or B.  Uses a workspace owned by the library (one per
+ * device, grown on demand with cudaMalloc, which synchronises the device when it
+ * grows; see ozk2_workspace_size for its size).  Each output entry is the
+ * correctly rounded value of the CRT result times 2^-(e_i + f_j).  Rows of A or
+ * columns of B holding NaN/Inf give NaN rows/columns of C.
+ */
+ozk2_status ozk2_dgemm(int64_t m, int64_t n, int64_t k,
+                       const double *A, int64_t lda,
+                       const double *B, int64_t ldb,
+                       double *C, int64_t ldc,
+                       int num_moduli, ozk2_stream_t stream);
+
+/*
+ * ozk2_workspace_size - bytes of device workspace one call with these sizes needs:
+ * the FP8 bound operands, M_N digit planes per operand (Sec. IV-B Eq. M), N int16
+ * residue-product matrices and the scale vectors.  Returns 0 on invalid arguments.
+ */
+size_t ozk2_workspace_size(int64_t m, int64_t n, int64_t k, int num_moduli);
+
+/*
+ * ozk2_dgemm_ws - ozk2_dgemm with a caller-owned workspace (device memory, at least
+ * ozk2_workspace_size bytes, 256-byte aligned).  The workspace is in use until the
+ * stream passes this call.  OZK2_ERR_INVALID_VALUE if it is too small or misaligned.
+ */
+ozk2_status ozk2_dgemm_ws(int64_t m, int64_t n, int64_t k,
+                          const double *A, int64_t lda,
+                          const double *B, int64_t ldb,
+                          double *C, int64_t ldc,
+                          int num_moduli, void *workspace, size_t workspace_bytes,
+                          ozk2_stream_t stream);
+
+/* ozk2_status_string - a static, human-readable name for a status code. */
+const char *ozk2_status_string(ozk2_status status);
+
+/*
+ * ozk2_device_status - synchronises `stream`, then reads and clears the device flag
+ * word of the given workspace (NULL: the library-owned workspace of the current
+ * device).  Returns OZK2_OK, OZK2_ERR_TIMEOUT, OZK2_ERR_RANGE or OZK2_ERR_NONFINITE
+ * (most severe first), or OZK2_ERR_CUDA if the synchronisation fails.
+ */
+ozk2_status ozk2_device_status(void *workspace, ozk2_stream_t stream);
+
+/*
+ * ozk2_moduli - writes the first N moduli of the hybrid list (Sec. III-D) to
+ * p_out (host memory, N entries).  Returns N, or -1 if N is outside 1..20.
+ */
+int ozk2_moduli(int num_moduli, int32_t *p_out);
+
+/*
+ * ozk2_set_timing / ozk2_get_timing - per-phase timing of the next ozk2_dgemm calls
+ * with CUDA events recorded on the call's stream (enable = 1 turns it on).
+ * ozk2_get_timing waits for the last timed call and writes up to `max` phase times
+ * in milliseconds, in the order: 0 scaling pass, 1 bound product, 2 exponents,
+ * 3 residues and digits, 4 residue products, 5 CRT and inverse scaling
+ * (the quant / gemms / requant / dequant split of Sec. V-C with requant fused into
+ * phase 4).  Returns the number of phases written, or -1 if nothing was timed.
+ */
+void ozk2_set_timing(int enable);
+int ozk2_get_timing(float *ms, int max);
+
+/* ozk2_last_launch_count - kernels launched by the last ozk2_dgemm / ozk2_dgemm_ws
+ * call on this thread (host-side count). */
+int ozk2_last_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * Parity hooks.  Each runs one step (or a prefix) of the method on its own so the
+ * CPU oracle can check it.  Same conventions as above; all arrays are device
+ * memory, and kp denotes the padded FP8 row length, kp = 32 * ceil(k / 32).
+ * ------------------------------------------------------------------------- */
+
+/*
+ * ozk2_debug_fp8_gemm - D = A8 * B8^T with FP8 E4M3 operands and FP32 accumulation
+ * on the tcgen05 tensor cores (the product used throughout Sec. III).  A8 is m x k
+ * bytes with row stride lda8, B8 is n x k bytes with row stride ldb8 (both K-major);
+ * lda8 and ldb8 must be multiples of 16 and the pointers 16-byte aligned.  D is
+ * m x n float, row stride ldd.  Any k >= 1 is accepted; bytes past column k of a
+ * row are never read.  The products are exact for integer-valued operands with
+ * k * max|a| * max|b| <= 2^24 (Sec. III-B, Eq. error-free-FP8-matmult).
+ */
+ozk2_status ozk2_debug_fp8_gemm(int64_t m, int64_t n, int64_t k,
+                                const uint8_t *A8, int64_t lda8,
+                                const uint8_t *B8, int64_t ldb8,
+                                float *D, int64_t ldd, ozk2_stream_t stream);
+
+/*
+ * ozk2_debug_scales - the accurate-mode scaling of Sec. III-E (workflow steps 1-3
+ * of Sec. IV-B): e'_i, f'_j (Eq. def:mu'nu'), the E4M3 bound operands
+ * Abar (m x kp) and Bbar^T (n x kp), the row / column maxima R_i, S_j of
+ * Cbar = RU((1 + k 2^-24) Abar Bbar) (Eq. barCupper), and the exponents e_i, f_j of
+ * Eqs. mu-computation / nu-computation.  Any output pointer may be NULL.
+ */
+ozk2_status ozk2_debug_scales(int64_t m, int64_t n, int64_t k,
+                              const double *A, int64_t lda,
+                              const double *B, int64_t ldb, int num_moduli,
+                              int32_t *e, int32_t *f, int32_t *eprime, int32_t *fprime,
+                              float *R, float *S, uint8_t *Abar, uint8_t *BbarT,
+                              ozk2_stream_t stream);
+
+/*
+ * ozk2_debug_residue_planes - FP8 digit planes of A' = trunc(diag(2^e) A) and
+ * B' = trunc(B diag(2^f)) for the given exponents (Eqs. def:A', def:B'; digit splits
+ * of Sec. III-B and III-D).  planesA: M_N x m x kp bytes, planesB: M_N x n x kp bytes
+ * (B transposed, K-major).  Square modulus l < 6 owns planes 2l, 2l+1 (d1, d2);
+ * Karatsuba modulus l >= 6 owns planes 12 + 3(l-6) + {0,1,2} (d1, d2, d3).
+ */
+ozk2_status ozk2_debug_residue_planes(int64_t m, int64_t n, int64_t k,
+                                      const double *A, int64_t lda,
+                                      const double *B, int64_t ldb, int num_moduli,
+                                      const int32_t *e, const int32_t *f,
+                                      uint8_t *planesA, uint8_t *planesB,
+                                      ozk2_stream_t stream);
+
+/*
+ * ozk2_debug_residue_products - C'_l = mod(A'_l B'_l, p_l), l = 1..N (Eq. CRTmatmul),
+ * from the three FP8 digit products per modulus (Eqs. 3matmult-notKaratsuba and
+ * C'-Karatsuba) for the given exponents.  Cres: N x m x n int16, contiguous,
+ * symmetric residues in [-floor(p/2), p - 1 - floor(p/2)].
+ */
+ozk2_status ozk2_debug_residue_products(int64_t m, int64_t n, int64_t k,
+                                        const double *A, int64_t lda,
+                                        const double *B, int64_t ldb, int num_moduli,
+                                        const int32_t *e, const int32_t *f,
+                                        int16_t *Cres, ozk2_stream_t stream);
+
+/*
+ * ozk2_debug_crt - C = diag(2^-e) mod(sum_l q_l P/p_l C'_l, P) diag(2^-f)
+ * (Eqs. CRT_finalreduction, inversescaling) from given residue products
+ * Cres (N x m x n int16, contiguous) and exponents; each entry correctly rounded.
+ */
+ozk2_status ozk2_debug_crt(int64_t m, int64_t n, int num_moduli,
+                           const int16_t *Cres, const int32_t *e, const int32_t *f,
+                           double *C, int64_t ldc, ozk2_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OZK2_H */

@@ -652,3 +652,15 @@ def exact_dot(a, b):
 def exact_abs_dot(a, b):
     """Exact sum_h |a_h| |b_h| as a Fraction ((|A||B|)_ij for the error bound)."""
     return exact_dot(np.abs(a), np.abs(b))
+
+
+def emulated_entry(a_row, b_col, e_i, f_j, moduli):
+    """One output entry of the method for given exponents, through the plain
+    definition: C'_ij = (A'B')_ij exactly (what the CRT returns when Eq. condition
+    holds), then RN(C'_ij 2^-(e_i+f_j)).  Returns (value, condition_holds)."""
+    P = product_P(moduli)
+    ai = [trunc_scaled(x, int(e_i)) for x in a_row]
+    bj = [trunc_scaled(x, int(f_j)) for x in b_col]
+    c = sum(x * y for x, y in zip(ai, bj))
+    lhs = 2 * sum(abs(x) * abs(y) for x, y in zip(ai, bj))
+    return round_scaled_to_double(c, int(e_i) + int(f_j)), lhs < P

@@ -1,0 +1,21 @@
+"""FP64 matrix multiplication emulated on GB300 FP8 tensor cores (Ozaki-II scheme with
+FP8 E4M3 digits, arXiv:2603.10634).
+
+The compute path is libozk2.so (hand-written sm_103a CUDA behind the C ABI of
+include/ozk2.h); this package is its thin binding.
+"""
+from .ozk2 import (  # noqa: F401
+    PHASES,
+    crt,
+    device_status,
+    dgemm,
+    fp8_gemm,
+    get_timing,
+    last_launch_count,
+    moduli,
+    residue_planes,
+    residue_products,
+    scales,
+    set_timing,
+    workspace_size,
+)

@@ -1,0 +1,552 @@
+// C ABI of libozk2 (declared in include/ozk2.h): argument validation, the workspace,
+// TMA descriptors, constant tables, and the order of the kernels of one emulated DGEMM:
+//
+//   scale rows of A | column maxima of B | scale columns of B   (Sec. III-E, Eq. def:mu'nu')
+//   bound product Abar Bbar -> row / column maxima               (Eq. barCupper)
+//   exponents e, f                                                (Eq. mu-computation)
+//   residues and FP8 digits of A' and B'                          (Sec. III-B..III-D)
+//   3N digit products + mod-reduce -> C'_l                        (Eqs. 3matmult, C'-Karatsuba)
+//   CRT + inverse scaling -> C                                    (Eqs. CRT_finalreduction,
+//                                                                  inversescaling)
+// All kernels are launched on the caller's stream; nothing here runs on the CPU
+// except bookkeeping.
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "internal.h"
+#include "ozk2.h"
+
+namespace ozk2 {
+namespace {
+
+constexpr int64_t kMaxDim = int64_t(1) << 20;
+
+// ------------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// ------------------------------------------------------------------ device checks
+struct DeviceInfo {
+  bool probed = false;
+  bool supported = false;
+  int num_sms = 0;
+};
+std::mutex g_dev_mutex;
+DeviceInfo g_dev[64];
+
+bool device_info(int* num_sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+  std::lock_guard<std::mutex> lk(g_dev_mutex);
+  DeviceInfo& d = g_dev[dev];
+  if (!d.probed) {
+    int major = 0, minor = 0, sms = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    d.supported = (major == 10 && minor == 3);  // the kernels are built for sm_103a only
+    d.num_sms = sms;
+    d.probed = true;
+  }
+  *num_sms = d.num_sms;
+  return d.supported;
+}
+
+// ------------------------------------------------------------------ constant tables
+struct Tables {
+  bool built = false;
+  ModTable mt;
+  CrtTable ct;
+  float pprime;
+};
+std::mutex g_tab_mutex;
+Tables g_tables[kMaxModuli + 1];
+
+const Tables* tables_for(int N) {
+  std::lock_guard<std::mutex> lk(g_tab_mutex);
+  Tables& t = g_tables[N];
+  if (!t.built) {
+    if (!build_mod_table(N, &t.mt) || !build_crt_table(N, &t.ct)) return nullptr;
+    t.pprime = p_prime_f32(N);
+    t.built = true;
+  }
+  return &t;
+}
+
+// ------------------------------------------------------------------ workspace layout
+struct Layout {
+  int64_t kp, ldr;
+  int planes;
+  size_t flags, R, S, colmax, colbad, zero_end;
+  size_t eprime, fprime, e, f, rowstat, colstat;
+  size_t Abar, BbarT, planesA, planesB, cres, total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(int64_t m, int64_t n, int64_t k, int N) {
+  Layout L;
+  L.kp = ((k + 31) / 32) * 32;
+  L.ldr = ((n + 7) / 8) * 8;
+  L.planes = (N <= kNumSquares) ? 2 * N : 3 * N - kNumSquares;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.flags = take(256);
+  L.R = take(4 * size_t(m));
+  L.S = take(4 * size_t(n));
+  L.colmax = take(8 * size_t(n));
+  L.colbad = take(4 * size_t(n));
+  L.zero_end = o;
+  L.eprime = take(4 * size_t(m));
+  L.fprime = take(4 * size_t(n));
+  L.e = take(4 * size_t(m));
+  L.f = take(4 * size_t(n));
+  L.rowstat = take(size_t(m));
+  L.colstat = take(size_t(n));
+  L.Abar = take(size_t(m) * L.kp);
+  L.BbarT = take(size_t(n) * L.kp);
+  L.planesA = take(size_t(L.planes) * m * L.kp);
+  L.planesB = take(size_t(L.planes) * n * L.kp);
+  L.cres = take(2 * size_t(N) * m * L.ldr);
+  L.total = o;
+  return L;
+}
+
+struct Ctx {
+  int m, n, k, N;
+  Layout L;
+  uint8_t* ws;
+  const Tables* tab;
+  int num_sms;
+  cudaStream_t st;
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(ws + off);
+  }
+};
+
+// ------------------------------------------------------------------ library-owned workspace
+struct OwnedWs {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+};
+std::mutex g_ws_mutex;
+OwnedWs g_ws[64];
+
+uint8_t* owned_workspace(size_t need, ozk2_status* err) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_ws_mutex);
+  OwnedWs& w = g_ws[dev];
+  if (w.bytes < need) {
+    if (w.ptr) cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.bytes = 0;
+    void* p = nullptr;
+    if (cudaMalloc(&p, need) != cudaSuccess) {
+      cudaGetLastError();
+      *err = OZK2_ERR_ALLOC;
+      return nullptr;
+    }
+    cudaMemset(p, 0, 256);
+    w.ptr = p;
+    w.bytes = need;
+  }
+  return static_cast<uint8_t*>(w.ptr);
+}
+
+// ------------------------------------------------------------------ timing
+struct Timing {
+  bool enabled = false;
+  bool have = false;
+  int dev = -1;
+  cudaEvent_t ev[7] = {};
+};
+Timing g_timing;
+std::mutex g_timing_mutex;
+thread_local int t_launches = 0;
+
+void mark(Ctx& c, int idx) {
+  if (!g_timing.enabled) return;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (g_timing.dev != dev) {
+    for (auto& e : g_timing.ev)
+      if (e) cudaEventDestroy(e);
+    for (auto& e : g_timing.ev) cudaEventCreate(&e);
+    g_timing.dev = dev;
+  }
+  cudaEventRecord(g_timing.ev[idx], c.st);
+  if (idx == 6) g_timing.have = true;
+}
+
+#define OZK2_TRY(expr)                      \
+  do {                                      \
+    cudaError_t _e = (expr);                \
+    if (_e != cudaSuccess) return OZK2_ERR_CUDA; \
+  } while (0)
+
+// ------------------------------------------------------------------ phases
+ozk2_status phase_scales(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb) {
+  const Layout& L = c.L;
+  OZK2_TRY(cudaMemsetAsync(c.ws, 0, L.zero_end, c.st));
+  OZK2_TRY(launch_scale_rows(A, lda, c.m, c.k, int(L.kp), c.at<int32_t>(L.eprime), c.at<uint8_t>(L.rowstat),
+                             c.at<uint8_t>(L.Abar), c.at<uint32_t>(L.flags), c.st));
+  OZK2_TRY(launch_colmax(B, ldb, c.k, c.n, c.at<unsigned long long>(L.colmax), c.at<uint32_t>(L.colbad), c.st));
+  OZK2_TRY(launch_scale_cols(B, ldb, c.k, c.n, int(L.kp), c.at<unsigned long long>(L.colmax),
+                             c.at<uint32_t>(L.colbad), c.at<int32_t>(L.fprime), c.at<uint8_t>(L.colstat),
+                             c.at<uint8_t>(L.BbarT), c.at<uint32_t>(L.flags), c.st));
+  t_launches += 3;
+  mark(c, 1);
+  GemmArgs g{};
+  g.mode = kModeBound;
+  g.m = c.m;
+  g.n = c.n;
+  g.k = c.k;
+  g.num_sms = c.num_sms;
+  g.factor = bound_factor_f32(c.k);
+  g.R = c.at<float>(L.R);
+  g.S = c.at<float>(L.S);
+  g.flags = c.at<uint32_t>(L.flags);
+  OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.Abar), L.kp, 1, c.at<uint8_t>(L.BbarT), L.kp, 1, c.st));
+  t_launches += 1;
+  mark(c, 2);
+  OZK2_TRY(launch_exponents(c.m, c.n, c.at<int32_t>(L.eprime), c.at<int32_t>(L.fprime), c.at<uint8_t>(L.rowstat),
+                            c.at<uint8_t>(L.colstat), c.at<float>(L.R), c.at<float>(L.S), c.tab->pprime,
+                            delta_f32(), c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.st));
+  t_launches += 1;
+  mark(c, 3);
+  return OZK2_OK;
+}
+
+ozk2_status phase_residues(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb,
+                           const int32_t* e, const int32_t* f, uint8_t* planesA, uint8_t* planesB) {
+  const Layout& L = c.L;
+  OZK2_TRY(launch_residues_rows(A, lda, c.m, c.k, int(L.kp), e, c.tab->mt, planesA, c.at<uint32_t>(L.flags), c.st));
+  OZK2_TRY(launch_residues_cols(B, ldb, c.k, c.n, int(L.kp), f, c.tab->mt, planesB, c.at<uint32_t>(L.flags), c.st));
+  t_launches += 2;
+  mark(c, 4);
+  return OZK2_OK;
+}
+
+ozk2_status phase_products(Ctx& c) {
+  const Layout& L = c.L;
+  GemmArgs g{};
+  g.mode = kModeResidue;
+  g.m = c.m;
+  g.n = c.n;
+  g.k = c.k;
+  g.num_sms = c.num_sms;
+  g.cres = c.at<int16_t>(L.cres);
+  g.ldr = L.ldr;
+  g.res_stride = int64_t(c.m) * L.ldr;
+  g.mt = &c.tab->mt;
+  g.flags = c.at<uint32_t>(L.flags);
+  OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA), L.kp, L.planes, c.at<uint8_t>(L.planesB), L.kp, L.planes,
+                           c.st));
+  t_launches += 1;
+  mark(c, 5);
+  return OZK2_OK;
+}
+
+ozk2_status phase_crt(Ctx& c, const int32_t* e, const int32_t* f, const uint8_t* rowstat,
+                      const uint8_t* colstat, double* C, int64_t ldc) {
+  const Layout& L = c.L;
+  OZK2_TRY(launch_crt(c.at<int16_t>(L.cres), L.ldr, int64_t(c.m) * L.ldr, c.m, c.n, e, f, rowstat, colstat, C, ldc,
+                      c.tab->ct, c.st));
+  t_launches += 1;
+  mark(c, 6);
+  return OZK2_OK;
+}
+
+ozk2_status check_sizes(int64_t m, int64_t n, int64_t k, int N) {
+  if (m < 0 || n < 0 || k < 0 || N < 1 || N > kMaxModuli) return OZK2_ERR_INVALID_VALUE;
+  if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return OZK2_ERR_UNSUPPORTED;
+  return OZK2_OK;
+}
+
+ozk2_status validate(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                     int64_t ldb, const double* C, int64_t ldc, int N) {
+  ozk2_status s = check_sizes(m, n, k, N);
+  if (s != OZK2_OK) return s;
+  if (lda < std::max<int64_t>(1, k) || ldb < std::max<int64_t>(1, n) || ldc < std::max<int64_t>(1, n))
+    return OZK2_ERR_INVALID_VALUE;
+  if (m == 0 || n == 0) return OZK2_OK;  // nothing is read or written
+  if (!C || (k > 0 && (!A || !B))) return OZK2_ERR_INVALID_VALUE;
+  return OZK2_OK;
+}
+
+ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, void* ws, size_t ws_bytes, cudaStream_t st) {
+  c.m = int(m);
+  c.n = int(n);
+  c.k = int(k);
+  c.N = N;
+  c.st = st;
+  if (!device_info(&c.num_sms)) return OZK2_ERR_UNSUPPORTED;
+  if (!encode_fn()) return OZK2_ERR_CUDA;
+  c.tab = tables_for(N);
+  if (!c.tab) return OZK2_ERR_INTERNAL;
+  c.L = make_layout(m, n, k, N);
+  if (ws) {
+    if (ws_bytes < c.L.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) return OZK2_ERR_INVALID_VALUE;
+    c.ws = static_cast<uint8_t*>(ws);
+  } else {
+    ozk2_status err = OZK2_OK;
+    c.ws = owned_workspace(c.L.total, &err);
+    if (!c.ws) return err;
+  }
+  return OZK2_OK;
+}
+
+ozk2_status dgemm_impl(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                       double* C, int64_t ldc, int N, void* ws, size_t ws_bytes, cudaStream_t st) {
+  t_launches = 0;
+  ozk2_status s = validate(m, n, k, A, lda, B, ldb, C, ldc, N);
+  if (s != OZK2_OK) return s;
+  if (m == 0 || n == 0) return OZK2_OK;
+  if (k == 0) {
+    OZK2_TRY(cudaMemset2DAsync(C, size_t(ldc) * 8, 0, size_t(n) * 8, size_t(m), st));
+    return OZK2_OK;
+  }
+  Ctx c;
+  s = setup(c, m, n, k, N, ws, ws_bytes, st);
+  if (s != OZK2_OK) return s;
+  mark(c, 0);
+  const Layout& L = c.L;
+  if ((s = phase_scales(c, A, lda, B, ldb)) != OZK2_OK) return s;
+  if ((s = phase_residues(c, A, lda, B, ldb, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesA),
+                          c.at<uint8_t>(L.planesB))) != OZK2_OK)
+    return s;
+  if ((s = phase_products(c)) != OZK2_OK) return s;
+  return phase_crt(c, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.rowstat), c.at<uint8_t>(L.colstat), C,
+                   ldc);
+}
+
+}  // namespace
+
+bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t planes,
+                    int64_t row_stride_bytes, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || cols < 1 || rows < 1 || planes < 1) return false;
+  const cuuint64_t dims[3] = {cuuint64_t(cols), cuuint64_t(rows), cuuint64_t(planes)};
+  const cuuint64_t strides[2] = {cuuint64_t(row_stride_bytes), cuuint64_t(row_stride_bytes) * cuuint64_t(rows)};
+  const cuuint32_t box[3] = {128u, cuuint32_t(box_rows), 1u};
+  const cuuint32_t estr[3] = {1u, 1u, 1u};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace ozk2
+
+using namespace ozk2;
+
+extern "C" {
+
+ozk2_status ozk2_dgemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                       double* C, int64_t ldc, int num_moduli, ozk2_stream_t stream) {
+  return dgemm_impl(m, n, k, A, lda, B, ldb, C, ldc, num_moduli, nullptr, 0, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ozk2_status ozk2_dgemm_ws(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                          double* C, int64_t ldc, int num_moduli, void* workspace, size_t workspace_bytes,
+                          ozk2_stream_t stream) {
+  if (!workspace) return OZK2_ERR_INVALID_VALUE;
+  return dgemm_impl(m, n, k, A, lda, B, ldb, C, ldc, num_moduli, workspace, workspace_bytes,
+                    reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t ozk2_workspace_size(int64_t m, int64_t n, int64_t k, int num_moduli) {
+  if (check_sizes(m, n, k, num_moduli) != OZK2_OK) return 0;
+  return make_layout(m, n, k, num_moduli).total;
+}
+
+const char* ozk2_status_string(ozk2_status s) {
+  switch (s) {
+    case OZK2_OK: return "OZK2_OK";
+    case OZK2_ERR_INVALID_VALUE: return "OZK2_ERR_INVALID_VALUE";
+    case OZK2_ERR_UNSUPPORTED: return "OZK2_ERR_UNSUPPORTED";
+    case OZK2_ERR_ALLOC: return "OZK2_ERR_ALLOC";
+    case OZK2_ERR_CUDA: return "OZK2_ERR_CUDA";
+    case OZK2_ERR_INTERNAL: return "OZK2_ERR_INTERNAL";
+    case OZK2_ERR_TIMEOUT: return "OZK2_ERR_TIMEOUT";
+    case OZK2_ERR_NONFINITE: return "OZK2_ERR_NONFINITE";
+    case OZK2_ERR_RANGE: return "OZK2_ERR_RANGE";
+  }
+  return "OZK2_UNKNOWN_STATUS";
+}
+
+ozk2_status ozk2_device_status(void* workspace, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return OZK2_ERR_CUDA;
+  void* ws = workspace;
+  if (!ws) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return OZK2_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_ws_mutex);
+    ws = g_ws[dev].ptr;
+  }
+  if (!ws) return OZK2_OK;
+  uint32_t flags = 0;
+  if (cudaMemcpy(&flags, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return OZK2_ERR_CUDA;
+  if (cudaMemset(ws, 0, 4) != cudaSuccess) return OZK2_ERR_CUDA;
+  if (flags & kFlagTimeout) return OZK2_ERR_TIMEOUT;
+  if (flags & kFlagRange) return OZK2_ERR_RANGE;
+  if (flags & kFlagNonfinite) return OZK2_ERR_NONFINITE;
+  return OZK2_OK;
+}
+
+int ozk2_moduli(int num_moduli, int32_t* p_out) {
+  int mods[kMaxModuli];
+  if (!p_out || hybrid_moduli(num_moduli, mods) != num_moduli) return -1;
+  for (int i = 0; i < num_moduli; ++i) p_out[i] = mods[i];
+  return num_moduli;
+}
+
+void ozk2_set_timing(int enable) {
+  std::lock_guard<std::mutex> lk(g_timing_mutex);
+  g_timing.enabled = enable != 0;
+  g_timing.have = false;
+}
+
+int ozk2_get_timing(float* ms, int max) {
+  std::lock_guard<std::mutex> lk(g_timing_mutex);
+  if (!g_timing.have || !ms) return -1;
+  if (cudaEventSynchronize(g_timing.ev[6]) != cudaSuccess) return -1;
+  int w = 0;
+  for (int i = 0; i < 6 && w < max; ++i, ++w) cudaEventElapsedTime(&ms[i], g_timing.ev[i], g_timing.ev[i + 1]);
+  return w;
+}
+
+int ozk2_last_launch_count(void) { return t_launches; }
+
+ozk2_status ozk2_debug_fp8_gemm(int64_t m, int64_t n, int64_t k, const uint8_t* A8, int64_t lda8, const uint8_t* B8,
+                                int64_t ldb8, float* D, int64_t ldd, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (m < 0 || n < 0 || k < 0) return OZK2_ERR_INVALID_VALUE;
+  if (m > kMaxDim || n > kMaxDim || k > kMaxDim) return OZK2_ERR_UNSUPPORTED;
+  if (m == 0 || n == 0) return OZK2_OK;
+  if (!D || ldd < n) return OZK2_ERR_INVALID_VALUE;
+  if (k == 0) {
+    OZK2_TRY(cudaMemset2DAsync(D, size_t(ldd) * 4, 0, size_t(n) * 4, size_t(m), st));
+    return OZK2_OK;
+  }
+  if (!A8 || !B8 || lda8 < k || ldb8 < k || (lda8 % 16) || (ldb8 % 16) ||
+      (reinterpret_cast<uintptr_t>(A8) & 15u) || (reinterpret_cast<uintptr_t>(B8) & 15u))
+    return OZK2_ERR_INVALID_VALUE;
+  int sms = 0;
+  if (!device_info(&sms)) return OZK2_ERR_UNSUPPORTED;
+  if (!encode_fn()) return OZK2_ERR_CUDA;
+  GemmArgs g{};
+  g.mode = kModeRaw;
+  g.m = int(m);
+  g.n = int(n);
+  g.k = int(k);
+  g.num_sms = sms;
+  g.D = D;
+  g.ldd = ldd;
+  ozk2_status err = OZK2_OK;
+  uint8_t* ws = owned_workspace(256, &err);  // flag word only
+  if (!ws) return err;
+  g.flags = reinterpret_cast<uint32_t*>(ws);
+  OZK2_TRY(launch_fp8_gemm(g, A8, lda8, 1, B8, ldb8, 1, st));
+  return OZK2_OK;
+}
+
+ozk2_status ozk2_debug_scales(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                              int64_t ldb, int num_moduli, int32_t* e, int32_t* f, int32_t* eprime, int32_t* fprime,
+                              float* R, float* S, uint8_t* Abar, uint8_t* BbarT, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ozk2_status s = check_sizes(m, n, k, num_moduli);
+  if (s != OZK2_OK) return s;
+  if (m == 0 || n == 0 || k == 0 || !A || !B || lda < k || ldb < n) return OZK2_ERR_INVALID_VALUE;
+  Ctx c;
+  if ((s = setup(c, m, n, k, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
+  if ((s = phase_scales(c, A, lda, B, ldb)) != OZK2_OK) return s;
+  const Layout& L = c.L;
+  auto cp = [&](void* dst, size_t off, size_t bytes) -> cudaError_t {
+    if (!dst) return cudaSuccess;
+    return cudaMemcpyAsync(dst, c.ws + off, bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  OZK2_TRY(cp(e, L.e, 4 * size_t(m)));
+  OZK2_TRY(cp(f, L.f, 4 * size_t(n)));
+  OZK2_TRY(cp(eprime, L.eprime, 4 * size_t(m)));
+  OZK2_TRY(cp(fprime, L.fprime, 4 * size_t(n)));
+  OZK2_TRY(cp(R, L.R, 4 * size_t(m)));
+  OZK2_TRY(cp(S, L.S, 4 * size_t(n)));
+  OZK2_TRY(cp(Abar, L.Abar, size_t(m) * L.kp));
+  OZK2_TRY(cp(BbarT, L.BbarT, size_t(n) * L.kp));
+  return OZK2_OK;
+}
+
+ozk2_status ozk2_debug_residue_planes(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                                      int64_t ldb, int num_moduli, const int32_t* e, const int32_t* f,
+                                      uint8_t* planesA, uint8_t* planesB, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ozk2_status s = check_sizes(m, n, k, num_moduli);
+  if (s != OZK2_OK) return s;
+  if (m == 0 || n == 0 || k == 0 || !A || !B || !e || !f || !planesA || !planesB || lda < k || ldb < n)
+    return OZK2_ERR_INVALID_VALUE;
+  Ctx c;
+  if ((s = setup(c, m, n, k, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
+  return phase_residues(c, A, lda, B, ldb, e, f, planesA, planesB);
+}
+
+ozk2_status ozk2_debug_residue_products(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                                        const double* B, int64_t ldb, int num_moduli, const int32_t* e,
+                                        const int32_t* f, int16_t* Cres, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ozk2_status s = check_sizes(m, n, k, num_moduli);
+  if (s != OZK2_OK) return s;
+  if (m == 0 || n == 0 || k == 0 || !A || !B || !e || !f || !Cres || lda < k || ldb < n)
+    return OZK2_ERR_INVALID_VALUE;
+  Ctx c;
+  if ((s = setup(c, m, n, k, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
+  const Layout& L = c.L;
+  if ((s = phase_residues(c, A, lda, B, ldb, e, f, c.at<uint8_t>(L.planesA), c.at<uint8_t>(L.planesB))) != OZK2_OK)
+    return s;
+  if ((s = phase_products(c)) != OZK2_OK) return s;
+  OZK2_TRY(cudaMemcpy2DAsync(Cres, size_t(n) * 2, c.ws + L.cres, size_t(L.ldr) * 2, size_t(n) * 2,
+                             size_t(num_moduli) * size_t(m), cudaMemcpyDeviceToDevice, st));
+  return OZK2_OK;
+}
+
+ozk2_status ozk2_debug_crt(int64_t m, int64_t n, int num_moduli, const int16_t* Cres, const int32_t* e,
+                           const int32_t* f, double* C, int64_t ldc, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ozk2_status s = check_sizes(m, n, 1, num_moduli);
+  if (s != OZK2_OK) return s;
+  if (m == 0 || n == 0) return OZK2_OK;
+  if (!Cres || !e || !f || !C || ldc < n) return OZK2_ERR_INVALID_VALUE;
+  Ctx c;
+  if ((s = setup(c, m, n, 1, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
+  const Layout& L = c.L;
+  OZK2_TRY(cudaMemcpy2DAsync(c.ws + L.cres, size_t(L.ldr) * 2, Cres, size_t(n) * 2, size_t(n) * 2,
+                             size_t(num_moduli) * size_t(m), cudaMemcpyDeviceToDevice, st));
+  return phase_crt(c, e, f, nullptr, nullptr, C, ldc);
+}
+
+}  // extern "C"

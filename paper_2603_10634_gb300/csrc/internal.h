@@ -1,0 +1,123 @@
+// Internal declarations shared by the host code and the kernels of libozk2.
+//
+// Parameter blocks are passed to kernels by value (no __constant__ state), so calls
+// with different N on different streams never interfere.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace ozk2 {
+
+constexpr int kMaxModuli = 20;
+constexpr int kMaxLimbs = 8;    // 32-bit limbs of the CRT arithmetic (N <= 20 needs 6)
+constexpr int kPow2Table = 64;  // 2^t mod p for t in [0, 64)
+constexpr int kNumSquares = 6;  // squares lead the hybrid list (Sec. III-D)
+
+// Device flag bits (a uint32 word in every workspace)
+constexpr uint32_t kFlagTimeout = 1u;    // a bounded device wait gave up
+constexpr uint32_t kFlagRange = 2u;      // a scaled value exceeded the supported range
+constexpr uint32_t kFlagNonfinite = 4u;  // NaN / Inf input seen
+
+// Line status bits (one byte per row of A / column of B)
+constexpr uint8_t kLineZero = 1;       // no nonzero finite entry
+constexpr uint8_t kLineNonfinite = 2;  // holds NaN or Inf
+
+// Per-modulus constants for the residue, GEMM-epilogue and CRT kernels.
+struct ModTable {
+  int N;
+  int num_planes;                 // M_N (Sec. IV-B Eq. M)
+  int p[kMaxModuli];              // modulus
+  int half[kMaxModuli];           // floor(p / 2)
+  int s[kMaxModuli];              // sqrt(p) for squares, 16 for Karatsuba moduli
+  int plane0[kMaxModuli];         // first digit plane of the modulus
+  float inv_p[kMaxModuli];        // RN(1 / p)
+  float inv_s[kMaxModuli];        // RN(1 / s)
+  int w16[kMaxModuli][4];         // 2^(16 j) mod p, j = 0..3
+  int16_t pow2[kMaxModuli][kPow2Table];  // 2^t mod p
+};
+
+struct CrtTable {
+  int N;
+  int limbs;                           // L, 32-bit limbs of the signed result
+  int p[kMaxModuli];
+  uint32_t w[kMaxModuli][kMaxLimbs];   // q_l P / p_l mod P
+  float frac[kMaxModuli];              // w_l / P (quotient estimate)
+  uint32_t P[kMaxLimbs];
+  uint32_t halfP[kMaxLimbs];           // P / 2 (P is even: 1024 is a modulus)
+};
+
+// Host-side constant generation (moduli.cpp)
+bool build_mod_table(int N, ModTable* mt);
+bool build_crt_table(int N, CrtTable* ct);
+int hybrid_moduli(int N, int* out);  // returns N or -1
+float p_prime_f32(int N);            // RD_fp32((log2(P - 1) - 1) / 2)
+float delta_f32();                   // RD_fp32(-1 / (2 - 2^-21))
+float bound_factor_f32(int64_t k);   // RU_fp32(1 + k 2^-24)
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (each returns the cudaError_t of its launch)
+// ---------------------------------------------------------------------------
+
+// scale.cu
+cudaError_t launch_scale_rows(const double* A, int64_t lda, int m, int k, int kp,
+                              int32_t* eprime, uint8_t* rowstat, uint8_t* Abar,
+                              uint32_t* flags, cudaStream_t st);
+cudaError_t launch_colmax(const double* B, int64_t ldb, int k, int n,
+                          unsigned long long* colmax, uint32_t* colbad, cudaStream_t st);
+cudaError_t launch_scale_cols(const double* B, int64_t ldb, int k, int n, int kp,
+                              const unsigned long long* colmax, const uint32_t* colbad,
+                              int32_t* fprime, uint8_t* colstat, uint8_t* BbarT,
+                              uint32_t* flags, cudaStream_t st);
+cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t* fprime,
+                             const uint8_t* rowstat, const uint8_t* colstat,
+                             const float* R, const float* S, float pprime, float delta,
+                             int32_t* e, int32_t* f, cudaStream_t st);
+
+// resid.cu
+cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp,
+                                 const int32_t* e, const ModTable& mt, uint8_t* planes,
+                                 uint32_t* flags, cudaStream_t st);
+cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp,
+                                 const int32_t* f, const ModTable& mt, uint8_t* planes,
+                                 uint32_t* flags, cudaStream_t st);
+
+// gemm.cu
+enum GemmMode { kModeResidue = 0, kModeBound = 1, kModeRaw = 2 };
+
+struct GemmArgs {
+  int mode;
+  int m, n, k;
+  int num_sms;
+  // residue products
+  int16_t* cres;
+  int64_t ldr;          // int16 elements per row of a residue plane
+  int64_t res_stride;   // elements between residue planes
+  const ModTable* mt;
+  // bound product
+  float factor;
+  float* R;
+  float* S;
+  // raw product
+  float* D;
+  int64_t ldd;
+  uint32_t* flags;
+};
+// A operand: `planes_a` digit planes (K-major, rows x k bytes, row stride lda8 bytes,
+// plane stride rows * lda8); B operand the same with n rows.
+cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a,
+                            const uint8_t* b, int64_t ldb8, int planes_b, cudaStream_t st);
+
+// crt.cu
+cudaError_t launch_crt(const int16_t* cres, int64_t ldr, int64_t res_stride, int m, int n,
+                       const int32_t* e, const int32_t* f, const uint8_t* rowstat,
+                       const uint8_t* colstat, double* C, int64_t ldc, const CrtTable& ct,
+                       cudaStream_t st);
+
+// tensor maps (api.cu)
+bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows,
+                    int64_t planes, int64_t row_stride_bytes, int box_rows);
+
+}  // namespace ozk2

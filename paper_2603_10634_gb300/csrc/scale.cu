@@ -1,0 +1,228 @@
+// Accurate-mode scaling, Sec. III-E of the paper (workflow steps 1 and 3 of Sec. IV-B).
+//
+//   e'_i = 7 - floor(log2 max_h |a_ih|)             (Eq. def:mu'nu', mu'_i = 2^e'_i)
+//   Abar_ih = RU_E4M3(2^e'_i |a_ih|)                 (cast to E4M3 in round-up mode)
+//   e_i = e'_i + int(P' + delta log2 max_j cbar_ij)  (Eq. mu-computation)
+// and the same for the columns of B, whose bound operand is stored transposed
+// (n x kp, K-major) so that both GEMM operands are K-major.
+//
+// Everything up to the exponent rule is integer manipulation of the IEEE-754
+// encoding: no FP64 arithmetic and no 2^e' factor is ever formed (e' reaches 1081
+// for subnormal rows, beyond the double range).  Non-finite entries count as 0 and
+// mark their row / column; a row with no nonzero finite entry gets e' = e = 0.
+#include "device.cuh"
+
+namespace ozk2 {
+namespace {
+
+constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+constexpr unsigned long long kFracMask = (1ull << 52) - 1;
+
+// floor(log2 x) of a positive finite double given by its bits.
+__device__ __forceinline__ int floor_log2_bits(unsigned long long mag) {
+  const int be = static_cast<int>(mag >> 52);
+  if (be != 0) return be - 1023;
+  return (63 - __clzll(mag)) - 1074;  // subnormal
+}
+
+// E4M3 code of the least E4M3 value >= |x| 2^sh, for |x| given by its (finite) bits and
+// |x| 2^sh < 2^8.  Positive values below 2^-9 give the smallest subnormal, 2^-9.
+// E4M3 codes of non-negative values increase with the value, so rounding the
+// 3-bit mantissa up may carry into the exponent field and stay correct.
+__device__ __forceinline__ uint32_t ru_e4m3_scaled(unsigned long long mag, int sh) {
+  if (mag == 0) return 0;
+  int be = static_cast<int>(mag >> 52);
+  unsigned long long f52 = mag & kFracMask;
+  int lg;
+  if (be == 0) {
+    const int top = 63 - __clzll(f52);
+    lg = top - 1074;
+    f52 = (f52 << (52 - top)) & kFracMask;
+  } else {
+    lg = be - 1023;
+  }
+  const int ev = lg + sh;  // floor(log2) of the scaled value, <= 7
+  if (ev >= -6) {          // E4M3 normal range
+    return static_cast<uint32_t>(((ev + 7) << 3) + static_cast<int>(f52 >> 49) +
+                                 ((f52 & ((1ull << 49) - 1)) != 0 ? 1 : 0));
+  }
+  if (ev >= -9) {  // E4M3 subnormal m 2^-9, m = ceil(v 2^9) in 1..8
+    const int shr = 52 - (ev + 9);
+    const unsigned long long mant = f52 | (1ull << 52);
+    return static_cast<uint32_t>((mant >> shr) + ((mant & ((1ull << shr) - 1)) != 0 ? 1 : 0));
+  }
+  return 1;
+}
+
+// One warp per row of A: row maximum, e'_i, row status, then Abar (m x kp bytes).
+__global__ void __launch_bounds__(256) scale_rows_kernel(const double* __restrict__ A, int64_t lda,
+                                                         int m, int k, int kp,
+                                                         int32_t* __restrict__ eprime,
+                                                         uint8_t* __restrict__ rowstat,
+                                                         uint8_t* __restrict__ Abar,
+                                                         uint32_t* flags) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (row >= m) return;
+  const double* a = A + static_cast<int64_t>(row) * lda;
+  unsigned long long mx = 0;
+  bool bad = false;
+  for (int h = lane; h < k; h += 32) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
+    if (b >= kInfBits) bad = true;
+    else mx = b > mx ? b : mx;
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+    mx = o > mx ? o : mx;
+  }
+  bad = __any_sync(0xffffffffu, bad);
+  const int ep = (mx == 0) ? 0 : 7 - floor_log2_bits(mx);
+  if (lane == 0) {
+    eprime[row] = ep;
+    rowstat[row] = static_cast<uint8_t>((mx == 0 ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
+    if (bad) atomicOr(flags, kFlagNonfinite);
+  }
+  uint8_t* out = Abar + static_cast<int64_t>(row) * kp;
+  for (int h0 = lane * 4; h0 < kp; h0 += 128) {
+    uint32_t word = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int h = h0 + t;
+      if (h < k) {
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
+        if (b < kInfBits) word |= ru_e4m3_scaled(b, ep) << (8 * t);
+      }
+    }
+    *reinterpret_cast<uint32_t*>(out + h0) = word;
+  }
+}
+
+constexpr int kColRows = 256;
+
+// Column maxima of |B| (as ordered IEEE bit patterns) and non-finite flags.
+__global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ B, int64_t ldb,
+                                                     int k, int n,
+                                                     unsigned long long* __restrict__ colmax,
+                                                     uint32_t* __restrict__ colbad) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int h0 = blockIdx.y * kColRows;
+  const int h1 = min(k, h0 + kColRows);
+  unsigned long long mx = 0;
+  bool bad = false;
+  for (int h = h0; h < h1; ++h) {
+    const unsigned long long b =
+        static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
+    if (b >= kInfBits) bad = true;
+    else mx = b > mx ? b : mx;
+  }
+  if (mx) atomicMax(colmax + j, mx);
+  if (bad) atomicOr(colbad + j, 1u);
+}
+
+// Bbar^T (n x kp bytes): thread (column j, 32 consecutive h) writes 32 bytes of row j.
+__global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restrict__ B, int64_t ldb,
+                                                         int k, int n, int kp,
+                                                         const unsigned long long* __restrict__ colmax,
+                                                         const uint32_t* __restrict__ colbad,
+                                                         int32_t* __restrict__ fprime,
+                                                         uint8_t* __restrict__ colstat,
+                                                         uint8_t* __restrict__ BbarT,
+                                                         uint32_t* flags) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int hb = blockIdx.y;
+  if (j >= n) return;
+  const unsigned long long mx = colmax[j];
+  const bool bad = colbad[j] != 0;
+  const int fp = (mx == 0) ? 0 : 7 - floor_log2_bits(mx);
+  if (hb == 0) {
+    fprime[j] = fp;
+    colstat[j] = static_cast<uint8_t>((mx == 0 ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
+    if (bad) atomicOr(flags, kFlagNonfinite);
+  }
+  uint32_t w[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) w[q] = 0;
+#pragma unroll
+  for (int t = 0; t < 32; ++t) {
+    const int h = hb * 32 + t;
+    if (h < k) {
+      const unsigned long long b =
+          static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
+      if (b < kInfBits) w[t >> 2] |= ru_e4m3_scaled(b, fp) << (8 * (t & 3));
+    }
+  }
+  uint4* dst = reinterpret_cast<uint4*>(BbarT + static_cast<int64_t>(j) * kp + hb * 32);
+  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// e = e' + floor(RD(P' + RD(delta * log2 R))) [Eq. mu-computation].  log2 is the FP32
+// rounding of the double-precision log2 (a correctly rounded FP32 log2 except in
+// vanishingly rare ties); P' + delta log2 R is evaluated in FP32 round-down.
+__device__ __forceinline__ int final_exponent(int ep, uint8_t stat, float rmax, float pprime,
+                                              float delta) {
+  if (stat & kLineZero) return 0;
+  if (!(rmax > 0.0f)) return ep + static_cast<int>(floorf(pprime));
+  const float lg = __double2float_rn(log2(static_cast<double>(rmax)));
+  const float t1 = __fmul_rd(delta, lg);
+  const float t2 = __fadd_rd(pprime, t1);
+  return ep + static_cast<int>(floorf(t2));
+}
+
+__global__ void exponents_kernel(int m, int n, const int32_t* __restrict__ eprime,
+                                 const int32_t* __restrict__ fprime,
+                                 const uint8_t* __restrict__ rowstat,
+                                 const uint8_t* __restrict__ colstat, const float* __restrict__ R,
+                                 const float* __restrict__ S, float pprime, float delta,
+                                 int32_t* __restrict__ e, int32_t* __restrict__ f) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) {
+    e[t] = final_exponent(eprime[t], rowstat[t], R[t], pprime, delta);
+  } else if (t < m + n) {
+    const int j = t - m;
+    f[j] = final_exponent(fprime[j], colstat[j], S[j], pprime, delta);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_scale_rows(const double* A, int64_t lda, int m, int k, int kp, int32_t* eprime,
+                              uint8_t* rowstat, uint8_t* Abar, uint32_t* flags, cudaStream_t st) {
+  const int rows_per_block = 8;
+  scale_rows_kernel<<<(m + rows_per_block - 1) / rows_per_block, 256, 0, st>>>(
+      A, lda, m, k, kp, eprime, rowstat, Abar, flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colmax(const double* B, int64_t ldb, int k, int n, unsigned long long* colmax,
+                          uint32_t* colbad, cudaStream_t st) {
+  dim3 grid((n + 255) / 256, (k + kColRows - 1) / kColRows);
+  colmax_kernel<<<grid, 256, 0, st>>>(B, ldb, k, n, colmax, colbad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale_cols(const double* B, int64_t ldb, int k, int n, int kp,
+                              const unsigned long long* colmax, const uint32_t* colbad,
+                              int32_t* fprime, uint8_t* colstat, uint8_t* BbarT, uint32_t* flags,
+                              cudaStream_t st) {
+  dim3 grid((n + 255) / 256, kp / 32);
+  scale_cols_kernel<<<grid, 256, 0, st>>>(B, ldb, k, n, kp, colmax, colbad, fprime, colstat, BbarT,
+                                          flags);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t* fprime,
+                             const uint8_t* rowstat, const uint8_t* colstat, const float* R,
+                             const float* S, float pprime, float delta, int32_t* e, int32_t* f,
+                             cudaStream_t st) {
+  const int total = m + n;
+  exponents_kernel<<<(total + 255) / 256, 256, 0, st>>>(m, n, eprime, fprime, rowstat, colstat, R, S,
+                                                        pprime, delta, e, f);
+  return cudaGetLastError();
+}
+
+}  // namespace ozk2

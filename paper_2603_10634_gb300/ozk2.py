@@ -1,0 +1,193 @@
+"""Python binding of libozk2: argument marshalling only.
+
+Every step of the emulated DGEMM runs in the library's CUDA kernels on the tensors'
+device and torch's current stream; torch supplies device memory and streams.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _lib
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _check_matrix(x, name, dtype=torch.float64):
+    if not isinstance(x, torch.Tensor) or x.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D torch tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    if x.size(1) > 1 and x.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major (unit stride along columns)")
+
+
+def _ld(x):
+    return max(1, x.stride(0) if x.size(0) > 1 else x.size(1))
+
+
+def moduli(num_moduli=12):
+    """The first N moduli of the hybrid list."""
+    lib = _lib.load()
+    buf = (ctypes.c_int32 * num_moduli)()
+    if lib.ozk2_moduli(num_moduli, buf) != num_moduli:
+        raise ValueError("num_moduli must be in 1..20")
+    return list(buf)
+
+
+def workspace_size(m, n, k, num_moduli=12):
+    return int(_lib.load().ozk2_workspace_size(m, n, k, num_moduli))
+
+
+def dgemm(A, B, num_moduli=12, out=None, workspace=None):
+    """C = A @ B in emulated FP64 (A: m x k, B: k x n, float64 CUDA tensors, row-major).
+
+    ``workspace`` may be a uint8 CUDA tensor of at least ``workspace_size`` bytes;
+    otherwise the library's own per-device workspace is used."""
+    _check_matrix(A, "A")
+    _check_matrix(B, "B")
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {A.shape} @ {B.shape}")
+    if A.device != B.device:
+        raise ValueError("A and B must be on the same device")
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    else:
+        _check_matrix(out, "out")
+        if tuple(out.shape) != (m, n):
+            raise ValueError("out has the wrong shape")
+    lib = _lib.load()
+    with torch.cuda.device(A.device):
+        st = _stream(A.device)
+        if workspace is None:
+            s = lib.ozk2_dgemm(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(out), _ld(out), num_moduli, st)
+        else:
+            s = lib.ozk2_dgemm_ws(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(out), _ld(out), num_moduli,
+                                  _ptr(workspace), workspace.numel(), st)
+    _lib.check(s, "ozk2_dgemm")
+    return out
+
+
+def device_status(workspace=None, device=None):
+    """Synchronise the current stream and return (and clear) the device flag status name."""
+    lib = _lib.load()
+    s = lib.ozk2_device_status(_ptr(workspace), _stream(device))
+    return _lib.STATUS.get(s, s)
+
+
+def set_timing(enable=True):
+    _lib.load().ozk2_set_timing(1 if enable else 0)
+
+
+PHASES = ("scale", "bound_gemm", "exponents", "residues", "residue_gemm", "crt")
+
+
+def get_timing():
+    """Per-phase milliseconds of the last timed call (dict), or None."""
+    buf = (ctypes.c_float * 6)()
+    n = _lib.load().ozk2_get_timing(buf, 6)
+    if n < 0:
+        return None
+    return {PHASES[i]: float(buf[i]) for i in range(n)}
+
+
+def last_launch_count():
+    return int(_lib.load().ozk2_last_launch_count())
+
+
+# ----------------------------------------------------------------- parity hooks
+
+def kp_of(k):
+    return 32 * ((k + 31) // 32)
+
+
+def num_planes(num_moduli):
+    return 2 * num_moduli if num_moduli <= 6 else 3 * num_moduli - 6
+
+
+def fp8_gemm(A8, B8, k=None):
+    """D = A8 @ B8^T, FP8 E4M3 codes (uint8, K-major, row stride multiple of 16) -> float32."""
+    m, n = A8.shape[0], B8.shape[0]
+    k = A8.shape[1] if k is None else k
+    D = torch.empty((m, n), dtype=torch.float32, device=A8.device)
+    lib = _lib.load()
+    s = lib.ozk2_debug_fp8_gemm(m, n, k, _ptr(A8), A8.stride(0), _ptr(B8), B8.stride(0), _ptr(D), n,
+                                _stream(A8.device))
+    _lib.check(s, "ozk2_debug_fp8_gemm")
+    return D
+
+
+def scales(A, B, num_moduli=12):
+    """Scaling intermediates: dict of e, f, eprime, fprime, R, S, Abar (m x kp), BbarT (n x kp)."""
+    _check_matrix(A, "A")
+    _check_matrix(B, "B")
+    m, k = A.shape
+    n = B.shape[1]
+    dev = A.device
+    kp = kp_of(k)
+    out = dict(e=torch.empty(m, dtype=torch.int32, device=dev), f=torch.empty(n, dtype=torch.int32, device=dev),
+               eprime=torch.empty(m, dtype=torch.int32, device=dev),
+               fprime=torch.empty(n, dtype=torch.int32, device=dev),
+               R=torch.empty(m, dtype=torch.float32, device=dev), S=torch.empty(n, dtype=torch.float32, device=dev),
+               Abar=torch.empty((m, kp), dtype=torch.uint8, device=dev),
+               BbarT=torch.empty((n, kp), dtype=torch.uint8, device=dev))
+    lib = _lib.load()
+    s = lib.ozk2_debug_scales(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), num_moduli, _ptr(out["e"]),
+                              _ptr(out["f"]), _ptr(out["eprime"]), _ptr(out["fprime"]), _ptr(out["R"]),
+                              _ptr(out["S"]), _ptr(out["Abar"]), _ptr(out["BbarT"]), _stream(dev))
+    _lib.check(s, "ozk2_debug_scales")
+    return out
+
+
+def residue_planes(A, B, e, f, num_moduli=12):
+    """Digit planes (uint8 E4M3 codes): planesA (M_N x m x kp), planesB (M_N x n x kp)."""
+    m, k = A.shape
+    n = B.shape[1]
+    kp = kp_of(k)
+    M = num_planes(num_moduli)
+    pa = torch.zeros((M, m, kp), dtype=torch.uint8, device=A.device)
+    pb = torch.zeros((M, n, kp), dtype=torch.uint8, device=A.device)
+    e = e.to(device=A.device, dtype=torch.int32).contiguous()
+    f = f.to(device=A.device, dtype=torch.int32).contiguous()
+    s = _lib.load().ozk2_debug_residue_planes(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), num_moduli, _ptr(e),
+                                              _ptr(f), _ptr(pa), _ptr(pb), _stream(A.device))
+    _lib.check(s, "ozk2_debug_residue_planes")
+    return pa, pb
+
+
+def residue_products(A, B, e, f, num_moduli=12):
+    """C'_l for l = 1..N as an int16 tensor N x m x n."""
+    m, k = A.shape
+    n = B.shape[1]
+    out = torch.empty((num_moduli, m, n), dtype=torch.int16, device=A.device)
+    e = e.to(device=A.device, dtype=torch.int32).contiguous()
+    f = f.to(device=A.device, dtype=torch.int32).contiguous()
+    s = _lib.load().ozk2_debug_residue_products(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), num_moduli, _ptr(e),
+                                                _ptr(f), _ptr(out), _stream(A.device))
+    _lib.check(s, "ozk2_debug_residue_products")
+    return out
+
+
+def crt(Cres, e, f, num_moduli=None):
+    """C from residue products (N x m x n int16) and exponents."""
+    N, m, n = Cres.shape
+    num_moduli = N if num_moduli is None else num_moduli
+    Cres = Cres.contiguous()
+    dev = Cres.device
+    e = e.to(device=dev, dtype=torch.int32).contiguous()
+    f = f.to(device=dev, dtype=torch.int32).contiguous()
+    C = torch.empty((m, n), dtype=torch.float64, device=dev)
+    s = _lib.load().ozk2_debug_crt(m, n, num_moduli, _ptr(Cres), _ptr(e), _ptr(f), _ptr(C), n, _stream(dev))
+    _lib.check(s, "ozk2_debug_crt")
+    return C

@@ -29,3 +29,17 @@ def read_golden(name):
 @pytest.fixture(scope="session")
 def golden():
     return read_golden
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    """The CUDA device with libozk2 built and loaded; fails loudly without a GPU."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test selected but no CUDA device is visible")
+    from paper_2603_10634_gb300 import _lib, build
+
+    build.build()
+    _lib.load()
+    return torch.device("cuda:0")
