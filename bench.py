@@ -1,0 +1,435 @@
+"""Benchmark: emulated DGEMM throughput (2mnk / t) of the FP8 Ozaki-II path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--size 16384] [--moduli 12] [--phi 1.0]
+
+One step is one ozk2_dgemm call: scaling pass, FP8 bound product, exponents,
+residues and digit planes, 3N FP8 residue products with mod-reduce, CRT and inverse
+scaling, on m = n = k = 16384 float64 inputs generated on the device from the
+paper's distribution (U - 0.5) exp(phi N(0,1)) (seed 0 for A, 1 for B).  Inputs
+(2 GiB each) are larger than the 129 MB L2, so no flush is needed between steps.
+
+Under torchrun (--gpus N > 1) every rank runs the same problem on its own GPU
+(replicas: the method has no exchange step), ranks are fenced by barriers and
+the slowest rank's time defines the step time.
+
+--impl reference times the CPU oracle (the plain Python/numpy implementation of
+the method) on the host cores, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "emulated DGEMM TFLOP/s (2mnk/t) at FP64-level error vs native FP64, 16384³"
+NOMINAL_FP8_TFLOPS = 4500.0  # dense FP8 per GPU, the FP8-count roofline of the method
+NOMINAL_HBM_GBS = 7700.0
+PROFILES = os.path.join(ROOT, "profiles")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=16384)
+    ap.add_argument("--moduli", type=int, default=12)
+    ap.add_argument("--phi", type=float, default=1.0)
+    ap.add_argument("--no-native", action="store_true", help="skip the native FP64 reference timing")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
+    ap.add_argument("--samples", type=int, default=32, help="entries checked against the exact product")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {
+        "workload": f"square DGEMM m=n=k={a.size}, phi={a.phi}, N={a.moduli} moduli, accurate mode",
+        "m": a.size, "n": a.size, "k": a.size, "phi": a.phi, "num_moduli": a.moduli, "seed": 0,
+        "l2": "inputs larger than L2 (2 x 8 k^2 bytes), no flush",
+        "parallelism": f"replicas x{a.gpus}" if a.gpus > 1 else "single GPU",
+    }
+
+
+# ------------------------------------------------------------------ distributed
+def dist_init(a):
+    rank, world = 0, 1
+    if a.gpus > 1 or "RANK" in os.environ:
+        import torch.distributed as dist
+
+        rank = int(os.environ.get("RANK", 0))
+        world = int(os.environ.get("WORLD_SIZE", 1))
+        backend = "nccl" if a.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks, traffic
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ["gemm.cu", "device.cuh", "internal.h"]:
+        with open(os.path.join(ROOT, "paper_2603_10634_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(size, moduli):
+    """DRAM bytes per residue-product launch from the committed ncu summary, if it was
+    taken on the current kernel source and this workload."""
+    p = os.path.join(PROFILES, "residue_gemm_traffic.txt")
+    try:
+        kv = {}
+        with open(p) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    key, v = line.split(":", 1)
+                    kv[key.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        if int(kv.get("size", -1)) != size or int(kv.get("num_moduli", -1)) != moduli:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ exact error samples
+def _exact_dot(a, b):
+    """Exact sum a_h b_h of two float64 sequences, as (numerator, denominator)."""
+    num, den = 0, 1
+    for x, y in zip(a, b):
+        x, y = float(x), float(y)
+        if x == 0.0 or y == 0.0:
+            continue
+        nx, dx = x.as_integer_ratio()
+        ny, dy = y.as_integer_ratio()
+        d = dx * dy
+        if d > den:
+            num *= d // den
+            den = d
+        num += nx * ny * (den // d)
+    return num, den
+
+
+def error_samples(A, B, C, Cnat, samples, seed=7):
+    import numpy as np
+    import torch
+
+    m, n = C.shape
+    rng = np.random.default_rng(seed)
+    rows = torch.as_tensor(rng.integers(0, m, samples), device=A.device)
+    cols = torch.as_tensor(rng.integers(0, n, samples), device=A.device)
+    Ar = A[rows].cpu().numpy()
+    Bc = B[:, cols].cpu().numpy()
+    Cs = C[rows, cols].cpu().numpy()
+    Cn = Cnat[rows, cols].cpu().numpy() if Cnat is not None else None
+    emu, nat, bound_ok = [], [], True
+    k = A.shape[1]
+    for t in range(samples):
+        num, den = _exact_dot(Ar[t], Bc[:, t])
+        anum, aden = _exact_dot(abs(Ar[t]), abs(Bc[:, t]))
+        ab = anum / aden
+        cn, cd = float(Cs[t]).as_integer_ratio()
+        err = abs(num * cd - cn * den) / (den * cd)
+        emu.append(err / ab)
+        bound_ok &= err <= k * 2.0**-52 * ab
+        if Cn is not None:
+            nn, nd = float(Cn[t]).as_integer_ratio()
+            nat.append(abs(num * nd - nn * den) / (den * nd) / ab)
+    out = {"samples": samples, "max_rel_err_vs_absAB": max(emu), "bound_k_2^-52_holds": bool(bound_ok)}
+    if nat:
+        out["native_fp64_max_rel_err_vs_absAB"] = max(nat)
+        out["within_2x_native"] = bool(max(emu) <= 2 * max(max(nat), 2.0**-53))
+    return out
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(size, phi, moduli):
+    """Time the oracle once on a size^3 instance of the same generator; returns seconds."""
+    import numpy as np
+
+    from oracle import ozaki2 as oz
+    from paper_2603_10634_gb300 import workloads
+
+    A, B = workloads.problem(size, size, size, phi, seed=0, device="cpu")
+    A, B = A.numpy(), B.numpy()
+    t0 = time.perf_counter()
+    oz.ozk2_dgemm(A, B, moduli)
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(a, size=1024):
+    dt = oracle_sample(size, a.phi, a.moduli)
+    return {"value": 2.0 * size**3 / dt / 1e12, "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
+            "sample": f"full oracle pipeline on one m=n=k={size} instance of the same generator "
+                      f"(phi={a.phi}, N={a.moduli}); {dt:.1f} s; python single-threaded except numpy BLAS"}
+
+
+def run_reference(a, rank, world):
+    """--impl reference: the CPU oracle as it stands, one bounded sample per step."""
+    if rank != 0:
+        return
+    size = int(os.environ.get("OZK2_REFERENCE_SAMPLE", "512"))
+    for _ in range(a.warmup):
+        oracle_sample(size, a.phi, a.moduli)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle_sample(size, a.phi, a.moduli)
+    dt = (time.perf_counter() - t0) / a.steps
+    val = 2.0 * size**3 / dt / 1e12
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+int", "data": "synthetic",
+        "config": workload_config(a),
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
+                         "sample": f"each step: full oracle pipeline on one m=n=k={size} instance of the "
+                                   f"workload's generator; python single-threaded except numpy BLAS"},
+        "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(a, rank, world):
+    import torch
+
+    import paper_2603_10634_gb300 as ozk
+    from paper_2603_10634_gb300 import _lib, workloads
+
+    _lib.load()  # fails loudly without the built library
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m = n = k = a.size
+    N = a.moduli
+    flops = 2.0 * m * n * k
+    A, B = workloads.problem(m, n, k, a.phi, seed=0, device=dev)
+    C = torch.empty((m, n), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(a.warmup):
+        ozk.dgemm(A, B, num_moduli=N, out=C)
+    torch.cuda.synchronize(dev)
+    assert ozk.device_status() == "OZK2_OK"
+    launches_per_call = ozk.last_launch_count()
+
+    # ---- timed region: K back-to-back calls, device inputs
+    ozk.set_timing(True)
+    phase_sum = {p: 0.0 for p in ozk.PHASES}
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(a.steps):
+            ozk.dgemm(A, B, num_moduli=N, out=C)
+            ph = ozk.get_timing()  # waits for this call's last event (host-side, ~us)
+            for p in ozk.PHASES:
+                phase_sum[p] += ph[p]
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    ozk.set_timing(False)
+    ms = start.elapsed_time(end) / a.steps
+    ms = max_over_ranks(ms, world, dev)
+    status = ozk.device_status()
+    phases = {p: v / a.steps for p, v in phase_sum.items()}
+    value = world * flops / (ms * 1e-3) / 1e12
+
+    # ---- roofline of the dominant kernel (the residue-product GEMM)
+    peaks, src = measured_peaks()
+    fp8_peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
+    gemm_flops = 3 * N * flops
+    achieved = gemm_flops / (phases["residue_gemm"] * 1e-3) / 1e12
+    traffic = recorded_traffic(a.size, N)
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp8_peak, "traffic": traffic,
+                "kernel": "fp8_gemm_kernel<residue> (3N FP8 products + mod-reduce)",
+                "peak_source": f"{src} bf16_tflops_sustained x 2 (dense FP8 / BF16 nominal ratio)"}
+    conv_bytes = (16 + 1 + (2 * N if N <= 6 else 3 * N - 6)) * (m * k + k * n) + 8 * m * n
+    t_roof = (3 * N + 1) * flops / (NOMINAL_FP8_TFLOPS * 1e12) + conv_bytes / (NOMINAL_HBM_GBS * 1e9)
+    roof_tflops = flops / t_roof / 1e12
+    fp8_count = {"roofline_tflops": roof_tflops, "frac": value / world / roof_tflops,
+                 "definition": "(3N+1) 2mnk at 4.5 PF/s + conversion bytes at 7.7 TB/s (nominal)"}
+
+    # ---- native FP64 reference point and error samples
+    Cnat, native = None, None
+    if not a.no_native:
+        Cnat = torch.empty_like(C)
+        torch.matmul(A, B, out=Cnat)
+        torch.cuda.synchronize(dev)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        torch.matmul(A, B, out=Cnat)
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        native = {"tflops": flops / (s0.elapsed_time(s1) * 1e-3) / 1e12, "impl": "torch.matmul float64 (cuBLAS)"}
+    err = error_samples(A, B, C, Cnat, a.samples) if rank == 0 else None
+
+    # ---- end to end: host buffers in and out, through the public API
+    e2e = None
+    if not a.no_e2e:
+        hA = A.cpu().pin_memory()
+        hB = B.cpu().pin_memory()
+        hC = torch.empty((m, n), dtype=torch.float64).pin_memory()
+        dA, dB = torch.empty_like(A), torch.empty_like(B)
+
+        def e2e_step():
+            dA.copy_(hA, non_blocking=True)
+            dB.copy_(hB, non_blocking=True)
+            ozk.dgemm(dA, dB, num_moduli=N, out=C)
+            hC.copy_(C, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(a.steps):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier(world)
+        ems = max_over_ranks(s0.elapsed_time(s1) / a.steps, world, dev)
+        e2e = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": hA.numel() * 8 + hB.numel() * 8, "d2h_bytes_per_step": hC.numel() * 8,
+               "ms_per_step": ems}
+        del hA, hB, hC, dA, dB
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_baseline(a)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f8e4m3", "emulates": "f64", "data": "synthetic",
+            "config": workload_config(a), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches_per_call * a.steps, "clocks": clk.summary(), "phases_ms": phases,
+            "fp8_count_roofline": fp8_count, "native_fp64": native, "error": err, "device_status": status,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    rank, world = dist_init(a)
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+    else:
+        run_ours(a, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -98,7 +98,7 @@ struct Layout {
   int planes;
   size_t flags, R, S, colmax, colbad, zero_end;
   size_t eprime, fprime, e, f, rowstat, colstat;
-  size_t Abar, BbarT, planesA, planesB, cres, total;
+  size_t Abar, BbarT, planesA, planesB, cres, scratch, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -131,6 +131,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N) {
   L.planesA = take(size_t(L.planes) * m * L.kp);
   L.planesB = take(size_t(L.planes) * n * L.kp);
   L.cres = take(2 * size_t(N) * m * L.ldr);
+  L.scratch = take(fp8_gemm_scratch_bytes(kMaxGemmCtas));
   L.total = o;
   return L;
 }
@@ -263,6 +264,7 @@ ozk2_status phase_products(Ctx& c) {
   g.cres = c.at<int16_t>(L.cres);
   g.ldr = L.ldr;
   g.res_stride = int64_t(c.m) * L.ldr;
+  g.scratch = c.at<uint32_t>(L.scratch);
   g.mt = &c.tab->mt;
   g.flags = c.at<uint32_t>(L.flags);
   OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA), L.kp, L.planes, c.at<uint8_t>(L.planesB), L.kp, L.planes,

@@ -1,28 +1,36 @@
-// FP8 tensor-core products of the method on tcgen05 (sm_103a), one kernel, three
-// epilogues:
+// FP8 tensor-core products of the method on tcgen05 (sm_103a): one persistent kernel,
+// three epilogues.
 //
-//   residue : for modulus l and an output tile, three products into three TMEM
-//             accumulators, then C'_l = mod(., p_l) in registers and an int16 store.
-//               square p = s^2 : X = A1 B2, Y = A2 B1, Z = A2 B2,
-//                                C'_l = mod(s (X + Y) + Z, p)     [Eq. 3matmult-notKaratsuba]
-//               Karatsuba      : Dx = Ax Bx (x = 1, 2, 3),
-//                                C'_l = mod(256 D1 + D2 + 16 (D3 - D1 - D2), p)
-//                                     = mod(16 mod(15 D1 + D3 - D2, p) + D2, p)  [Eq. C'-Karatsuba]
-//             Every accumulator holds one product over at most 2^16 terms of digits
-//             |d| <= 16, so its FP32 value is an exact integer of magnitude <= 2^24
-//             (Eq. error-free-FP8-matmult).  Longer reductions are split into 2^16
-//             blocks whose residues are added mod p.
+//   residue : C'_l = mod(A'_l B'_l, p_l) for an output tile, from digit-plane products
+//             held in TMEM and reduced mod p in registers:
+//               square p = s^2 : X = A1 B2 + A2 B1 (one accumulator), Z = A2 B2,
+//                                C'_l = mod(s X + Z, p)           [Eq. 3matmult-notKaratsuba]
+//               Karatsuba      : Dx = Ax Bx, x = 1, 2, 3,
+//                                256 D1 + D2 + 16 (D3 - D1 - D2) = 16 (15 D1 - D2 + D3) + D2
+//                                                                  [Eq. C'-Karatsuba]
+//             Every FP32 accumulator is an exact integer of magnitude <= 2^24
+//             (Eq. error-free-FP8-matmult): a Karatsuba product over at most 2^16
+//             terms of digits |d| <= 16, or the shared square accumulator over at most
+//             2^15.  Longer reductions run in blocks whose residues are added mod p.
 //   bound   : Cbar = RU((1 + k 2^-24) Abar Bbar) folded into row / column maxima
 //             (Eq. barCupper); Cbar itself is never stored.
 //   raw     : D = A B^T in FP32 (a parity hook for the tensor-core path).
 //
-// Structure: persistent CTAs (one per SM), 192 threads in three roles.
-//   warp 0      TMA producer: 128 x 128 byte tiles of A and B^T (K-major, 128-byte
-//               swizzle) into a 6-stage shared-memory ring, mbarrier complete_tx.
-//   warp 1      TMEM allocation (512 columns) and the single MMA-issuing thread:
-//               tcgen05.mma kind::f8f6f4, M = N = 128, K = 32 per instruction.
-//   warps 2-5   epilogue: tcgen05.ld of their TMEM lane quadrant, integer math,
-//               global stores.
+// Tiles are 128 x 256 (M x N) with two 256-column FP32 accumulators, the whole 512
+// columns of TMEM.  A square modulus is one round (X, Z).  A Karatsuba modulus is
+// two rounds: (D1, D2), whose epilogue parks mod(15 D1 - D2, p) and mod(D2, p) as an
+// int16 pair in a CTA-private scratch tile (L2-resident), then (D3), whose epilogue
+// finishes the residue.  The wide tile halves the operand bytes each SM pulls per
+// flop compared with 128 x 128.
+//
+// Roles (320 threads, one persistent CTA per SM):
+//   warp 0      TMA producer: 128-row A and 256-row B^T boxes of 128 bytes along K
+//               (K-major, 128-byte swizzle, zero fill past m, n, k) into a 4-stage
+//               ring of 48 KiB stages, mbarrier complete_tx.
+//   warp 1      TMEM allocation and the single MMA-issuing thread:
+//               tcgen05.mma.cta_group::1.kind::f8f6f4, M = 128, N = 256, K = 32.
+//   warps 2-9   epilogue: warp w reads TMEM lane quadrant w % 4, column half
+//               (w - 2) / 4, with tcgen05.ld; integer math; global stores.
 // Every wait is bounded (device.cuh); a wait that gives up raises a CTA-wide abort
 // flag and the global timeout flag, drains the copies and products this CTA has in
 // flight, frees TMEM and returns.
@@ -32,15 +40,18 @@ namespace ozk2 {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 128;
+constexpr int BN = 256;
 constexpr int BK = 128;  // bytes = FP8 elements per k-step (one 128-byte swizzle row)
-constexpr int kStages = 6;
-constexpr int kTileBytes = BM * BK;  // 16 KiB (BN == BM)
-constexpr int kStageBytes = 2 * kTileBytes;
-constexpr int kThreads = 192;
+constexpr int kStages = 4;
+constexpr int kATileBytes = BM * BK;  // 16 KiB
+constexpr int kBTileBytes = BN * BK;  // 32 KiB
+constexpr int kStageBytes = kATileBytes + kBTileBytes;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;
-constexpr int kChunk = 65536;  // exactness block of the residue products
-constexpr int kGroupM = 8;     // tile rasterisation: bands of 8 tile rows
+constexpr int kChunkKaratsuba = 65536;  // 2^16 * 16 * 16 = 2^24
+constexpr int kChunkSquare = 32768;     // shared accumulator: 2 * 2^15 * 16 * 16 = 2^24
+constexpr int kGroupM = 8;              // tile rasterisation: bands of 8 tile rows
 constexpr size_t kSmemBytes = 1024 + static_cast<size_t>(kStages) * kStageBytes + 256;
 
 struct EpiMod {
@@ -51,14 +62,14 @@ struct EpiMod {
 };
 
 struct GemmParams {
+  int mode;
   int m, n, k;
   int tiles_m, tiles_n, tiles;
   int num_units;
-  int kchunks;
-  int chunk_len;
   int16_t* cres;
   int64_t ldr;
   int64_t res_stride;
+  uint32_t* scratch;  // residue mode: BM x BN words per CTA
   EpiMod mod;
   float factor;
   float* R;
@@ -80,16 +91,56 @@ __device__ __forceinline__ void decode_unit(const GemmParams& P, int u, int& mod
   tn = r / gsz;
 }
 
-// Digit planes of product x of modulus `mod` (plane layout of the residue kernels).
-__device__ __forceinline__ void planes_of(int mode, int mod, int x, int& pa, int& pb) {
-  if (mode != kModeResidue) {
+// Round structure of a unit.
+struct UnitPlan {
+  int chunk_len;  // k per exactness block
+  int nchunks;
+  int nphases;    // rounds per block
+};
+
+template <int MODE>
+__device__ __forceinline__ UnitPlan plan_of(const GemmParams& P, int mod) {
+  UnitPlan u;
+  if (MODE == kModeResidue) {
+    const bool square = mod < kNumSquares;
+    u.chunk_len = square ? kChunkSquare : kChunkKaratsuba;
+    u.nphases = square ? 1 : 2;
+  } else {
+    u.chunk_len = ((P.k + BK - 1) / BK) * BK;
+    u.nphases = 1;
+  }
+  u.nchunks = (P.k + u.chunk_len - 1) / u.chunk_len;
+  return u;
+}
+
+// Products of one round: count, digit planes (pa, pb), target accumulator and whether
+// the product is the first writer of that accumulator in the round.
+template <int MODE>
+__device__ __forceinline__ int num_products(int mod, int phase) {
+  if (MODE != kModeResidue) return 1;
+  if (mod < kNumSquares) return 3;
+  return phase == 0 ? 2 : 1;
+}
+
+template <int MODE>
+__device__ __forceinline__ void product_of(int mod, int phase, int x, int& pa, int& pb, int& acc,
+                                           bool& first) {
+  if (MODE != kModeResidue) {
     pa = pb = 0;
+    acc = 0;
+    first = true;
   } else if (mod < kNumSquares) {
-    const int a0 = 2 * mod;  // (A1, B2), (A2, B1), (A2, B2)
+    const int a0 = 2 * mod;  // (A1, B2) -> X, (A2, B1) -> X, (A2, B2) -> Z
     pa = (x == 0) ? a0 : a0 + 1;
     pb = (x == 1) ? a0 : a0 + 1;
+    acc = (x == 2) ? 1 : 0;
+    first = (x != 1);
   } else {
-    pa = pb = 12 + 3 * (mod - kNumSquares) + x;  // (Ax, Bx)
+    const int a0 = 2 * kNumSquares + 3 * (mod - kNumSquares);
+    const int plane = (phase == 0) ? x : 2;  // (A1,B1) -> 0, (A2,B2) -> 1 ; then (A3,B3) -> 0
+    pa = pb = a0 + plane;
+    acc = (phase == 0) ? x : 0;
+    first = true;
   }
 }
 
@@ -109,11 +160,48 @@ __device__ __forceinline__ float warp_column_max(float (&v)[32], int lane) {
   return v[0];
 }
 
+__device__ __forceinline__ int acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
+
+// Store 32 int16 residues of one row (adding the previous block's residues when
+// `accumulate`), vectorised when the 32 columns are all inside the matrix.
+__device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int (&res)[32], bool accumulate,
+                                               int p, int h) {
+  if (gc + 32 <= n) {
+    uint4* o = reinterpret_cast<uint4*>(dst + gc);
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+      if (accumulate) {
+        const uint4 pv = o[w];
+        const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+        for (int z = 0; z < 4; ++z) {
+          res[w * 8 + 2 * z] = smod_small(res[w * 8 + 2 * z] + static_cast<int16_t>(pr[z] & 0xFFFFu), p, h);
+          res[w * 8 + 2 * z + 1] = smod_small(res[w * 8 + 2 * z + 1] + static_cast<int16_t>(pr[z] >> 16), p, h);
+        }
+      }
+      uint32_t pk[4];
+#pragma unroll
+      for (int z = 0; z < 4; ++z)
+        pk[z] = (static_cast<uint32_t>(res[w * 8 + 2 * z]) & 0xFFFFu) |
+                (static_cast<uint32_t>(res[w * 8 + 2 * z + 1]) << 16);
+      o[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (gc + j < n) {
+        int r = res[j];
+        if (accumulate) r = smod_small(r + dst[gc + j], p, h);
+        dst[gc + j] = static_cast<int16_t>(r);
+      }
+    }
+  }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ GemmParams prm) {
-  constexpr int NPROD = (MODE == kModeResidue) ? 3 : 1;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;
@@ -134,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(empty + s, 1);
     }
     mbar_init(tfull, 1);
-    mbar_init(tempty, 4 * 32);
+    mbar_init(tempty, 32 * kEpiWarps);
     mbar_init(done, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -162,28 +250,31 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
         int mod, tm, tn;
         decode_unit(prm, u, mod, tm, tn);
-        for (int c = 0; ok && c < prm.kchunks; ++c) {
-          const int k0 = c * prm.chunk_len;
-          const int k1 = min(prm.k, k0 + prm.chunk_len);
-          const int ksteps = (k1 - k0 + BK - 1) / BK;
-          for (int s = 0; ok && s < ksteps; ++s) {
-#pragma unroll
-            for (int x = 0; x < NPROD; ++x) {
-              if (!mbar_wait_bounded(empty + stage, phase ^ 1u, abort_flag)) {
-                ok = false;
-                break;
-              }
-              int pa, pb;
-              planes_of(MODE, mod, x, pa, pb);
-              uint8_t* dst = tiles + stage * kStageBytes;
-              mbar_arrive_expect_tx(full + stage, kStageBytes);
-              tma_load_3d(dst, &tmA, full + stage, k0 + s * BK, tm * BM, pa);
-              tma_load_3d(dst + kTileBytes, &tmB, full + stage, k0 + s * BK, tn * BN, pb);
-              issued |= 1u << stage;
-              issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
-              if (++stage == kStages) {
-                stage = 0;
-                phase ^= 1u;
+        const UnitPlan up = plan_of<MODE>(prm, mod);
+        for (int c = 0; ok && c < up.nchunks; ++c) {
+          const int k0 = c * up.chunk_len;
+          const int ksteps = (min(prm.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
+          for (int ph = 0; ok && ph < up.nphases; ++ph) {
+            const int np = num_products<MODE>(mod, ph);
+            for (int s = 0; ok && s < ksteps; ++s) {
+              for (int x = 0; x < np; ++x) {
+                if (!mbar_wait_bounded(empty + stage, phase ^ 1u, abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                int pa, pb, acc;
+                bool first;
+                product_of<MODE>(mod, ph, x, pa, pb, acc, first);
+                uint8_t* dst = tiles + stage * kStageBytes;
+                mbar_arrive_expect_tx(full + stage, kStageBytes);
+                tma_load_3d(dst, &tmA, full + stage, k0 + s * BK, tm * BM, pa);
+                tma_load_3d(dst + kATileBytes, &tmB, full + stage, k0 + s * BK, tn * BN, pb);
+                issued |= 1u << stage;
+                issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+                if (++stage == kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
               }
             }
           }
@@ -192,8 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (!ok) {
         *abort_flag = 1;
         atomicOr(prm.flags, kFlagTimeout);
-        // let the copies this thread issued land before the CTA exits
-        int no_abort = 0;
+        int no_abort = 0;  // let this thread's copies in flight land before exiting
         for (int s = 0; s < kStages; ++s)
           if (issued & (1u << s)) mbar_wait_bounded(full + s, (issued_phase >> s) & 1u, &no_abort);
       }
@@ -206,43 +296,50 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0, rc = 0;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
-        for (int c = 0; ok && c < prm.kchunks; ++c) {
-          if (!mbar_wait_bounded(tempty, (rc & 1u) ^ 1u, abort_flag)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const int k0 = c * prm.chunk_len;
-          const int k1 = min(prm.k, k0 + prm.chunk_len);
-          const int ksteps = (k1 - k0 + BK - 1) / BK;
-          for (int s = 0; ok && s < ksteps; ++s) {
+        int mod, tm, tn;
+        decode_unit(prm, u, mod, tm, tn);
+        const UnitPlan up = plan_of<MODE>(prm, mod);
+        for (int c = 0; ok && c < up.nchunks; ++c) {
+          const int k0 = c * up.chunk_len;
+          const int ksteps = (min(prm.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
+          for (int ph = 0; ok && ph < up.nphases; ++ph) {
+            if (!mbar_wait_bounded(tempty, (rc & 1u) ^ 1u, abort_flag)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const int np = num_products<MODE>(mod, ph);
+            for (int s = 0; ok && s < ksteps; ++s) {
+              for (int x = 0; x < np; ++x) {
+                if (!mbar_wait_bounded(full + stage, phase, abort_flag)) {
+                  ok = false;
+                  break;
+                }
+                tc_fence_after();
+                int pa, pb, acc;
+                bool first;
+                product_of<MODE>(mod, ph, x, pa, pb, acc, first);
+                const uint32_t sa = smem_addr(tiles + stage * kStageBytes);
+                const uint64_t adesc = sw128_kmajor_desc(sa);
+                const uint64_t bdesc = sw128_kmajor_desc(sa + kATileBytes);
+                const uint32_t dtm = tmem_base + static_cast<uint32_t>(acc * BN);
 #pragma unroll
-            for (int x = 0; x < NPROD; ++x) {
-              if (!mbar_wait_bounded(full + stage, phase, abort_flag)) {
-                ok = false;
-                break;
-              }
-              tc_fence_after();
-              const uint32_t sa = smem_addr(tiles + stage * kStageBytes);
-              const uint64_t adesc = sw128_kmajor_desc(sa);
-              const uint64_t bdesc = sw128_kmajor_desc(sa + kTileBytes);
-              const uint32_t dtm = tmem_base + static_cast<uint32_t>(x * BN);
-#pragma unroll
-              for (int kk = 0; kk < BK / 32; ++kk)
-                mma_fp8(dtm, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (s | kk) != 0 ? 1u : 0u);
-              mma_commit(empty + stage);
-              if (++stage == kStages) {
-                stage = 0;
-                phase ^= 1u;
+                for (int kk = 0; kk < BK / 32; ++kk)
+                  mma_fp8(dtm, adesc + 2ull * kk, bdesc + 2ull * kk, idesc,
+                          (first && s == 0 && kk == 0) ? 0u : 1u);
+                mma_commit(empty + stage);
+                if (++stage == kStages) {
+                  stage = 0;
+                  phase ^= 1u;
+                }
               }
             }
+            if (ok) mma_commit(tfull);
+            ++rc;
           }
-          if (ok) mma_commit(tfull);
-          ++rc;
         }
       }
-      // every product issued here must be complete before TMEM is released
-      mma_commit(done);
+      mma_commit(done);  // every product issued here completes before TMEM is freed
       int no_abort = 0;
       mbar_wait_bounded(done, 0, &no_abort);
       if (!ok) {
@@ -252,124 +349,117 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const int q = warp & 3;                 // TMEM lane quadrant this warp may access
+    const int chalf = (warp - 2) >> 2;      // column half of the tile
     const int row = q * 32 + lane;
-    const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16);
+    const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
+    uint32_t* scr = prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BN) + row * BN + chalf * (BN / 2);
     uint32_t rc = 0;
     bool ok = true;
     for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
       int mod, tm, tn;
       decode_unit(prm, u, mod, tm, tn);
+      const UnitPlan up = plan_of<MODE>(prm, mod);
       const int gi = tm * BM + row;
-      for (int c = 0; ok && c < prm.kchunks; ++c) {
-        ok = mbar_wait_bounded(tfull, rc & 1u, abort_flag);
-        ok = __all_sync(0xffffffffu, ok);
-        if (!ok) break;
-        tc_fence_after();
-        if constexpr (MODE == kModeResidue) {
-          const int p = prm.mod.p[mod], h = prm.mod.half[mod], sq = prm.mod.s[mod];
-          const float ip = prm.mod.inv_p[mod];
-          const bool square = mod < kNumSquares;
-          int16_t* dst = prm.cres + static_cast<int64_t>(mod) * prm.res_stride +
-                         static_cast<int64_t>(gi) * prm.ldr;
+      for (int c = 0; ok && c < up.nchunks; ++c) {
+        for (int ph = 0; ok && ph < up.nphases; ++ph) {
+          ok = mbar_wait_bounded(tfull, rc & 1u, abort_flag);
+          ok = __all_sync(0xffffffffu, ok);
+          if (!ok) break;
+          tc_fence_after();
+          if constexpr (MODE == kModeResidue) {
+            const int p = prm.mod.p[mod], h = prm.mod.half[mod], sq = prm.mod.s[mod];
+            const float ip = prm.mod.inv_p[mod];
+            int16_t* dst = prm.cres + static_cast<int64_t>(mod) * prm.res_stride + static_cast<int64_t>(gi) * prm.ldr;
 #pragma unroll 1
-          for (int cb = 0; cb < BN / 32; ++cb) {
-            uint32_t v0[32], v1[32], v2[32];
-            tmem_ld_32cols(tq + cb * 32, v0);
-            tmem_ld_32cols(tq + BN + cb * 32, v1);
-            tmem_ld_32cols(tq + 2 * BN + cb * 32, v2);
-            tmem_ld_wait();
-            const int gc = tn * BN + cb * 32;
-            int res[32];
+            for (int cb = 0; cb < BN / 64; ++cb) {
+              const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
+              int res[32];
+              if (mod < kNumSquares) {
+                uint32_t vx[32], vz[32];
+                tmem_ld_32cols(tq + cb * 32, vx);
+                tmem_ld_32cols(tq + BN + cb * 32, vz);
+                tmem_ld_wait();
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              const int a = __float2int_rn(__uint_as_float(v0[j]));
-              const int b = __float2int_rn(__uint_as_float(v1[j]));
-              const int d = __float2int_rn(__uint_as_float(v2[j]));
-              int r;
-              if (square) {
-                r = smod_i32(sq * (a + b) + d, p, h, ip);
-              } else {
-                const int t = smod_i32(15 * a + d - b, p, h, ip);
-                r = smod_i32(16 * t + b, p, h, ip);
-              }
-              res[j] = r;
-            }
-            if (gi < prm.m) {
-              if (gc + 32 <= prm.n) {
-                uint4* o = reinterpret_cast<uint4*>(dst + gc);
-                if (c > 0) {
-#pragma unroll
-                  for (int w = 0; w < 4; ++w) {
-                    const uint4 pv = o[w];
-                    const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
-#pragma unroll
-                    for (int z = 0; z < 4; ++z) {
-                      res[w * 8 + 2 * z] = smod_small(res[w * 8 + 2 * z] + static_cast<int16_t>(pr[z] & 0xFFFFu), p, h);
-                      res[w * 8 + 2 * z + 1] = smod_small(res[w * 8 + 2 * z + 1] + static_cast<int16_t>(pr[z] >> 16), p, h);
-                    }
-                  }
-                }
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                  uint32_t pk[4];
-#pragma unroll
-                  for (int z = 0; z < 4; ++z)
-                    pk[z] = (static_cast<uint32_t>(res[w * 8 + 2 * z]) & 0xFFFFu) |
-                            (static_cast<uint32_t>(res[w * 8 + 2 * z + 1]) << 16);
-                  o[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-                }
-              } else {
+                for (int j = 0; j < 32; ++j) res[j] = smod_i32(sq * acc_int(vx[j]) + acc_int(vz[j]), p, h, ip);
+              } else if (ph == 0) {
+                uint32_t v1[32], v2[32];
+                tmem_ld_32cols(tq + cb * 32, v1);
+                tmem_ld_32cols(tq + BN + cb * 32, v2);
+                tmem_ld_wait();
+                uint32_t pk[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                  if (gc + j < prm.n) {
-                    int r = res[j];
-                    if (c > 0) r = smod_small(r + dst[gc + j], p, h);
-                    dst[gc + j] = static_cast<int16_t>(r);
+                  const int d2 = acc_int(v2[j]);
+                  const int u1 = smod_i32(15 * acc_int(v1[j]) - d2, p, h, ip);
+                  const int r2 = smod_i32(d2, p, h, ip);
+                  pk[j] = (static_cast<uint32_t>(u1) & 0xFFFFu) | (static_cast<uint32_t>(r2) << 16);
+                }
+                uint4* sp = reinterpret_cast<uint4*>(scr + cb * 32);
+#pragma unroll
+                for (int w = 0; w < 8; ++w) sp[w] = make_uint4(pk[4 * w], pk[4 * w + 1], pk[4 * w + 2], pk[4 * w + 3]);
+                continue;  // the residue is finished in the next round
+              } else {
+                uint32_t v3[32];
+                tmem_ld_32cols(tq + cb * 32, v3);
+                tmem_ld_wait();
+                const uint4* sp = reinterpret_cast<const uint4*>(scr + cb * 32);
+#pragma unroll
+                for (int w = 0; w < 8; ++w) {
+                  const uint4 pv = sp[w];
+                  const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                  for (int z = 0; z < 4; ++z) {
+                    const int j = 4 * w + z;
+                    const int u1 = static_cast<int16_t>(pr[z] & 0xFFFFu);
+                    const int r2 = static_cast<int16_t>(pr[z] >> 16);
+                    const int uu = smod_i32(u1 + acc_int(v3[j]), p, h, ip);
+                    res[j] = smod_i32(16 * uu + r2, p, h, ip);
                   }
                 }
               }
+              if (gi < prm.m) store_residues(dst, gc, prm.n, res, c > 0, p, h);
             }
-          }
-        } else if constexpr (MODE == kModeBound) {
-          float rmax = 0.0f;
+          } else if constexpr (MODE == kModeBound) {
+            float rmax = 0.0f;
 #pragma unroll 1
-          for (int cb = 0; cb < BN / 32; ++cb) {
-            uint32_t v0[32];
-            tmem_ld_32cols(tq + cb * 32, v0);
-            tmem_ld_wait();
-            const int gc = tn * BN + cb * 32;
-            float cv[32];
+            for (int cb = 0; cb < BN / 64; ++cb) {
+              uint32_t v0[32];
+              tmem_ld_32cols(tq + cb * 32, v0);
+              tmem_ld_wait();
+              const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
+              float cv[32];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-              float cb_ = __fmul_ru(prm.factor, __uint_as_float(v0[j]));
-              cb_ = (gi < prm.m && gc + j < prm.n) ? cb_ : 0.0f;
-              rmax = fmaxf(rmax, cb_);
-              cv[j] = cb_;
+              for (int j = 0; j < 32; ++j) {
+                float cj = __fmul_ru(prm.factor, __uint_as_float(v0[j]));
+                cj = (gi < prm.m && gc + j < prm.n) ? cj : 0.0f;
+                rmax = fmaxf(rmax, cj);
+                cv[j] = cj;
+              }
+              const float cm = warp_column_max(cv, lane);
+              if (gc + lane < prm.n && cm > 0.0f)
+                atomicMax(reinterpret_cast<int*>(prm.S) + gc + lane, __float_as_int(cm));
             }
-            const float cm = warp_column_max(cv, lane);
-            if (gc + lane < prm.n && cm > 0.0f)
-              atomicMax(reinterpret_cast<int*>(prm.S) + gc + lane, __float_as_int(cm));
-          }
-          if (gi < prm.m && rmax > 0.0f) atomicMax(reinterpret_cast<int*>(prm.R) + gi, __float_as_int(rmax));
-        } else {
+            if (gi < prm.m && rmax > 0.0f) atomicMax(reinterpret_cast<int*>(prm.R) + gi, __float_as_int(rmax));
+          } else {
 #pragma unroll 1
-          for (int cb = 0; cb < BN / 32; ++cb) {
-            uint32_t v0[32];
-            tmem_ld_32cols(tq + cb * 32, v0);
-            tmem_ld_wait();
-            const int gc = tn * BN + cb * 32;
-            if (gi < prm.m) {
-              float* o = prm.D + static_cast<int64_t>(gi) * prm.ldd;
+            for (int cb = 0; cb < BN / 64; ++cb) {
+              uint32_t v0[32];
+              tmem_ld_32cols(tq + cb * 32, v0);
+              tmem_ld_wait();
+              const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
+              if (gi < prm.m) {
+                float* o = prm.D + static_cast<int64_t>(gi) * prm.ldd;
 #pragma unroll
-              for (int j = 0; j < 32; ++j)
-                if (gc + j < prm.n) o[gc + j] = __uint_as_float(v0[j]);
+                for (int j = 0; j < 32; ++j)
+                  if (gc + j < prm.n) o[gc + j] = __uint_as_float(v0[j]);
+              }
             }
           }
+          tc_fence_before();
+          mbar_arrive(tempty);
+          ++rc;
         }
-        tc_fence_before();
-        mbar_arrive(tempty);
-        ++rc;
       }
     }
     if (!ok) {
@@ -393,8 +483,7 @@ cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUte
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            static_cast<int>(kSmemBytes));
     if (err != cudaSuccess) return err;
     configured[dev] = true;
@@ -405,9 +494,12 @@ cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUte
 
 }  // namespace
 
-cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a,
-                            const uint8_t* b, int64_t ldb8, int planes_b, cudaStream_t st) {
+size_t fp8_gemm_scratch_bytes(int num_ctas) { return static_cast<size_t>(num_ctas) * BM * BN * 4; }
+
+cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a, const uint8_t* b,
+                            int64_t ldb8, int planes_b, cudaStream_t st) {
   GemmParams prm{};
+  prm.mode = g.mode;
   prm.m = g.m;
   prm.n = g.n;
   prm.k = g.k;
@@ -416,11 +508,10 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.tiles = prm.tiles_m * prm.tiles_n;
   const int nmod = (g.mode == kModeResidue) ? g.mt->N : 1;
   prm.num_units = prm.tiles * nmod;
-  prm.chunk_len = (g.mode == kModeResidue) ? kChunk : ((g.k + BK - 1) / BK) * BK;
-  prm.kchunks = (g.k + prm.chunk_len - 1) / prm.chunk_len;
   prm.cres = g.cres;
   prm.ldr = g.ldr;
   prm.res_stride = g.res_stride;
+  prm.scratch = g.scratch;
   if (g.mode == kModeResidue) {
     for (int l = 0; l < g.mt->N; ++l) {
       prm.mod.p[l] = g.mt->p[l];
@@ -428,6 +519,7 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
       prm.mod.s[l] = g.mt->s[l];
       prm.mod.inv_p[l] = g.mt->inv_p[l];
     }
+    if (!g.scratch) return cudaErrorInvalidValue;
   }
   prm.factor = g.factor;
   prm.R = g.R;
@@ -439,7 +531,8 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   CUtensorMap ta, tb;
   if (!encode_fp8_map(&ta, a, g.k, g.m, planes_a, lda8, BM)) return cudaErrorInvalidValue;
   if (!encode_fp8_map(&tb, b, g.k, g.n, planes_b, ldb8, BN)) return cudaErrorInvalidValue;
-  const int grid = prm.num_units < g.num_sms ? prm.num_units : g.num_sms;
+  const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
+  const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {
     case kModeResidue:
       return launch_mode<kModeResidue>(prm, ta, tb, grid, st);

@@ -95,6 +95,7 @@ struct GemmArgs {
   int16_t* cres;
   int64_t ldr;          // int16 elements per row of a residue plane
   int64_t res_stride;   // elements between residue planes
+  uint32_t* scratch;    // fp8_gemm_scratch_bytes(num_sms) bytes, residue products only
   const ModTable* mt;
   // bound product
   float factor;
@@ -107,6 +108,8 @@ struct GemmArgs {
 };
 // A operand: `planes_a` digit planes (K-major, rows x k bytes, row stride lda8 bytes,
 // plane stride rows * lda8); B operand the same with n rows.
+constexpr int kMaxGemmCtas = 192;  // persistent GEMM CTAs (scratch is sized for this many)
+size_t fp8_gemm_scratch_bytes(int num_ctas);
 cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a,
                             const uint8_t* b, int64_t ldb8, int planes_b, cudaStream_t st);
 

@@ -18,7 +18,7 @@
 //
 // Rows of A produce K-major planes directly.  Columns of B are written transposed
 // (plane rows are columns of B), so both operands of the tensor-core products are
-// K-major.  Each thread owns 32 elements: it decodes them once into two registers
+// K-major.  Each thread owns 16 elements: it decodes them once into two registers
 // each, then loops over the moduli.
 #include <cuda_fp8.h>
 
@@ -72,21 +72,20 @@ struct ModConsts {
   float inv_p;
 };
 
+// Symmetric residue of the signed integer a' = +-M' 2^t' encoded in v.  The sign is
+// applied before the reduction, so the result needs no correction afterwards.
 __device__ __forceinline__ int residue_of(uint2 v, const ModConsts& c, const int16_t* pow2,
                                           bool use_pow2) {
   const uint32_t c0 = v.x & 0xFFFFu, c1 = v.x >> 16, c2 = v.y & 0xFFFFu, c3 = (v.y >> 16) & 0x1Fu;
-  const int x = static_cast<int>(c0 + c1 * static_cast<uint32_t>(c.w1) +
-                                 c2 * static_cast<uint32_t>(c.w2) + c3 * static_cast<uint32_t>(c.w3));
-  int r = smod_i32(x, c.p, c.h, c.inv_p);
+  int x = static_cast<int>(c0 + c1 * static_cast<uint32_t>(c.w1) + c2 * static_cast<uint32_t>(c.w2) +
+                           c3 * static_cast<uint32_t>(c.w3));  // < 2^28.1
   if (use_pow2) {
     const int tp = static_cast<int>((v.y >> 21) & 63u);
-    r = smod_i32(r * static_cast<int>(pow2[tp]), c.p, c.h, c.inv_p);  // |r 2^t'| < 2^19.2
+    x = smod_i32(x, c.p, c.h, c.inv_p) * static_cast<int>(pow2[tp]);  // |x| < 2^19.2
   }
-  if (v.y >> 31) {
-    r = -r;
-    r = (r > c.p - 1 - c.h) ? r - c.p : r;  // only for even p: -(-p/2) -> -p/2
-  }
-  return r;
+  const int neg = -static_cast<int>(v.y >> 31);  // 0 or -1
+  x = (x ^ neg) - neg;
+  return smod_i32(x, c.p, c.h, c.inv_p);
 }
 
 // Digits of residue r as floats (exact small integers, never -0).
@@ -137,27 +136,30 @@ __device__ __forceinline__ ModConsts consts_of(const ModTable& mt, int l) {
   return c;
 }
 
-// Rows of A.  One warp covers 1024 consecutive k of one row: lane l owns elements
-// base + 128 g + 4 l + {0..3}, g = 0..7, so loads and 4-byte plane stores coalesce.
+// Rows of A.  One warp covers 512 consecutive k of one row: lane l owns elements
+// base + 128 g + 4 l + {0..3}, g = 0..3, so loads and 4-byte plane stores coalesce.
+constexpr int kRowGroups = 4;
+constexpr int kRowSpan = 128 * kRowGroups;
+
 __global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a,
                                                             const __grid_constant__ ModTable mt) {
   __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
-  const int nkw = (a.kp + 1023) / 1024;
+  const int nkw = (a.kp + kRowSpan - 1) / kRowSpan;
   const int64_t items = static_cast<int64_t>(a.lines) * nkw;
   bool range_err = false;
   for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5);
        it < items; it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
     const int row = static_cast<int>(it / nkw);
-    const int base = static_cast<int>(it % nkw) * 1024;
+    const int base = static_cast<int>(it % nkw) * kRowSpan;
     const double* x = a.X + static_cast<int64_t>(row) * a.ldx;
     const int e = a.exps[row];
-    uint2 v[32];
+    uint2 v[4 * kRowGroups];
     uint32_t any_tp = 0;
 #pragma unroll
-    for (int g = 0; g < 8; ++g) {
+    for (int g = 0; g < kRowGroups; ++g) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int h = base + g * 128 + lane * 4 + t;
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a,
         const int s = mt.s[l];
         const float inv_s = mt.inv_s[l];
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
+        for (int g = 0; g < kRowGroups; ++g) {
           float d1[4], d2[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t)
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a,
         }
       } else {
 #pragma unroll
-        for (int g = 0; g < 8; ++g) {
+        for (int g = 0; g < kRowGroups; ++g) {
           float d1[4], d2[4], d3[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t)
@@ -207,32 +209,39 @@ __global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a,
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
-// Columns of B.  Thread (column j, 32 consecutive h) reads B[h][j] (coalesced across
-// the warp's consecutive columns) and writes 32 bytes of row j of every plane.
+// Columns of B.  A warp covers 16 columns x 32 consecutive h: lanes 2jj and 2jj+1 take
+// column j0 + jj, rows h0..h0+15 and h0+16..h0+31.  Loads read two 128-byte row
+// segments per instruction; each lane pair writes one full 32-byte sector of row j of
+// every plane.
 __global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a,
                                                             const __grid_constant__ ModTable mt) {
   __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
+  const int lane = threadIdx.x & 31;
+  const int jj = lane >> 1, half = lane & 1;
+  const int warps_per_block = blockDim.x >> 5;
+  const int ncg = (a.lines + 15) / 16;  // column groups of 16
   const int nkb = a.kp / 32;
-  const int64_t items = static_cast<int64_t>(a.lines) * nkb;
+  const int64_t items = static_cast<int64_t>(ncg) * nkb;
   bool range_err = false;
-  for (int64_t it = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-       it - threadIdx.x < items; it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const bool active = it < items;
-    const int hb = active ? static_cast<int>(it / a.lines) : 0;
-    const int j = active ? static_cast<int>(it % a.lines) : 0;
+  for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5);
+       it < items; it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
+    const int hb = static_cast<int>(it / ncg);
+    const int j = static_cast<int>(it % ncg) * 16 + jj;
+    const bool active = j < a.lines;
     const int e = active ? a.exps[j] : 0;
-    uint2 v[32];
+    const int h0 = hb * 32 + half * 16;
+    uint2 v[16];
     uint32_t any_tp = 0;
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const int h = hb * 32 + t;
+    for (int t = 0; t < 16; ++t) {
+      const int h = h0 + t;
       const double val = (active && h < a.k) ? __ldg(a.X + static_cast<int64_t>(h) * a.ldx + j) : 0.0;
       v[t] = encode_element(val, e, range_err);
       any_tp |= v[t].y & (63u << 21);
     }
     const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
-    uint8_t* colp = a.planes + static_cast<int64_t>(j) * a.kp + hb * 32;
+    uint8_t* colp = a.planes + static_cast<int64_t>(active ? j : 0) * a.kp + h0;
     for (int l = 0; l < mt.N; ++l) {
       const ModConsts c = consts_of(mt, l);
       const int16_t* pw = pow2_s + l * kPow2Table;
@@ -240,9 +249,9 @@ __global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a,
       if (l < kNumSquares) {
         const int s = mt.s[l];
         const float inv_s = mt.inv_s[l];
-        uint32_t w1[8], w2[8];
+        uint32_t w1[4], w2[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 4; ++q) {
           float d1[4], d2[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t)
@@ -251,17 +260,13 @@ __global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a,
           w2[q] = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
         }
         if (active) {
-          uint4* o1 = reinterpret_cast<uint4*>(pl);
-          uint4* o2 = reinterpret_cast<uint4*>(pl + a.plane_stride);
-          o1[0] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-          o1[1] = make_uint4(w1[4], w1[5], w1[6], w1[7]);
-          o2[0] = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-          o2[1] = make_uint4(w2[4], w2[5], w2[6], w2[7]);
+          *reinterpret_cast<uint4*>(pl) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+          *reinterpret_cast<uint4*>(pl + a.plane_stride) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
         }
       } else {
-        uint32_t w1[8], w2[8], w3[8];
+        uint32_t w1[4], w2[4], w3[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
+        for (int q = 0; q < 4; ++q) {
           float d1[4], d2[4], d3[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t)
@@ -271,15 +276,9 @@ __global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a,
           w3[q] = e4m3x4(d3[0], d3[1], d3[2], d3[3]);
         }
         if (active) {
-          uint4* o1 = reinterpret_cast<uint4*>(pl);
-          uint4* o2 = reinterpret_cast<uint4*>(pl + a.plane_stride);
-          uint4* o3 = reinterpret_cast<uint4*>(pl + 2 * a.plane_stride);
-          o1[0] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-          o1[1] = make_uint4(w1[4], w1[5], w1[6], w1[7]);
-          o2[0] = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-          o2[1] = make_uint4(w2[4], w2[5], w2[6], w2[7]);
-          o3[0] = make_uint4(w3[0], w3[1], w3[2], w3[3]);
-          o3[1] = make_uint4(w3[4], w3[5], w3[6], w3[7]);
+          *reinterpret_cast<uint4*>(pl) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+          *reinterpret_cast<uint4*>(pl + a.plane_stride) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+          *reinterpret_cast<uint4*>(pl + 2 * a.plane_stride) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
         }
       }
     }
@@ -302,7 +301,7 @@ cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int
                                  const int32_t* e, const ModTable& mt, uint8_t* planes,
                                  uint32_t* flags, cudaStream_t st) {
   ResidArgs a{A, lda, m, k, kp, e, planes, static_cast<int64_t>(m) * kp, flags};
-  const int64_t warps = static_cast<int64_t>(m) * ((kp + 1023) / 1024);
+  const int64_t warps = static_cast<int64_t>(m) * ((kp + kRowSpan - 1) / kRowSpan);
   residues_rows_kernel<<<grid_for(warps, 8), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
@@ -311,8 +310,8 @@ cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int
                                  const int32_t* f, const ModTable& mt, uint8_t* planes,
                                  uint32_t* flags, cudaStream_t st) {
   ResidArgs a{B, ldb, n, k, kp, f, planes, static_cast<int64_t>(n) * kp, flags};
-  const int64_t threads = static_cast<int64_t>(n) * (kp / 32);
-  residues_cols_kernel<<<grid_for(threads, 256), 256, 0, st>>>(a, mt);
+  const int64_t warps = static_cast<int64_t>((n + 15) / 16) * (kp / 32);
+  residues_cols_kernel<<<grid_for(warps, 8), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
 

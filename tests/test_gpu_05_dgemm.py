@@ -66,8 +66,11 @@ def test_empty_and_degenerate_shapes(cuda):
         if k == 0:
             assert np.all(C == 0)
         elif m and n:
-            want = (A.numpy() @ B.numpy())
-            assert np.allclose(C, want, rtol=1e-15, atol=0)
+            sc = ozk.scales(A.to(cuda), B.to(cuda), num_moduli=12)
+            r = oz.ozk2_dgemm(A.numpy(), B.numpy(), 12, e=sc["e"].cpu().numpy(), f=sc["f"].cpu().numpy())
+            assert np.array_equal(C.view(np.uint64), r["C"].view(np.uint64))
+            absab = np.abs(A.numpy()) @ np.abs(B.numpy())
+            assert np.all(np.abs(C - A.numpy() @ B.numpy()) <= (k + 2) * 2.0**-52 * absab)
 
 
 def test_zero_rows_and_nonfinite(cuda):
