@@ -91,6 +91,30 @@ ozk2_status ozk2_dgemm_ws(int64_t m, int64_t n, int64_t k,
                           int num_moduli, void *workspace, size_t workspace_bytes,
                           ozk2_stream_t stream);
 
+/*
+ * ozk2_dgemm_noalloc - ozk2_dgemm for callers that may not allocate device memory
+ * (their GPU memory is owned by a host application or framework, or they cannot
+ * afford the device-wide synchronisation that cudaMalloc / cudaFree may cause).  It
+ * allocates nothing: its workspace is a static device array of this library, of
+ * OZK2_NOALLOC_MAX_BYTES bytes, which every GPU that loads it keeps until the process
+ * exits.  The paper has no counterpart; this is an interface convenience.
+ *
+ * Same arguments and result as ozk2_dgemm.  Returns OZK2_ERR_UNSUPPORTED, touching no
+ * memory, when ozk2_workspace_size(m, n, k, num_moduli) exceeds OZK2_NOALLOC_MAX_BYTES
+ * (for N = 12 that is square sizes up to 1664).  The first call on a device looks
+ * the array up (cudaGetSymbolAddress, which may load this part of the library on that
+ * device); make that first call before any stream capture.  All calls on a device share
+ * the array and each call overwrites it, so calls whose work overlaps on the GPU (other
+ * streams, other threads) race; serialise them.  Device-side conditions are not
+ * reported through ozk2_device_status (non-finite inputs still give NaN rows/columns).
+ */
+#define OZK2_NOALLOC_MAX_BYTES (256u * 1024u * 1024u)
+ozk2_status ozk2_dgemm_noalloc(int64_t m, int64_t n, int64_t k,
+                               const double *A, int64_t lda,
+                               const double *B, int64_t ldb,
+                               double *C, int64_t ldc,
+                               int num_moduli, ozk2_stream_t stream);
+
 /* ozk2_status_string - a static, human-readable name for a status code. */
 const char *ozk2_status_string(ozk2_status status);
 

@@ -20,7 +20,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libozk2.so")
-SOURCES = ["api.cu", "scale.cu", "resid.cu", "gemm.cu", "crt.cu", "moduli.cpp"]
+SOURCES = ["api.cu", "scale.cu", "resid.cu", "gemm.cu", "crt.cu", "noalloc.cu", "moduli.cpp"]
 HEADERS = ["internal.h", "device.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
