@@ -350,15 +350,16 @@ ozk2_status dgemm_impl(int64_t m, int64_t n, int64_t k, const double* A, int64_t
 }  // namespace
 
 bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t planes,
-                    int64_t row_stride_bytes, int box_rows) {
+                    int64_t row_stride_bytes, int box_rows, int box_cols) {
   EncodeTiledFn fn = encode_fn();
-  if (!fn || cols < 1 || rows < 1 || planes < 1) return false;
+  if (!fn || cols < 1 || rows < 1 || planes < 1 || (box_cols != 128 && box_cols != 64)) return false;
   const cuuint64_t dims[3] = {cuuint64_t(cols), cuuint64_t(rows), cuuint64_t(planes)};
   const cuuint64_t strides[2] = {cuuint64_t(row_stride_bytes), cuuint64_t(row_stride_bytes) * cuuint64_t(rows)};
-  const cuuint32_t box[3] = {128u, cuuint32_t(box_rows), 1u};
+  const cuuint32_t box[3] = {cuuint32_t(box_cols), cuuint32_t(box_rows), 1u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
+  const CUtensorMapSwizzle sw = (box_cols == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
   return fn(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 

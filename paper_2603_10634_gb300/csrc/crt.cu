@@ -4,13 +4,16 @@
 //   C'_ij = mod(sum_l w_l C'_l,ij, P),  w_l = q_l P / p_l,  symmetric in [-P/2, P/2)
 //   C_ij  = RN(C'_ij 2^-(e_i + f_j))
 //
-// The sum is formed exactly in integer arithmetic: with u_l = C'_l mod p_l in [0, p_l),
-// limb t of sum_l u_l w_l is accumulated in a 64-bit integer (each term < 2^43, N <= 20
-// terms), the quotient Q = round(V / P) is estimated in FP32 from sum_l u_l (w_l / P)
-// (error < 0.05), V - Q P is normalised to L signed 32-bit limbs and corrected once
-// into [-P/2, P/2).  The double is then assembled bit by bit with round-to-nearest-even
-// at the right position, which gives the correctly rounded value including gradual
-// underflow and overflow to infinity.  No FP64 arithmetic is used.
+// The sum is formed exactly in integer arithmetic: with u_l = C'_l mod p_l in [0, p_l)
+// and the weights split into 16-bit limbs, limb t of sum_l u_l w_l accumulates in a
+// 32-bit integer (each term < 2^27, N <= 20 terms, sum < 2^31.4), one IMAD per limb.
+// The quotient Q = round(V / P) comes from the fixed-point estimate
+// sum_l u_l round(2^16 w_l / P) (error < 0.17); V - Q P is normalised to L signed
+// 32-bit limbs.  When the estimate is at least 0.3 away from a rounding boundary the
+// result is already in [-P/2, P/2); otherwise one exact comparison with +-P/2 corrects
+// it.  The double is then assembled bit by bit with round-to-nearest-even at the right
+// position, which gives the correctly rounded value including gradual underflow and
+// overflow to infinity.  No FP64 arithmetic is used.
 #include "device.cuh"
 
 namespace ozk2 {
@@ -43,21 +46,10 @@ __device__ __forceinline__ bool is_negative(const uint32_t (&x)[L]) {
 }
 
 template <int L>
-__device__ __forceinline__ double crt_finish(int64_t (&acc)[L], float est, int scale, bool nan_out,
+__device__ __forceinline__ double crt_finish(uint32_t (&v)[L], bool exact_check, int scale, bool nan_out,
                                              const CrtTable& ct) {
-  const int64_t q = static_cast<int64_t>(__float2int_rn(est));
-#pragma unroll
-  for (int t = 0; t < L; ++t) acc[t] -= q * static_cast<int64_t>(ct.P[t]);
-  uint32_t v[L];
-  int64_t carry = 0;
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    const int64_t x = acc[t] + carry;
-    v[t] = static_cast<uint32_t>(x);
-    carry = x >> 32;  // arithmetic shift: signed carry
-  }
-  // |v| < 0.55 P here; one correction brings it into [-P/2, P/2)
-  {
+  // v = V - Q P in two's complement; |v| < 1.5 P.  Bring it into [-P/2, P/2).
+  if (exact_check) {
     uint32_t tst[L];
 #pragma unroll
     for (int t = 0; t < L; ++t) tst[t] = v[t];
@@ -120,71 +112,87 @@ __device__ __forceinline__ double crt_finish(int64_t (&acc)[L], float est, int s
   return __longlong_as_double(static_cast<long long>(bits));
 }
 
-// Thread (row i, 4 consecutive columns).
-template <int L>
-__global__ void __launch_bounds__(256) crt_kernel(const int16_t* __restrict__ cres, int64_t ldr,
-                                                  int64_t rstride, int m, int n,
-                                                  const int32_t* __restrict__ e,
-                                                  const int32_t* __restrict__ f,
-                                                  const uint8_t* __restrict__ rowstat,
-                                                  const uint8_t* __restrict__ colstat,
-                                                  double* __restrict__ C, int64_t ldc,
-                                                  const __grid_constant__ CrtTable ct) {
-  const int nq = (n + 3) >> 2;
+// 32-bit limbs of the signed results for N moduli (bit length of P plus a sign bit,
+// at least 4): N <= 13 -> 4, N <= 17 -> 5, N <= 20 -> 6.
+__host__ __device__ constexpr int limbs_for(int N) { return N <= 13 ? 4 : (N <= 17 ? 5 : 6); }
+
+// Thread (row i, 2 consecutive columns).  One instance per N, so the modulus loop is
+// unrolled and the N residue loads of a thread can be issued together.
+template <int N>
+__global__ void __launch_bounds__(256, 2)
+    crt_kernel(const int16_t* __restrict__ cres, int64_t ldr, int64_t rstride, int m, int n,
+               const int32_t* __restrict__ e, const int32_t* __restrict__ f,
+               const uint8_t* __restrict__ rowstat, const uint8_t* __restrict__ colstat,
+               double* __restrict__ C, int64_t ldc, const __grid_constant__ CrtTable ct) {
+  constexpr int L = limbs_for(N);
+  constexpr int L16 = 2 * L;
+  const int nq = (n + 1) >> 1;
   const int64_t total = static_cast<int64_t>(m) * nq;
   for (int64_t it = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; it < total;
        it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int i = static_cast<int>(it / nq);
-    const int j0 = static_cast<int>(it % nq) * 4;
-    int64_t acc[4][L];
-    float est[4];
-#pragma unroll
-    for (int z = 0; z < 4; ++z) {
-      est[z] = 0.0f;
-#pragma unroll
-      for (int t = 0; t < L; ++t) acc[z][t] = 0;
-    }
+    const int j0 = static_cast<int>(it % nq) * 2;
     const int16_t* src = cres + static_cast<int64_t>(i) * ldr + j0;
-    for (int l = 0; l < ct.N; ++l) {
-      const uint2 raw = *reinterpret_cast<const uint2*>(src + static_cast<int64_t>(l) * rstride);
-      const int p = ct.p[l];
-      const int cz[4] = {static_cast<int16_t>(raw.x & 0xFFFFu), static_cast<int16_t>(raw.x >> 16),
-                         static_cast<int16_t>(raw.y & 0xFFFFu), static_cast<int16_t>(raw.y >> 16)};
+    uint32_t acc[2][L16];
+    uint32_t est[2] = {0u, 0u};
 #pragma unroll
-      for (int z = 0; z < 4; ++z) {
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+      for (int t = 0; t < L16; ++t) acc[z][t] = 0u;
+#pragma unroll
+    for (int l = 0; l < N; ++l) {
+      const int p = ct.p[l];
+      const uint32_t raw = __ldg(reinterpret_cast<const unsigned int*>(src + static_cast<int64_t>(l) * rstride));
+      const int cz[2] = {static_cast<int16_t>(raw & 0xFFFFu), static_cast<int16_t>(raw >> 16)};
+#pragma unroll
+      for (int z = 0; z < 2; ++z) {
         const uint32_t u = static_cast<uint32_t>(cz[z] < 0 ? cz[z] + p : cz[z]);
 #pragma unroll
-        for (int t = 0; t < L; ++t) acc[z][t] += static_cast<int64_t>(static_cast<uint64_t>(u) * ct.w[l][t]);
-        est[z] = fmaf(static_cast<float>(u), ct.frac[l], est[z]);
+        for (int t = 0; t < L16; ++t) acc[z][t] += u * static_cast<uint32_t>(ct.w16[l][t]);
+        est[z] += u * ct.frac16[l];
       }
     }
     const int ei = e[i];
     const bool rbad = rowstat != nullptr && (rowstat[i] & kLineNonfinite);
     double* out = C + static_cast<int64_t>(i) * ldc;
 #pragma unroll
-    for (int z = 0; z < 4; ++z) {
+    for (int z = 0; z < 2; ++z) {
       const int j = j0 + z;
       if (j < n) {
+        // Q = round(est / 2^16); est / 2^16 is within 0.17 of V / P
+        const uint32_t q = (est[z] + 0x8000u) >> 16;
+        const int32_t off = static_cast<int32_t>(est[z] - (q << 16));  // in [-2^15, 2^15)
+        const bool exact_check = (off > 19660 || off < -19660);        // |est - Q| > 0.3
+        // v = V - Q P from the 16-bit-limb sums, normalised to 32-bit limbs
+        uint32_t v[L];
+        int64_t carry = 0;
+#pragma unroll
+        for (int t = 0; t < L; ++t) {
+          const int64_t lo = static_cast<int64_t>(acc[z][2 * t]) - static_cast<int64_t>(q) * ct.P16[2 * t];
+          const int64_t hi = static_cast<int64_t>(acc[z][2 * t + 1]) - static_cast<int64_t>(q) * ct.P16[2 * t + 1];
+          const int64_t x = carry + lo + hi * 65536;
+          v[t] = static_cast<uint32_t>(x);
+          carry = x >> 32;  // arithmetic: signed carry
+        }
         const bool bad = rbad || (colstat != nullptr && (colstat[j] & kLineNonfinite));
-        out[j] = crt_finish<L>(acc[z], est[z], ei + f[j], bad, ct);
+        out[j] = crt_finish<L>(v, exact_check, ei + f[j], bad, ct);
       }
     }
   }
 }
 
-template <int L>
-cudaError_t launch_L(const int16_t* cres, int64_t ldr, int64_t rs, int m, int n, const int32_t* e,
+template <int N>
+cudaError_t launch_N(const int16_t* cres, int64_t ldr, int64_t rs, int m, int n, const int32_t* e,
                      const int32_t* f, const uint8_t* rowstat, const uint8_t* colstat, double* C,
                      int64_t ldc, const CrtTable& ct, cudaStream_t st) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t threads = static_cast<int64_t>(m) * ((n + 3) / 4);
+  const int64_t threads = static_cast<int64_t>(m) * ((n + 1) / 2);
   int64_t blocks = (threads + 255) / 256;
   if (blocks > static_cast<int64_t>(sms) * 16) blocks = static_cast<int64_t>(sms) * 16;
   if (blocks < 1) blocks = 1;
-  crt_kernel<L><<<static_cast<int>(blocks), 256, 0, st>>>(cres, ldr, rs, m, n, e, f, rowstat, colstat,
-                                                         C, ldc, ct);
+  crt_kernel<N><<<static_cast<int>(blocks), 256, 0, st>>>(cres, ldr, rs, m, n, e, f, rowstat, colstat, C, ldc, ct);
   return cudaGetLastError();
 }
 
@@ -194,18 +202,17 @@ cudaError_t launch_crt(const int16_t* cres, int64_t ldr, int64_t res_stride, int
                        const int32_t* e, const int32_t* f, const uint8_t* rowstat,
                        const uint8_t* colstat, double* C, int64_t ldc, const CrtTable& ct,
                        cudaStream_t st) {
-  switch (ct.limbs) {
-    case 1:
-    case 2:
-    case 3:
-    case 4:
-      return launch_L<4>(cres, ldr, res_stride, m, n, e, f, rowstat, colstat, C, ldc, ct, st);
-    case 5:
-      return launch_L<5>(cres, ldr, res_stride, m, n, e, f, rowstat, colstat, C, ldc, ct, st);
-    case 6:
-      return launch_L<6>(cres, ldr, res_stride, m, n, e, f, rowstat, colstat, C, ldc, ct, st);
+  if (ct.limbs > limbs_for(ct.N)) return cudaErrorInvalidValue;
+  switch (ct.N) {
+#define OZK2_CASE(nn) \
+  case nn:            \
+    return launch_N<nn>(cres, ldr, res_stride, m, n, e, f, rowstat, colstat, C, ldc, ct, st);
+    OZK2_CASE(1) OZK2_CASE(2) OZK2_CASE(3) OZK2_CASE(4) OZK2_CASE(5) OZK2_CASE(6) OZK2_CASE(7)
+    OZK2_CASE(8) OZK2_CASE(9) OZK2_CASE(10) OZK2_CASE(11) OZK2_CASE(12) OZK2_CASE(13) OZK2_CASE(14)
+    OZK2_CASE(15) OZK2_CASE(16) OZK2_CASE(17) OZK2_CASE(18) OZK2_CASE(19) OZK2_CASE(20)
+#undef OZK2_CASE
     default:
-      return launch_L<7>(cres, ldr, res_stride, m, n, e, f, rowstat, colstat, C, ldc, ct, st);
+      return cudaErrorInvalidValue;
   }
 }
 

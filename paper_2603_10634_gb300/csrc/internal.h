@@ -35,18 +35,19 @@ struct ModTable {
   int plane0[kMaxModuli];         // first digit plane of the modulus
   float inv_p[kMaxModuli];        // RN(1 / p)
   float inv_s[kMaxModuli];        // RN(1 / s)
-  int w16[kMaxModuli][4];         // 2^(16 j) mod p, j = 0..3
-  int16_t pow2[kMaxModuli][kPow2Table];  // 2^t mod p
+  float w8[kMaxModuli][7];        // 2^(8 j) mod p, symmetric representative, j = 0..6
+  int16_t pow2[kMaxModuli][kPow2Table];  // 2^t mod p, symmetric representative
 };
 
 struct CrtTable {
   int N;
-  int limbs;                           // L, 32-bit limbs of the signed result
+  int limbs;                               // L, 32-bit limbs of the signed result
   int p[kMaxModuli];
-  uint32_t w[kMaxModuli][kMaxLimbs];   // q_l P / p_l mod P
-  float frac[kMaxModuli];              // w_l / P (quotient estimate)
+  uint16_t w16[kMaxModuli][2 * kMaxLimbs]; // q_l P / p_l mod P in 16-bit limbs
+  uint32_t frac16[kMaxModuli];             // round(2^16 w_l / P) (quotient estimate)
+  uint16_t P16[2 * kMaxLimbs];             // P in 16-bit limbs
   uint32_t P[kMaxLimbs];
-  uint32_t halfP[kMaxLimbs];           // P / 2 (P is even: 1024 is a modulus)
+  uint32_t halfP[kMaxLimbs];               // P / 2 (P is even: 1024 is a modulus)
 };
 
 // Host-side constant generation (moduli.cpp)
@@ -120,7 +121,8 @@ cudaError_t launch_crt(const int16_t* cres, int64_t ldr, int64_t res_stride, int
                        cudaStream_t st);
 
 // tensor maps (api.cu)
+// Boxes of box_rows x box_cols bytes (box_cols 128 or 64, swizzled to match).
 bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows,
-                    int64_t planes, int64_t row_stride_bytes, int box_rows);
+                    int64_t planes, int64_t row_stride_bytes, int box_rows, int box_cols);
 
 }  // namespace ozk2

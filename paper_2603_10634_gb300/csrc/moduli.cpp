@@ -166,10 +166,12 @@ bool build_mod_table(int N, ModTable* mt) {
     mt->plane0[l] = (l < kNumSquares) ? 2 * l : 2 * kNumSquares + 3 * (l - kNumSquares);
     mt->inv_p[l] = static_cast<float>(1.0 / p);
     mt->inv_s[l] = static_cast<float>(1.0 / mt->s[l]);
+    const int h = p / 2;
+    auto sym = [p, h](int v) { return v > p - 1 - h ? v - p : v; };  // [-h, p-1-h]
     int v = 1 % p;
     for (int t = 0; t < kPow2Table; ++t) {
-      mt->pow2[l][t] = static_cast<int16_t>(v);
-      if (t % 16 == 0 && t / 16 < 4) mt->w16[l][t / 16] = v;
+      mt->pow2[l][t] = static_cast<int16_t>(sym(v));
+      if (t % 8 == 0 && t / 8 < 7) mt->w8[l][t / 8] = static_cast<float>(sym(v));
       v = (2 * v) % p;
     }
   }
@@ -196,12 +198,19 @@ bool build_crt_table(int N, CrtTable* ct) {
     div_small(Pl, static_cast<uint32_t>(p), &rem);
     const int q = modinv(static_cast<int>(rem), p);
     const Big w = mul_small(Pl, static_cast<uint32_t>(q));  // < P, already reduced
-    for (size_t t = 0; t < w.size() && t < static_cast<size_t>(kMaxLimbs); ++t) ct->w[l][t] = w[t];
+    for (size_t t = 0; t < w.size() && t < static_cast<size_t>(kMaxLimbs); ++t) {
+      ct->w16[l][2 * t] = static_cast<uint16_t>(w[t] & 0xFFFFu);
+      ct->w16[l][2 * t + 1] = static_cast<uint16_t>(w[t] >> 16);
+    }
     int ew;
     const double wtop = w.empty() ? 0.0 : top_as_double(w, &ew);
-    ct->frac[l] = w.empty() ? 0.0f : static_cast<float>(std::ldexp(wtop / Ptop, ew - eP));
+    ct->frac16[l] = w.empty() ? 0u : static_cast<uint32_t>(std::llround(std::ldexp(wtop / Ptop, ew - eP + 16)));
   }
-  for (size_t t = 0; t < P.size(); ++t) ct->P[t] = P[t];
+  for (size_t t = 0; t < P.size(); ++t) {
+    ct->P[t] = P[t];
+    ct->P16[2 * t] = static_cast<uint16_t>(P[t] & 0xFFFFu);
+    ct->P16[2 * t + 1] = static_cast<uint16_t>(P[t] >> 16);
+  }
   uint32_t dummy;
   const Big half = div_small(P, 2u, &dummy);
   for (size_t t = 0; t < half.size(); ++t) ct->halfP[t] = half[t];

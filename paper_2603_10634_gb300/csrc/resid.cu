@@ -8,18 +8,22 @@
 //                    d3 = d1 + d2                                (Sec. III-B)
 // and each digit (|d| <= 16, exact in E4M3) is stored as an E4M3 byte in its plane.
 //
-// a' is never materialised as a wide integer or a double: with a = M 2^E (M the
-// 53-bit significand) and t = E + e, a' = M' 2^t' where M' = M >> -t, t' = 0 if t < 0
-// and M' = M, t' = t otherwise.  Then
-//   a' mod p = (sum_j c_j (2^16j mod p)) * (2^t' mod p)  mod p,
-// with c_j the 16-bit pieces of M' and 2^t' mod p read from a per-modulus table.
-// Every partial value stays below 2^28.1, where the float-estimated remainder of
-// smod_i32 is exact.
+// a' is never formed as a wide integer or a double.  With a = M 2^E (M the 53-bit
+// significand) and t = E + e: a' = M' 2^t', where M' = M >> -t, t' = 0 if t < 0 and
+// M' = M, t' = t otherwise.  M' is split once into seven signed byte pieces c_j
+// (exact floats), and for each modulus
+//   x = sum_j c_j w_j,   w_j = 2^(8j) mod p in [-p/2, p/2],   |x| < 2^20
+// is formed with exact FP32 fused multiply-adds.  For odd p the exact product x (1/p)
+// (rounded once, see reduce) is within 1.4e-4 of x / p (|x| < 2^20, p >= 443), closer
+// than any half-integer can be (1/(2p) >= 4.6e-4), so q is the nearest integer to x / p
+// and r = x - q p (one exact FMA) is the symmetric remainder with no correction step.
+// p = 1024 uses q = floor((x + 512) / 1024), exact.  No conversion instruction is used:
+// every rounding is an FP32 add of 1.5 2^23.  When t' > 0 the remainder is
+// multiplied by 2^t' mod p (|product| < 2^19) and reduced once more.
 //
 // Rows of A produce K-major planes directly.  Columns of B are written transposed
 // (plane rows are columns of B), so both operands of the tensor-core products are
-// K-major.  Each thread owns 16 elements: it decodes them once into two registers
-// each, then loops over the moduli.
+// K-major.  Each thread owns 8 elements.
 #include <cuda_fp8.h>
 
 #include "device.cuh"
@@ -29,75 +33,88 @@ namespace {
 
 constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+constexpr int kPieces = 7;
+constexpr int kElems = 8;  // elements per thread
 
-// Packed element: x = bits 0..31 of M', y = bits 32..52 of M' | t' << 21 | sign << 31.
-__device__ __forceinline__ uint2 encode_element(double a, int e, bool& range_err) {
+// Signed byte pieces of a' (as floats) and t'.
+__device__ __forceinline__ void decode_element(double a, int e, float (&c)[kPieces], int& tp, bool& range_err) {
   const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(a));
   const unsigned long long mag = bits & kAbsMask;
-  uint2 r = make_uint2(0u, 0u);
-  if (mag == 0 || mag >= kInfBits) return r;
-  const int be = static_cast<int>(mag >> 52);
-  unsigned long long M;
-  int E;
-  if (be == 0) {
-    M = mag;
-    E = -1074;
-  } else {
-    M = (mag & ((1ull << 52) - 1)) | (1ull << 52);
-    E = be - 1075;
+  unsigned long long Mp = 0;
+  tp = 0;
+  if (mag != 0 && mag < kInfBits) {
+    const int be = static_cast<int>(mag >> 52);
+    const unsigned long long M = be ? ((mag & ((1ull << 52) - 1)) | (1ull << 52)) : mag;
+    const int t = (be ? be - 1075 : -1074) + e;
+    if (t >= 0) {
+      Mp = M;
+      tp = t;
+    } else {
+      Mp = (t <= -64) ? 0ull : (M >> (-t));
+    }
+    if (tp >= kPow2Table) {
+      range_err = true;
+      Mp = 0;
+      tp = 0;
+    }
   }
-  const int t = E + e;
-  unsigned long long Mp;
-  int tp;
-  if (t >= 0) {
-    Mp = M;
-    tp = t;
-  } else {
-    Mp = (t <= -64) ? 0ull : (M >> (-t));
-    tp = 0;
+  // byte b -> float via the bit pattern of 2^23 + b (exact), sign folded into one FMA:
+  // sg (2^23 + b) - sg 2^23 = sg b
+  const uint32_t lo = static_cast<uint32_t>(Mp), hi = static_cast<uint32_t>(Mp >> 32);
+  const float sg = (bits >> 63) ? -1.0f : 1.0f;
+  const float off = -sg * 8388608.0f;
+  const uint32_t bytes[kPieces] = {lo & 0xFFu, (lo >> 8) & 0xFFu, (lo >> 16) & 0xFFu, lo >> 24,
+                                   hi & 0xFFu, (hi >> 8) & 0xFFu, hi >> 16};
+#pragma unroll
+  for (int j = 0; j < kPieces; ++j) c[j] = fmaf(sg, __uint_as_float(0x4B000000u | bytes[j]), off);
+}
+
+struct ModF {
+  float p, inv_p;
+  float w[kPieces];
+  bool pow2_modulus;  // p = 1024
+};
+
+// Rounding to an integer without a conversion instruction: for |y| < 2^22, y + 1.5 2^23
+// rounds (to nearest, ties to even) to an integer-valued float, and subtracting
+// 1.5 2^23 is exact.  fmaf(x, inv_p, kMagic) rounds the exact product x (1/p), so the
+// quotient estimate carries only the error of inv_p: |x| (1/p) 2^-24 < 1.4e-4 < 1/(2p).
+// Inputs are never -0 (the pieces c_j come out of an exact FMA as +0 when zero), so
+// no remainder or digit is -0 (E4M3 0x80).
+constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+
+__device__ __forceinline__ float reduce(float x, const ModF& m) {
+  if (m.pow2_modulus) {
+    // floor((x + 512) / 1024) = round((x + 0.5) / 1024) for integer x (never a tie);
+    // (x + 0.5) / 1024 is formed exactly by the inner FMA.
+    const float q = (fmaf(x, 0.0009765625f, 0.00048828125f) + kMagic) - kMagic;
+    return fmaf(-1024.0f, q, x);
   }
-  if (Mp == 0) return r;
-  if (tp >= kPow2Table) {
-    range_err = true;
-    return r;
-  }
-  r.x = static_cast<uint32_t>(Mp);
-  r.y = static_cast<uint32_t>(Mp >> 32) | (static_cast<uint32_t>(tp) << 21) |
-        (static_cast<uint32_t>(bits >> 63) << 31);
+  const float q = fmaf(x, m.inv_p, kMagic) - kMagic;
+  return fmaf(-m.p, q, x);
+}
+
+__device__ __forceinline__ float residue_of(const float (&c)[kPieces], int tp, const ModF& m, const int16_t* pow2,
+                                            bool use_pow2) {
+  float x = c[0];
+#pragma unroll
+  for (int j = 1; j < kPieces; ++j) x = fmaf(c[j], m.w[j], x);
+  float r = reduce(x, m);
+  if (use_pow2) r = reduce(fmaf(r, static_cast<float>(pow2[tp]), 0.0f), m);  // +0, never -0
   return r;
 }
 
-struct ModConsts {
-  int p, h, w1, w2, w3;
-  float inv_p;
-};
-
-// Symmetric residue of the signed integer a' = +-M' 2^t' encoded in v.  The sign is
-// applied before the reduction, so the result needs no correction afterwards.
-__device__ __forceinline__ int residue_of(uint2 v, const ModConsts& c, const int16_t* pow2,
-                                          bool use_pow2) {
-  const uint32_t c0 = v.x & 0xFFFFu, c1 = v.x >> 16, c2 = v.y & 0xFFFFu, c3 = (v.y >> 16) & 0x1Fu;
-  int x = static_cast<int>(c0 + c1 * static_cast<uint32_t>(c.w1) + c2 * static_cast<uint32_t>(c.w2) +
-                           c3 * static_cast<uint32_t>(c.w3));  // < 2^28.1
-  if (use_pow2) {
-    const int tp = static_cast<int>((v.y >> 21) & 63u);
-    x = smod_i32(x, c.p, c.h, c.inv_p) * static_cast<int>(pow2[tp]);  // |x| < 2^19.2
-  }
-  const int neg = -static_cast<int>(v.y >> 31);  // 0 or -1
-  x = (x ^ neg) - neg;
-  return smod_i32(x, c.p, c.h, c.inv_p);
+// Digits of a residue r (an exact float, never -0); the digits are never -0 either
+// (an exact zero from x - x or x + (-x) is +0 in round-to-nearest).
+__device__ __forceinline__ void square_digits(float r, float s, float inv_s, float& d1, float& d2) {
+  d1 = fmaf(r, inv_s, kMagic) - kMagic;  // round(r / s), ties to even (only s = 32 has ties)
+  d2 = fmaf(-s, d1, r);
 }
-
-// Digits of residue r as floats (exact small integers, never -0).
-__device__ __forceinline__ void square_digits(int r, int s, float inv_s, float& d1, float& d2) {
-  const float rf = static_cast<float>(r);
-  d1 = __fadd_rn(rintf(rf * inv_s), 0.0f);
-  d2 = fmaf(-static_cast<float>(s), d1, rf);
-}
-__device__ __forceinline__ void karatsuba_digits(int r, float& d1, float& d2, float& d3) {
-  const float rf = static_cast<float>(r);
-  d1 = copysignf(ceilf(fabsf(rf) * 0.0625f), rf);
-  d2 = fmaf(-16.0f, d1, rf);
+__device__ __forceinline__ void karatsuba_digits(float r, float& d1, float& d2, float& d3) {
+  // ceil(|r| / 16) = round((|r| + 7.5) / 16) for integer |r| (never a tie)
+  const float m1 = (fmaf(fabsf(r), 0.0625f, 0.46875f) + kMagic) - kMagic;
+  d1 = copysignf(m1, r);
+  d2 = fmaf(-16.0f, d1, r);
   d3 = d1 + d2;
 }
 
@@ -120,29 +137,62 @@ struct ResidArgs {
 
 __device__ __forceinline__ void load_table(const ModTable& mt, int16_t* pow2_s) {
   const int total = mt.N * kPow2Table;
-  for (int i = threadIdx.x; i < total; i += blockDim.x)
-    pow2_s[i] = mt.pow2[i / kPow2Table][i % kPow2Table];
+  for (int i = threadIdx.x; i < total; i += blockDim.x) pow2_s[i] = mt.pow2[i / kPow2Table][i % kPow2Table];
   __syncthreads();
 }
 
-__device__ __forceinline__ ModConsts consts_of(const ModTable& mt, int l) {
-  ModConsts c;
-  c.p = mt.p[l];
-  c.h = mt.half[l];
-  c.w1 = mt.w16[l][1];
-  c.w2 = mt.w16[l][2];
-  c.w3 = mt.w16[l][3];
-  c.inv_p = mt.inv_p[l];
-  return c;
+__device__ __forceinline__ ModF consts_of(const ModTable& mt, int l) {
+  ModF m;
+  m.p = static_cast<float>(mt.p[l]);
+  m.inv_p = mt.inv_p[l];
+#pragma unroll
+  for (int j = 0; j < kPieces; ++j) m.w[j] = mt.w8[l][j];
+  m.pow2_modulus = (mt.p[l] == 1024);
+  return m;
 }
 
-// Rows of A.  One warp covers 512 consecutive k of one row: lane l owns elements
-// base + 128 g + 4 l + {0..3}, g = 0..3, so loads and 4-byte plane stores coalesce.
-constexpr int kRowGroups = 4;
-constexpr int kRowSpan = 128 * kRowGroups;
+__host__ __device__ constexpr int plane_of(int l) {
+  return l < kNumSquares ? 2 * l : 2 * kNumSquares + 3 * (l - kNumSquares);
+}
 
-__global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a,
-                                                            const __grid_constant__ ModTable mt) {
+// Digits of the thread's 8 elements for modulus l, packed as E4M3 bytes: words[x][q]
+// holds plane x's bytes of elements 4q .. 4q+3.
+__device__ __forceinline__ void digits_of(const float (&c)[kElems][kPieces], const int (&tp)[kElems],
+                                          const ModTable& mt, int l, const int16_t* pow2_s, bool use_pow2,
+                                          uint32_t (&words)[3][2]) {
+  const ModF m = consts_of(mt, l);
+  const int16_t* pw = pow2_s + l * kPow2Table;
+  if (l < kNumSquares) {
+    const float s = static_cast<float>(mt.s[l]);
+    const float inv_s = mt.inv_s[l];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float d1[4], d2[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) square_digits(residue_of(c[4 * q + t], tp[4 * q + t], m, pw, use_pow2), s, inv_s,
+                                                d1[t], d2[t]);
+      words[0][q] = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
+      words[1][q] = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      float d1[4], d2[4], d3[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        karatsuba_digits(residue_of(c[4 * q + t], tp[4 * q + t], m, pw, use_pow2), d1[t], d2[t], d3[t]);
+      words[0][q] = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
+      words[1][q] = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
+      words[2][q] = e4m3x4(d3[0], d3[1], d3[2], d3[3]);
+    }
+  }
+}
+
+// Rows of A.  One warp covers 256 consecutive k of one row: lane l owns elements
+// base + 128 g + 4 l + {0..3}, g = 0, 1, so loads and 4-byte plane stores coalesce.
+constexpr int kRowSpan = 256;
+
+__global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
   __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
   const int lane = threadIdx.x & 31;
@@ -150,58 +200,38 @@ __global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a,
   const int nkw = (a.kp + kRowSpan - 1) / kRowSpan;
   const int64_t items = static_cast<int64_t>(a.lines) * nkw;
   bool range_err = false;
-  for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5);
-       it < items; it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
+  for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); it < items;
+       it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
     const int row = static_cast<int>(it / nkw);
     const int base = static_cast<int>(it % nkw) * kRowSpan;
     const double* x = a.X + static_cast<int64_t>(row) * a.ldx;
     const int e = a.exps[row];
-    uint2 v[4 * kRowGroups];
-    uint32_t any_tp = 0;
+    float c[kElems][kPieces];
+    int tp[kElems];
+    int any_tp = 0;
 #pragma unroll
-    for (int g = 0; g < kRowGroups; ++g) {
+    for (int g = 0; g < 2; ++g) {
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int h = base + g * 128 + lane * 4 + t;
-        const double val = (h < a.k) ? __ldg(x + h) : 0.0;
-        v[g * 4 + t] = encode_element(val, e, range_err);
-        any_tp |= v[g * 4 + t].y & (63u << 21);
+        decode_element((h < a.k) ? __ldg(x + h) : 0.0, e, c[4 * g + t], tp[4 * g + t], range_err);
+        any_tp |= tp[4 * g + t];
       }
     }
     const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
     uint8_t* rowp = a.planes + static_cast<int64_t>(row) * a.kp;
     for (int l = 0; l < mt.N; ++l) {
-      const ModConsts c = consts_of(mt, l);
-      const int16_t* pw = pow2_s + l * kPow2Table;
-      uint8_t* pl = rowp + static_cast<int64_t>(mt.plane0[l]) * a.plane_stride;
-      if (l < kNumSquares) {
-        const int s = mt.s[l];
-        const float inv_s = mt.inv_s[l];
+      uint32_t words[3][2];
+      digits_of(c, tp, mt, l, pow2_s, use_pow2, words);
+      uint8_t* pl = rowp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
+      const int nplanes = (l < kNumSquares) ? 2 : 3;
 #pragma unroll
-        for (int g = 0; g < kRowGroups; ++g) {
-          float d1[4], d2[4];
+      for (int g = 0; g < 2; ++g) {
+        const int h = base + g * 128 + lane * 4;
+        if (h < a.kp) {
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            square_digits(residue_of(v[g * 4 + t], c, pw, use_pow2), s, inv_s, d1[t], d2[t]);
-          const int h = base + g * 128 + lane * 4;
-          if (h < a.kp) {
-            *reinterpret_cast<uint32_t*>(pl + h) = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
-            *reinterpret_cast<uint32_t*>(pl + a.plane_stride + h) = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
-          }
-        }
-      } else {
-#pragma unroll
-        for (int g = 0; g < kRowGroups; ++g) {
-          float d1[4], d2[4], d3[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-            karatsuba_digits(residue_of(v[g * 4 + t], c, pw, use_pow2), d1[t], d2[t], d3[t]);
-          const int h = base + g * 128 + lane * 4;
-          if (h < a.kp) {
-            *reinterpret_cast<uint32_t*>(pl + h) = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
-            *reinterpret_cast<uint32_t*>(pl + a.plane_stride + h) = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
-            *reinterpret_cast<uint32_t*>(pl + 2 * a.plane_stride + h) = e4m3x4(d3[0], d3[1], d3[2], d3[3]);
-          }
+          for (int xp = 0; xp < 3; ++xp)
+            if (xp < nplanes) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride + h) = words[xp][g];
         }
       }
     }
@@ -209,109 +239,77 @@ __global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a,
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
-// Columns of B.  A warp covers 16 columns x 32 consecutive h: lanes 2jj and 2jj+1 take
-// column j0 + jj, rows h0..h0+15 and h0+16..h0+31.  Loads read two 128-byte row
-// segments per instruction; each lane pair writes one full 32-byte sector of row j of
-// every plane.
-__global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a,
-                                                            const __grid_constant__ ModTable mt) {
+// Columns of B.  A warp covers 8 columns x 32 consecutive h: lane 4 jj + qq takes
+// column j0 + jj, rows h0 + 8 qq .. h0 + 8 qq + 7.  Each group of four lanes writes one
+// full 32-byte sector of row j of every plane.
+__global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
   __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
   const int lane = threadIdx.x & 31;
-  const int jj = lane >> 1, half = lane & 1;
+  const int jj = lane >> 2, qq = lane & 3;
   const int warps_per_block = blockDim.x >> 5;
-  const int ncg = (a.lines + 15) / 16;  // column groups of 16
+  const int ncg = (a.lines + 7) / 8;  // column groups of 8
   const int nkb = a.kp / 32;
   const int64_t items = static_cast<int64_t>(ncg) * nkb;
   bool range_err = false;
-  for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5);
-       it < items; it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
+  for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); it < items;
+       it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
     const int hb = static_cast<int>(it / ncg);
-    const int j = static_cast<int>(it % ncg) * 16 + jj;
+    const int j = static_cast<int>(it % ncg) * 8 + jj;
     const bool active = j < a.lines;
     const int e = active ? a.exps[j] : 0;
-    const int h0 = hb * 32 + half * 16;
-    uint2 v[16];
-    uint32_t any_tp = 0;
+    const int h0 = hb * 32 + qq * 8;
+    float c[kElems][kPieces];
+    int tp[kElems];
+    int any_tp = 0;
 #pragma unroll
-    for (int t = 0; t < 16; ++t) {
+    for (int t = 0; t < kElems; ++t) {
       const int h = h0 + t;
       const double val = (active && h < a.k) ? __ldg(a.X + static_cast<int64_t>(h) * a.ldx + j) : 0.0;
-      v[t] = encode_element(val, e, range_err);
-      any_tp |= v[t].y & (63u << 21);
+      decode_element(val, e, c[t], tp[t], range_err);
+      any_tp |= tp[t];
     }
     const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
     uint8_t* colp = a.planes + static_cast<int64_t>(active ? j : 0) * a.kp + h0;
     for (int l = 0; l < mt.N; ++l) {
-      const ModConsts c = consts_of(mt, l);
-      const int16_t* pw = pow2_s + l * kPow2Table;
-      uint8_t* pl = colp + static_cast<int64_t>(mt.plane0[l]) * a.plane_stride;
-      if (l < kNumSquares) {
-        const int s = mt.s[l];
-        const float inv_s = mt.inv_s[l];
-        uint32_t w1[4], w2[4];
+      uint32_t words[3][2];
+      digits_of(c, tp, mt, l, pow2_s, use_pow2, words);
+      uint8_t* pl = colp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
+      const int nplanes = (l < kNumSquares) ? 2 : 3;
+      if (active) {
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float d1[4], d2[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-            square_digits(residue_of(v[q * 4 + t], c, pw, use_pow2), s, inv_s, d1[t], d2[t]);
-          w1[q] = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
-          w2[q] = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
-        }
-        if (active) {
-          *reinterpret_cast<uint4*>(pl) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-          *reinterpret_cast<uint4*>(pl + a.plane_stride) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-        }
-      } else {
-        uint32_t w1[4], w2[4], w3[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float d1[4], d2[4], d3[4];
-#pragma unroll
-          for (int t = 0; t < 4; ++t)
-            karatsuba_digits(residue_of(v[q * 4 + t], c, pw, use_pow2), d1[t], d2[t], d3[t]);
-          w1[q] = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
-          w2[q] = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
-          w3[q] = e4m3x4(d3[0], d3[1], d3[2], d3[3]);
-        }
-        if (active) {
-          *reinterpret_cast<uint4*>(pl) = make_uint4(w1[0], w1[1], w1[2], w1[3]);
-          *reinterpret_cast<uint4*>(pl + a.plane_stride) = make_uint4(w2[0], w2[1], w2[2], w2[3]);
-          *reinterpret_cast<uint4*>(pl + 2 * a.plane_stride) = make_uint4(w3[0], w3[1], w3[2], w3[3]);
-        }
+        for (int xp = 0; xp < 3; ++xp)
+          if (xp < nplanes) *reinterpret_cast<uint2*>(pl + xp * a.plane_stride) = make_uint2(words[xp][0], words[xp][1]);
       }
     }
   }
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
-int grid_for(int64_t work_items, int per_block) {
+int grid_for(int64_t warps) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t want = (work_items + per_block - 1) / per_block;
-  const int64_t cap = static_cast<int64_t>(sms) * 8;
+  const int64_t want = (warps + 7) / 8;
+  const int64_t cap = static_cast<int64_t>(sms) * 16;
   return static_cast<int>(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
 }  // namespace
 
-cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp,
-                                 const int32_t* e, const ModTable& mt, uint8_t* planes,
-                                 uint32_t* flags, cudaStream_t st) {
+cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp, const int32_t* e,
+                                 const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st) {
   ResidArgs a{A, lda, m, k, kp, e, planes, static_cast<int64_t>(m) * kp, flags};
   const int64_t warps = static_cast<int64_t>(m) * ((kp + kRowSpan - 1) / kRowSpan);
-  residues_rows_kernel<<<grid_for(warps, 8), 256, 0, st>>>(a, mt);
+  residues_rows_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp,
-                                 const int32_t* f, const ModTable& mt, uint8_t* planes,
-                                 uint32_t* flags, cudaStream_t st) {
+cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, const int32_t* f,
+                                 const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st) {
   ResidArgs a{B, ldb, n, k, kp, f, planes, static_cast<int64_t>(n) * kp, flags};
-  const int64_t warps = static_cast<int64_t>((n + 15) / 16) * (kp / 32);
-  residues_cols_kernel<<<grid_for(warps, 8), 256, 0, st>>>(a, mt);
+  const int64_t warps = static_cast<int64_t>((n + 7) / 8) * (kp / 32);
+  residues_cols_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
 
