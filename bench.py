@@ -51,13 +51,17 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--samples", type=int, default=32, help="entries checked against the exact product")
+    ap.add_argument("--mode", default="accurate", choices=["accurate", "fast"], help="scaling mode")
+    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd"],
+                    help="dgemm: the square product above; autograd: forward + backward of "
+                         "C = A B with A 8192 x 4096, B 4096 x 4096 and upstream gradient W ~ N(0, 1)")
     return ap.parse_args()
 
 
 def workload_config(a):
     return {
-        "workload": f"square DGEMM m=n=k={a.size}, phi={a.phi}, N={a.moduli} moduli, accurate mode",
-        "m": a.size, "n": a.size, "k": a.size, "phi": a.phi, "num_moduli": a.moduli, "seed": 0,
+        "workload": f"square DGEMM m=n=k={a.size}, phi={a.phi}, N={a.moduli} moduli, {a.mode} mode",
+        "m": a.size, "n": a.size, "k": a.size, "phi": a.phi, "num_moduli": a.moduli, "seed": 0, "mode": a.mode,
         "l2": "inputs larger than L2 (2 x 8 k^2 bytes), no flush",
         "parallelism": f"replicas x{a.gpus}" if a.gpus > 1 else "single GPU",
     }
@@ -314,7 +318,7 @@ def run_ours(a, rank, world):
     stream = torch.cuda.current_stream(dev)
 
     for _ in range(a.warmup):
-        ozk.dgemm(A, B, num_moduli=N, out=C)
+        ozk.dgemm(A, B, num_moduli=N, out=C, mode=a.mode)
     torch.cuda.synchronize(dev)
     assert ozk.device_status() == "OZK2_OK"
     launches_per_call = ozk.last_launch_count()
@@ -328,7 +332,7 @@ def run_ours(a, rank, world):
     with ClockSampler(local) as clk:
         start.record(stream)
         for _ in range(a.steps):
-            ozk.dgemm(A, B, num_moduli=N, out=C)
+            ozk.dgemm(A, B, num_moduli=N, out=C, mode=a.mode)
             ph = ozk.get_timing()  # waits for this call's last event (host-side, ~us)
             for p in ozk.PHASES:
                 phase_sum[p] += ph[p]
@@ -345,7 +349,7 @@ def run_ours(a, rank, world):
     # ---- roofline of the dominant kernel (the residue-product GEMM)
     peaks, src = measured_peaks()
     fp8_peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
-    gemm_flops = 3 * N * flops
+    gemm_flops = 3 * N * flops  # residue products only; the bound product is its own phase
     achieved = gemm_flops / (phases["residue_gemm"] * 1e-3) / 1e12
     traffic = recorded_traffic(a.size, N)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
@@ -383,7 +387,7 @@ def run_ours(a, rank, world):
         def e2e_step():
             dA.copy_(hA, non_blocking=True)
             dB.copy_(hB, non_blocking=True)
-            ozk.dgemm(dA, dB, num_moduli=N, out=C)
+            ozk.dgemm(dA, dB, num_moduli=N, out=C, mode=a.mode)
             hC.copy_(C, non_blocking=True)
 
         e2e_step()
@@ -418,11 +422,68 @@ def run_ours(a, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_autograd(a, rank, world):
+    """Forward + backward of the differentiable product: C = A B, then dA = W B^T and
+    dB = A^T W for the upstream gradient W; three emulated products per step."""
+    import torch
+
+    import paper_2603_10634_gb300 as ozk
+    from paper_2603_10634_gb300 import _lib, workloads
+
+    _lib.load()
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, k, n, N = 8192, 4096, 4096, a.moduli
+    A = workloads.phi_matrix(m, k, a.phi, 0, device=dev).requires_grad_(True)
+    B = workloads.phi_matrix(k, n, a.phi, 1, device=dev).requires_grad_(True)
+    W = workloads.normal_matrix(m, n, 2, device=dev)
+    flops = 3 * 2.0 * m * n * k
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        A.grad = None
+        B.grad = None
+        ozk.matmul(A, B, N, a.mode).backward(W)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    launches = 0
+    for _ in range(1):
+        step()
+        launches = 3 * ozk.last_launch_count()  # the three products launch alike
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        start.record(stream)
+        for _ in range(a.steps):
+            step()
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    ms = max_over_ranks(start.elapsed_time(end) / a.steps, world, dev)
+    if rank == 0:
+        line = {
+            "metric": "emulated FP64 forward+backward TFLOP/s (3 x 2mnk / t)", "value": world * flops / ms / 1e9,
+            "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f8e4m3", "emulates": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"autograd A {m}x{k} @ B {k}x{n}, W ~ N(0,1), phi={a.phi}, N={N}, {a.mode} mode",
+                       "l2": "operands larger than L2, no flush"},
+            "gpu_launches": launches * a.steps, "clocks": clk.summary(), "device_status": ozk.device_status(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     rank, world = dist_init(a)
     if a.impl == "reference":
         run_reference(a, rank, world)
+    elif a.workload == "autograd":
+        run_autograd(a, rank, world)
     else:
         run_ours(a, rank, world)
     if world > 1:

@@ -115,6 +115,42 @@ ozk2_status ozk2_dgemm_noalloc(int64_t m, int64_t n, int64_t k,
                                double *C, int64_t ldc,
                                int num_moduli, ozk2_stream_t stream);
 
+/* Operand form and scaling mode of ozk2_dgemm_ex. */
+typedef enum { OZK2_OP_N = 0, OZK2_OP_T = 1 } ozk2_op;
+typedef enum {
+  OZK2_MODE_ACCURATE = 0, /* bound from an FP8 product of |A| and |B| (Sec. III-E); 3N + 1
+                             FP8 products                                              */
+  OZK2_MODE_FAST = 1      /* Cauchy-Schwarz bound from row / column norms (Sec. III-E,
+                             "fast mode"); 3N FP8 products, a few bits less accuracy     */
+} ozk2_mode;
+
+/*
+ * ozk2_dgemm_ex - C := op(A) * op(B) with the choices ozk2_dgemm fixes left open.
+ *
+ * op(A) is m x k: A itself (transa = OZK2_OP_N, A is m x k, lda >= max(1, k)) or A^T
+ * (OZK2_OP_T, A is stored k x m, lda >= max(1, m)); op(B) is k x n: B (OZK2_OP_N, ldb >=
+ * max(1, n)) or B^T (OZK2_OP_T, B stored n x k, ldb >= max(1, k)).  Row-major storage.
+ * mode selects the scaling of Sec. III-E (accurate or fast).  block_m, block_n > 0 run the
+ * product as independent emulations of block_m x block_n blocks of C with k unblocked
+ * (the m/n blocking of Sec. IV-C), each with its own scaling, so the workspace is that of
+ * one block; 0 means no blocking.  workspace (device, 256-byte aligned, at least
+ * ozk2_workspace_size_ex bytes) or NULL for the library-owned workspace.
+ */
+ozk2_status ozk2_dgemm_ex(ozk2_op transa, ozk2_op transb,
+                          int64_t m, int64_t n, int64_t k,
+                          const double *A, int64_t lda,
+                          const double *B, int64_t ldb,
+                          double *C, int64_t ldc,
+                          int num_moduli, ozk2_mode mode,
+                          int64_t block_m, int64_t block_n,
+                          void *workspace, size_t workspace_bytes,
+                          ozk2_stream_t stream);
+
+/* ozk2_workspace_size_ex - workspace bytes of one ozk2_dgemm_ex call with these sizes,
+ * mode and blocking (the transposes do not change it); 0 on invalid arguments. */
+size_t ozk2_workspace_size_ex(int64_t m, int64_t n, int64_t k, int num_moduli,
+                              ozk2_mode mode, int64_t block_m, int64_t block_n);
+
 /* ozk2_status_string - a static, human-readable name for a status code. */
 const char *ozk2_status_string(ozk2_status status);
 
@@ -181,6 +217,20 @@ ozk2_status ozk2_debug_scales(int64_t m, int64_t n, int64_t k,
                               int32_t *e, int32_t *f, int32_t *eprime, int32_t *fprime,
                               float *R, float *S, uint8_t *Abar, uint8_t *BbarT,
                               ozk2_stream_t stream);
+
+/*
+ * ozk2_debug_scales_ex - ozk2_debug_scales for op(A), op(B) and either scaling mode.
+ * In fast mode R and S receive the round-up sums of squares of the scaled rows of op(A)
+ * and columns of op(B) (the Cauchy-Schwarz bound that replaces the row / column maxima
+ * of Cbar), and Abar, BbarT are not produced.
+ */
+ozk2_status ozk2_debug_scales_ex(ozk2_op transa, ozk2_op transb,
+                                 int64_t m, int64_t n, int64_t k,
+                                 const double *A, int64_t lda,
+                                 const double *B, int64_t ldb, int num_moduli, ozk2_mode mode,
+                                 int32_t *e, int32_t *f, int32_t *eprime, int32_t *fprime,
+                                 float *R, float *S, uint8_t *Abar, uint8_t *BbarT,
+                                 ozk2_stream_t stream);
 
 /*
  * ozk2_debug_residue_planes - FP8 digit planes of A' = trunc(diag(2^e) A) and

@@ -45,6 +45,10 @@ Readings taken where the paper is silent or ambiguous:
       in a row of A or a column of B holding one is NaN.
   R11 The final value is RN-even of the exact rational C' 2^-(e_i+f_j), with
       gradual underflow and overflow to +-inf.
+  R15 Fast mode (Sec. III-E gives no formula): the bound of a row is the FP32 round-up
+      of sum_h RU_fp32(2^e' |a_ih|)^2, an upper bound of ||2^e' a_i||^2, and the
+      exponent rule of Eq. mu-computation is applied to it in place of max_j cbar_ij;
+      then 2 mu_i nu_j ||a_i|| ||b_j|| <= P - 1 as in accurate mode.
 """
 
 from __future__ import annotations
@@ -397,23 +401,50 @@ def final_exponent(eprime, rmax, pprime, delta, row_is_zero):
     return int(eprime) + math.floor(float(t2))
 
 
-def scaling_exponents(A, B, N, moduli=None):
-    """Accurate-mode exponents (e for the rows of A, f for the columns of B) and the
-    intermediate quantities [Sec. III-E, steps 1-3 of the workflow in Sec. IV-B]."""
+def sum_of_squares_bound(X, eprime):
+    """Fast-mode line norms (reading R15): s_i = RU_fp32(sum_h v_ih^2) with
+    v_ih = RU_fp32(2^e'_i |x_ih|), computed exactly (v^2 as an exact rational, the sum in
+    Python integers) and rounded up once.  ||2^e'_i x_i||_2^2 <= s_i."""
+    m, k = X.shape
+    out = np.zeros(m, dtype=np.float32)
+    for i in range(m):
+        sc = Fraction(2) ** int(eprime[i])
+        total = Fraction(0)
+        for h in range(k):
+            a = float(X[i, h])
+            if a == 0.0 or not math.isfinite(a):
+                continue
+            v = Fraction(float(f32_round_up(Fraction(abs(a)) * sc)))
+            total += v * v
+        out[i] = f32_round_up(total) if total else np.float32(0.0)
+    return out
+
+
+def scaling_exponents(A, B, N, moduli=None, mode="accurate"):
+    """Exponents (e for the rows of A, f for the columns of B) and the intermediate
+    quantities.  accurate: the FP8 bound product of Sec. III-E (workflow steps 1-3 of
+    Sec. IV-B).  fast: the Cauchy-Schwarz bound of Sec. III-E, 2 sum |a'||b'| <=
+    2 mu nu ||a_i|| ||b_j||, with the same exponent rule applied to the squared norms
+    (reading R15)."""
     moduli = hybrid_moduli(N) if moduli is None else moduli
     k = A.shape[1]
     Af = np.where(np.isfinite(A), A, 0.0)
     Bf = np.where(np.isfinite(B), B, 0.0)
     ep = prelim_exponent_rows(Af)
     fp = prelim_exponent_rows(Bf.T)
-    Abar = bound_operand(Af, ep)
-    Bbar = bound_operand(Bf.T, fp).T  # k x n
-    cbar = bound_product(Abar, Bbar, k)
     pprime = p_prime_constant(moduli)
     delta = delta_constant()
     m, n = A.shape[0], B.shape[1]
-    R = cbar.max(axis=1) if n else np.zeros(m, np.float32)
-    S = cbar.max(axis=0) if m else np.zeros(n, np.float32)
+    if mode == "fast":
+        Abar = Bbar = cbar = None
+        R = sum_of_squares_bound(Af, ep)
+        S = sum_of_squares_bound(Bf.T, fp)
+    else:
+        Abar = bound_operand(Af, ep)
+        Bbar = bound_operand(Bf.T, fp).T  # k x n
+        cbar = bound_product(Abar, Bbar, k)
+        R = cbar.max(axis=1) if n else np.zeros(m, np.float32)
+        S = cbar.max(axis=0) if m else np.zeros(n, np.float32)
     zero_row = ~np.any(Af != 0, axis=1)
     zero_col = ~np.any(Bf != 0, axis=0)
     e = np.array([final_exponent(ep[i], R[i], pprime, delta, zero_row[i]) for i in range(m)],
@@ -575,7 +606,7 @@ def nonfinite_masks(A, B):
     return ~np.all(np.isfinite(A), axis=1), ~np.all(np.isfinite(B), axis=0)
 
 
-def ozk2_dgemm(A, B, N, e=None, f=None, keep=False):
+def ozk2_dgemm(A, B, N, e=None, f=None, keep=False, mode="accurate"):
     """Emulated C = A B with N hybrid moduli in accurate mode.
 
     A is m x k, B is k x n (float64).  ``e``/``f`` inject row/column exponents (for
@@ -590,7 +621,7 @@ def ozk2_dgemm(A, B, N, e=None, f=None, keep=False):
     moduli = hybrid_moduli(N)
     out = {"moduli": moduli}
     if e is None or f is None:
-        sc = scaling_exponents(A, B, N, moduli)
+        sc = scaling_exponents(A, B, N, moduli, mode=mode)
         e = sc["e"] if e is None else e
         f = sc["f"] if f is None else f
         if keep:

@@ -4,7 +4,10 @@ FP8 E4M3 digits, arXiv:2603.10634).
 The compute path is libozk2.so (hand-written sm_103a CUDA behind the C ABI of
 include/ozk2.h); this package is its thin binding.
 """
+from ._lib import Ozk2Error  # noqa: F401
+from .autograd import OzakiMatmul, matmul  # noqa: F401
 from .ozk2 import (  # noqa: F401
+    MODES,
     PHASES,
     crt,
     device_status,

@@ -92,18 +92,38 @@ const Tables* tables_for(int N) {
   return &t;
 }
 
+// ------------------------------------------------------------------ operands
+// The lines of an operand are the rows of op(A) (m of them) or the columns of op(B)
+// (n of them); each line has k elements.  A line is contiguous along k for A and for
+// B^T, strided (by ld) for B and for A^T.
+struct Operand {
+  const double* ptr;
+  int64_t ld;
+  bool kcontig;
+};
+
+Operand operand_a(ozk2_op transa, const double* A, int64_t lda) { return Operand{A, lda, transa == OZK2_OP_N}; }
+Operand operand_b(ozk2_op transb, const double* B, int64_t ldb) { return Operand{B, ldb, transb == OZK2_OP_T}; }
+
+// Sub-operand of lines [first, ...).
+Operand shift_lines(const Operand& o, int64_t first) {
+  Operand r = o;
+  r.ptr = o.kcontig ? o.ptr + first * o.ld : o.ptr + first;
+  return r;
+}
+
 // ------------------------------------------------------------------ workspace layout
 struct Layout {
   int64_t kp, ldr;
   int planes;
-  size_t flags, R, S, colmax, colbad, zero_end;
+  size_t flags, R, S, colmaxA, colbadA, colmaxB, colbadB, zero_end;
   size_t eprime, fprime, e, f, rowstat, colstat;
-  size_t Abar, BbarT, planesA, planesB, cres, scratch, total;
+  size_t Abar, BbarT, partA, partB, planesA, planesB, cres, scratch, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-Layout make_layout(int64_t m, int64_t n, int64_t k, int N) {
+Layout make_layout(int64_t m, int64_t n, int64_t k, int N, bool fast) {
   Layout L;
   L.kp = ((k + 31) / 32) * 32;
   L.ldr = ((n + 7) / 8) * 8;
@@ -117,8 +137,10 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N) {
   L.flags = take(256);
   L.R = take(4 * size_t(m));
   L.S = take(4 * size_t(n));
-  L.colmax = take(8 * size_t(n));
-  L.colbad = take(4 * size_t(n));
+  L.colmaxA = take(8 * size_t(m));
+  L.colbadA = take(4 * size_t(m));
+  L.colmaxB = take(8 * size_t(n));
+  L.colbadB = take(4 * size_t(n));
   L.zero_end = o;
   L.eprime = take(4 * size_t(m));
   L.fprime = take(4 * size_t(n));
@@ -126,8 +148,10 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N) {
   L.f = take(4 * size_t(n));
   L.rowstat = take(size_t(m));
   L.colstat = take(size_t(n));
-  L.Abar = take(size_t(m) * L.kp);
-  L.BbarT = take(size_t(n) * L.kp);
+  L.Abar = fast ? o : take(size_t(m) * L.kp);
+  L.BbarT = fast ? o : take(size_t(n) * L.kp);
+  L.partA = fast ? take(4 * size_t(m) * (L.kp / 32)) : o;
+  L.partB = fast ? take(4 * size_t(n) * (L.kp / 32)) : o;
   L.planesA = take(size_t(L.planes) * m * L.kp);
   L.planesB = take(size_t(L.planes) * n * L.kp);
   L.cres = take(2 * size_t(N) * m * L.ldr);
@@ -138,6 +162,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N) {
 
 struct Ctx {
   int m, n, k, N;
+  bool fast;
   Layout L;
   uint8_t* ws;
   const Tables* tab;
@@ -211,29 +236,54 @@ void mark(Ctx& c, int idx) {
   } while (0)
 
 // ------------------------------------------------------------------ phases
-ozk2_status phase_scales(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb) {
+// e'/status and either the E4M3 bound operand (accurate) or the sums of squares (fast)
+// of one operand.
+ozk2_status scale_operand(Ctx& c, const Operand& op, int lines, size_t eprime, size_t stat, size_t bar, size_t sq,
+                          size_t part, size_t colmax, size_t colbad) {
   const Layout& L = c.L;
-  OZK2_TRY(cudaMemsetAsync(c.ws, 0, L.zero_end, c.st));
-  OZK2_TRY(launch_scale_rows(A, lda, c.m, c.k, int(L.kp), c.at<int32_t>(L.eprime), c.at<uint8_t>(L.rowstat),
-                             c.at<uint8_t>(L.Abar), c.at<uint32_t>(L.flags), c.st));
-  OZK2_TRY(launch_colmax(B, ldb, c.k, c.n, c.at<unsigned long long>(L.colmax), c.at<uint32_t>(L.colbad), c.st));
-  OZK2_TRY(launch_scale_cols(B, ldb, c.k, c.n, int(L.kp), c.at<unsigned long long>(L.colmax),
-                             c.at<uint32_t>(L.colbad), c.at<int32_t>(L.fprime), c.at<uint8_t>(L.colstat),
-                             c.at<uint8_t>(L.BbarT), c.at<uint32_t>(L.flags), c.st));
-  t_launches += 3;
+  if (op.kcontig) {
+    OZK2_TRY(launch_scale_rows(op.ptr, op.ld, lines, c.k, int(L.kp), c.at<int32_t>(eprime), c.at<uint8_t>(stat),
+                               c.at<uint8_t>(bar), c.at<float>(sq), c.fast, c.at<uint32_t>(L.flags), c.st));
+    t_launches += 1;
+  } else {
+    OZK2_TRY(launch_colmax(op.ptr, op.ld, c.k, lines, c.at<unsigned long long>(colmax), c.at<uint32_t>(colbad), c.st));
+    OZK2_TRY(launch_scale_cols(op.ptr, op.ld, c.k, lines, int(L.kp), c.at<unsigned long long>(colmax),
+                               c.at<uint32_t>(colbad), c.at<int32_t>(eprime), c.at<uint8_t>(stat),
+                               c.at<uint8_t>(bar), c.at<float>(part), c.at<float>(sq), c.fast,
+                               c.at<uint32_t>(L.flags), c.st));
+    t_launches += c.fast ? 3 : 2;
+  }
+  return OZK2_OK;
+}
+
+// clear_flags: start a new flag word (the first block of a call); later blocks of a
+// blocked call keep what earlier blocks recorded.
+ozk2_status phase_scales(Ctx& c, const Operand& a, const Operand& b, bool clear_flags) {
+  const Layout& L = c.L;
+  ozk2_status s;
+  if (clear_flags)
+    OZK2_TRY(cudaMemsetAsync(c.ws, 0, L.zero_end, c.st));
+  else
+    OZK2_TRY(cudaMemsetAsync(c.ws + L.R, 0, L.zero_end - L.R, c.st));
+  if ((s = scale_operand(c, a, c.m, L.eprime, L.rowstat, L.Abar, L.R, L.partA, L.colmaxA, L.colbadA)) != OZK2_OK)
+    return s;
+  if ((s = scale_operand(c, b, c.n, L.fprime, L.colstat, L.BbarT, L.S, L.partB, L.colmaxB, L.colbadB)) != OZK2_OK)
+    return s;
   mark(c, 1);
-  GemmArgs g{};
-  g.mode = kModeBound;
-  g.m = c.m;
-  g.n = c.n;
-  g.k = c.k;
-  g.num_sms = c.num_sms;
-  g.factor = bound_factor_f32(c.k);
-  g.R = c.at<float>(L.R);
-  g.S = c.at<float>(L.S);
-  g.flags = c.at<uint32_t>(L.flags);
-  OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.Abar), L.kp, 1, c.at<uint8_t>(L.BbarT), L.kp, 1, c.st));
-  t_launches += 1;
+  if (!c.fast) {
+    GemmArgs g{};
+    g.mode = kModeBound;
+    g.m = c.m;
+    g.n = c.n;
+    g.k = c.k;
+    g.num_sms = c.num_sms;
+    g.factor = bound_factor_f32(c.k);
+    g.R = c.at<float>(L.R);
+    g.S = c.at<float>(L.S);
+    g.flags = c.at<uint32_t>(L.flags);
+    OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.Abar), L.kp, 1, c.at<uint8_t>(L.BbarT), L.kp, 1, c.st));
+    t_launches += 1;
+  }
   mark(c, 2);
   OZK2_TRY(launch_exponents(c.m, c.n, c.at<int32_t>(L.eprime), c.at<int32_t>(L.fprime), c.at<uint8_t>(L.rowstat),
                             c.at<uint8_t>(L.colstat), c.at<float>(L.R), c.at<float>(L.S), c.tab->pprime,
@@ -243,11 +293,18 @@ ozk2_status phase_scales(Ctx& c, const double* A, int64_t lda, const double* B, 
   return OZK2_OK;
 }
 
-ozk2_status phase_residues(Ctx& c, const double* A, int64_t lda, const double* B, int64_t ldb,
-                           const int32_t* e, const int32_t* f, uint8_t* planesA, uint8_t* planesB) {
-  const Layout& L = c.L;
-  OZK2_TRY(launch_residues_rows(A, lda, c.m, c.k, int(L.kp), e, c.tab->mt, planesA, c.at<uint32_t>(L.flags), c.st));
-  OZK2_TRY(launch_residues_cols(B, ldb, c.k, c.n, int(L.kp), f, c.tab->mt, planesB, c.at<uint32_t>(L.flags), c.st));
+cudaError_t residues_operand(Ctx& c, const Operand& op, int lines, const int32_t* ex, uint8_t* planes) {
+  if (op.kcontig)
+    return launch_residues_rows(op.ptr, op.ld, lines, c.k, int(c.L.kp), ex, c.tab->mt, planes,
+                                c.at<uint32_t>(c.L.flags), c.st);
+  return launch_residues_cols(op.ptr, op.ld, c.k, lines, int(c.L.kp), ex, c.tab->mt, planes,
+                              c.at<uint32_t>(c.L.flags), c.st);
+}
+
+ozk2_status phase_residues(Ctx& c, const Operand& a, const Operand& b, const int32_t* e, const int32_t* f,
+                           uint8_t* planesA, uint8_t* planesB) {
+  OZK2_TRY(residues_operand(c, a, c.m, e, planesA));
+  OZK2_TRY(residues_operand(c, b, c.n, f, planesB));
   t_launches += 2;
   mark(c, 4);
   return OZK2_OK;
@@ -290,28 +347,43 @@ ozk2_status check_sizes(int64_t m, int64_t n, int64_t k, int N) {
   return OZK2_OK;
 }
 
-ozk2_status validate(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                     int64_t ldb, const double* C, int64_t ldc, int N) {
+bool valid_op(int op) { return op == OZK2_OP_N || op == OZK2_OP_T; }
+bool valid_mode(int mode) { return mode == OZK2_MODE_ACCURATE || mode == OZK2_MODE_FAST; }
+
+ozk2_status validate(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                     const double* B, int64_t ldb, const double* C, int64_t ldc, int N) {
   ozk2_status s = check_sizes(m, n, k, N);
   if (s != OZK2_OK) return s;
-  if (lda < std::max<int64_t>(1, k) || ldb < std::max<int64_t>(1, n) || ldc < std::max<int64_t>(1, n))
+  if (!valid_op(transa) || !valid_op(transb)) return OZK2_ERR_INVALID_VALUE;
+  const int64_t min_lda = transa == OZK2_OP_N ? k : m;
+  const int64_t min_ldb = transb == OZK2_OP_N ? n : k;
+  if (lda < std::max<int64_t>(1, min_lda) || ldb < std::max<int64_t>(1, min_ldb) || ldc < std::max<int64_t>(1, n))
     return OZK2_ERR_INVALID_VALUE;
   if (m == 0 || n == 0) return OZK2_OK;  // nothing is read or written
   if (!C || (k > 0 && (!A || !B))) return OZK2_ERR_INVALID_VALUE;
   return OZK2_OK;
 }
 
-ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, void* ws, size_t ws_bytes, cudaStream_t st) {
+// validate() for the scaling hook, which writes no C.
+ozk2_status validate_operands(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
+                              int64_t lda, const double* B, int64_t ldb, int N) {
+  static double dummy;
+  return validate(transa, transb, m, n, k, A, lda, B, ldb, &dummy, std::max<int64_t>(1, n), N);
+}
+
+ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, bool fast, void* ws, size_t ws_bytes,
+                  cudaStream_t st) {
   c.m = int(m);
   c.n = int(n);
   c.k = int(k);
   c.N = N;
+  c.fast = fast;
   c.st = st;
   if (!device_info(&c.num_sms)) return OZK2_ERR_UNSUPPORTED;
   if (!encode_fn()) return OZK2_ERR_CUDA;
   c.tab = tables_for(N);
   if (!c.tab) return OZK2_ERR_INTERNAL;
-  c.L = make_layout(m, n, k, N);
+  c.L = make_layout(m, n, k, N, fast);
   if (ws) {
     if (ws_bytes < c.L.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) return OZK2_ERR_INVALID_VALUE;
     c.ws = static_cast<uint8_t*>(ws);
@@ -323,28 +395,55 @@ ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, void* ws, size
   return OZK2_OK;
 }
 
-ozk2_status dgemm_impl(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-                       double* C, int64_t ldc, int N, void* ws, size_t ws_bytes, cudaStream_t st) {
+// One emulated product over whole operands (no blocking); arguments already validated,
+// m, n, k > 0.
+ozk2_status run_one(const Operand& a, const Operand& b, int64_t m, int64_t n, int64_t k, double* C, int64_t ldc,
+                    int N, bool fast, bool first, void* ws, size_t ws_bytes, cudaStream_t st) {
+  Ctx c;
+  ozk2_status s = setup(c, m, n, k, N, fast, ws, ws_bytes, st);
+  if (s != OZK2_OK) return s;
+  mark(c, 0);
+  const Layout& L = c.L;
+  if ((s = phase_scales(c, a, b, first)) != OZK2_OK) return s;
+  if ((s = phase_residues(c, a, b, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesA),
+                          c.at<uint8_t>(L.planesB))) != OZK2_OK)
+    return s;
+  if ((s = phase_products(c)) != OZK2_OK) return s;
+  return phase_crt(c, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.rowstat), c.at<uint8_t>(L.colstat), C,
+                   ldc);
+}
+
+int64_t block_or_all(int64_t b, int64_t total) { return (b <= 0 || b >= total) ? total : b; }
+
+size_t workspace_bytes(int64_t m, int64_t n, int64_t k, int N, bool fast, int64_t bm, int64_t bn) {
+  return make_layout(block_or_all(bm, m), block_or_all(bn, n), k, N, fast).total;
+}
+
+ozk2_status dgemm_general(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
+                          int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int N, int mode,
+                          int64_t block_m, int64_t block_n, void* ws, size_t ws_bytes, cudaStream_t st) {
   t_launches = 0;
-  ozk2_status s = validate(m, n, k, A, lda, B, ldb, C, ldc, N);
+  if (!valid_mode(mode) || block_m < 0 || block_n < 0) return OZK2_ERR_INVALID_VALUE;
+  ozk2_status s = validate(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, N);
   if (s != OZK2_OK) return s;
   if (m == 0 || n == 0) return OZK2_OK;
   if (k == 0) {
     OZK2_TRY(cudaMemset2DAsync(C, size_t(ldc) * 8, 0, size_t(n) * 8, size_t(m), st));
     return OZK2_OK;
   }
-  Ctx c;
-  s = setup(c, m, n, k, N, ws, ws_bytes, st);
-  if (s != OZK2_OK) return s;
-  mark(c, 0);
-  const Layout& L = c.L;
-  if ((s = phase_scales(c, A, lda, B, ldb)) != OZK2_OK) return s;
-  if ((s = phase_residues(c, A, lda, B, ldb, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesA),
-                          c.at<uint8_t>(L.planesB))) != OZK2_OK)
-    return s;
-  if ((s = phase_products(c)) != OZK2_OK) return s;
-  return phase_crt(c, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.rowstat), c.at<uint8_t>(L.colstat), C,
-                   ldc);
+  const bool fast = mode == OZK2_MODE_FAST;
+  const Operand a = operand_a(transa, A, lda);
+  const Operand b = operand_b(transb, B, ldb);
+  const int64_t bm = block_or_all(block_m, m), bn = block_or_all(block_n, n);
+  for (int64_t i0 = 0; i0 < m; i0 += bm) {
+    for (int64_t j0 = 0; j0 < n; j0 += bn) {
+      const int64_t mm = std::min(bm, m - i0), nn = std::min(bn, n - j0);
+      s = run_one(shift_lines(a, i0), shift_lines(b, j0), mm, nn, k, C + i0 * ldc + j0, ldc, N, fast,
+                  i0 == 0 && j0 == 0, ws, ws_bytes, st);
+      if (s != OZK2_OK) return s;
+    }
+  }
+  return OZK2_OK;
 }
 
 }  // namespace
@@ -371,20 +470,35 @@ extern "C" {
 
 ozk2_status ozk2_dgemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
                        double* C, int64_t ldc, int num_moduli, ozk2_stream_t stream) {
-  return dgemm_impl(m, n, k, A, lda, B, ldb, C, ldc, num_moduli, nullptr, 0, reinterpret_cast<cudaStream_t>(stream));
+  return dgemm_general(OZK2_OP_N, OZK2_OP_N, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, OZK2_MODE_ACCURATE, 0, 0,
+                       nullptr, 0, reinterpret_cast<cudaStream_t>(stream));
 }
 
 ozk2_status ozk2_dgemm_ws(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
                           double* C, int64_t ldc, int num_moduli, void* workspace, size_t workspace_bytes,
                           ozk2_stream_t stream) {
   if (!workspace) return OZK2_ERR_INVALID_VALUE;
-  return dgemm_impl(m, n, k, A, lda, B, ldb, C, ldc, num_moduli, workspace, workspace_bytes,
-                    reinterpret_cast<cudaStream_t>(stream));
+  return dgemm_general(OZK2_OP_N, OZK2_OP_N, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, OZK2_MODE_ACCURATE, 0, 0,
+                       workspace, workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ozk2_status ozk2_dgemm_ex(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
+                          int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int num_moduli,
+                          ozk2_mode mode, int64_t block_m, int64_t block_n, void* workspace, size_t workspace_bytes,
+                          ozk2_stream_t stream) {
+  return dgemm_general(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode, block_m, block_n, workspace,
+                       workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 size_t ozk2_workspace_size(int64_t m, int64_t n, int64_t k, int num_moduli) {
   if (check_sizes(m, n, k, num_moduli) != OZK2_OK) return 0;
-  return make_layout(m, n, k, num_moduli).total;
+  return workspace_bytes(m, n, k, num_moduli, false, 0, 0);
+}
+
+size_t ozk2_workspace_size_ex(int64_t m, int64_t n, int64_t k, int num_moduli, ozk2_mode mode, int64_t block_m,
+                              int64_t block_n) {
+  if (check_sizes(m, n, k, num_moduli) != OZK2_OK || !valid_mode(mode) || block_m < 0 || block_n < 0) return 0;
+  return workspace_bytes(m, n, k, num_moduli, mode == OZK2_MODE_FAST, block_m, block_n);
 }
 
 const char* ozk2_status_string(ozk2_status s) {
@@ -479,16 +593,19 @@ ozk2_status ozk2_debug_fp8_gemm(int64_t m, int64_t n, int64_t k, const uint8_t* 
   return OZK2_OK;
 }
 
-ozk2_status ozk2_debug_scales(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                              int64_t ldb, int num_moduli, int32_t* e, int32_t* f, int32_t* eprime, int32_t* fprime,
-                              float* R, float* S, uint8_t* Abar, uint8_t* BbarT, ozk2_stream_t stream) {
+ozk2_status ozk2_debug_scales_ex(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
+                                 int64_t lda, const double* B, int64_t ldb, int num_moduli, ozk2_mode mode,
+                                 int32_t* e, int32_t* f, int32_t* eprime, int32_t* fprime, float* R, float* S,
+                                 uint8_t* Abar, uint8_t* BbarT, ozk2_stream_t stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  ozk2_status s = check_sizes(m, n, k, num_moduli);
+  if (!valid_mode(mode)) return OZK2_ERR_INVALID_VALUE;
+  ozk2_status s = validate_operands(transa, transb, m, n, k, A, lda, B, ldb, num_moduli);
   if (s != OZK2_OK) return s;
-  if (m == 0 || n == 0 || k == 0 || !A || !B || lda < k || ldb < n) return OZK2_ERR_INVALID_VALUE;
+  if (m == 0 || n == 0 || k == 0 || !A || !B) return OZK2_ERR_INVALID_VALUE;
+  const bool fast = mode == OZK2_MODE_FAST;
   Ctx c;
-  if ((s = setup(c, m, n, k, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
-  if ((s = phase_scales(c, A, lda, B, ldb)) != OZK2_OK) return s;
+  if ((s = setup(c, m, n, k, num_moduli, fast, nullptr, 0, st)) != OZK2_OK) return s;
+  if ((s = phase_scales(c, operand_a(transa, A, lda), operand_b(transb, B, ldb), true)) != OZK2_OK) return s;
   const Layout& L = c.L;
   auto cp = [&](void* dst, size_t off, size_t bytes) -> cudaError_t {
     if (!dst) return cudaSuccess;
@@ -500,9 +617,18 @@ ozk2_status ozk2_debug_scales(int64_t m, int64_t n, int64_t k, const double* A, 
   OZK2_TRY(cp(fprime, L.fprime, 4 * size_t(n)));
   OZK2_TRY(cp(R, L.R, 4 * size_t(m)));
   OZK2_TRY(cp(S, L.S, 4 * size_t(n)));
-  OZK2_TRY(cp(Abar, L.Abar, size_t(m) * L.kp));
-  OZK2_TRY(cp(BbarT, L.BbarT, size_t(n) * L.kp));
+  if (!fast) {
+    OZK2_TRY(cp(Abar, L.Abar, size_t(m) * L.kp));
+    OZK2_TRY(cp(BbarT, L.BbarT, size_t(n) * L.kp));
+  }
   return OZK2_OK;
+}
+
+ozk2_status ozk2_debug_scales(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                              int64_t ldb, int num_moduli, int32_t* e, int32_t* f, int32_t* eprime, int32_t* fprime,
+                              float* R, float* S, uint8_t* Abar, uint8_t* BbarT, ozk2_stream_t stream) {
+  return ozk2_debug_scales_ex(OZK2_OP_N, OZK2_OP_N, m, n, k, A, lda, B, ldb, num_moduli, OZK2_MODE_ACCURATE, e, f,
+                              eprime, fprime, R, S, Abar, BbarT, stream);
 }
 
 ozk2_status ozk2_debug_residue_planes(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
@@ -514,8 +640,8 @@ ozk2_status ozk2_debug_residue_planes(int64_t m, int64_t n, int64_t k, const dou
   if (m == 0 || n == 0 || k == 0 || !A || !B || !e || !f || !planesA || !planesB || lda < k || ldb < n)
     return OZK2_ERR_INVALID_VALUE;
   Ctx c;
-  if ((s = setup(c, m, n, k, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
-  return phase_residues(c, A, lda, B, ldb, e, f, planesA, planesB);
+  if ((s = setup(c, m, n, k, num_moduli, false, nullptr, 0, st)) != OZK2_OK) return s;
+  return phase_residues(c, operand_a(OZK2_OP_N, A, lda), operand_b(OZK2_OP_N, B, ldb), e, f, planesA, planesB);
 }
 
 ozk2_status ozk2_debug_residue_products(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
@@ -527,9 +653,10 @@ ozk2_status ozk2_debug_residue_products(int64_t m, int64_t n, int64_t k, const d
   if (m == 0 || n == 0 || k == 0 || !A || !B || !e || !f || !Cres || lda < k || ldb < n)
     return OZK2_ERR_INVALID_VALUE;
   Ctx c;
-  if ((s = setup(c, m, n, k, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
+  if ((s = setup(c, m, n, k, num_moduli, false, nullptr, 0, st)) != OZK2_OK) return s;
   const Layout& L = c.L;
-  if ((s = phase_residues(c, A, lda, B, ldb, e, f, c.at<uint8_t>(L.planesA), c.at<uint8_t>(L.planesB))) != OZK2_OK)
+  if ((s = phase_residues(c, operand_a(OZK2_OP_N, A, lda), operand_b(OZK2_OP_N, B, ldb), e, f,
+                          c.at<uint8_t>(L.planesA), c.at<uint8_t>(L.planesB))) != OZK2_OK)
     return s;
   if ((s = phase_products(c)) != OZK2_OK) return s;
   OZK2_TRY(cudaMemcpy2DAsync(Cres, size_t(n) * 2, c.ws + L.cres, size_t(L.ldr) * 2, size_t(n) * 2,
@@ -545,7 +672,7 @@ ozk2_status ozk2_debug_crt(int64_t m, int64_t n, int num_moduli, const int16_t* 
   if (m == 0 || n == 0) return OZK2_OK;
   if (!Cres || !e || !f || !C || ldc < n) return OZK2_ERR_INVALID_VALUE;
   Ctx c;
-  if ((s = setup(c, m, n, 1, num_moduli, nullptr, 0, st)) != OZK2_OK) return s;
+  if ((s = setup(c, m, n, 1, num_moduli, false, nullptr, 0, st)) != OZK2_OK) return s;
   const Layout& L = c.L;
   OZK2_TRY(cudaMemcpy2DAsync(c.ws + L.cres, size_t(L.ldr) * 2, Cres, size_t(n) * 2, size_t(n) * 2,
                              size_t(num_moduli) * size_t(m), cudaMemcpyDeviceToDevice, st));

@@ -62,16 +62,17 @@ float bound_factor_f32(int64_t k);   // RU_fp32(1 + k 2^-24)
 // Kernel launchers (each returns the cudaError_t of its launch)
 // ---------------------------------------------------------------------------
 
-// scale.cu
+// scale.cu.  "rows": lines contiguous along k; "cols": lines strided along k.  With
+// fast = true the kernels write sums of squares (sq) instead of bound operands.
 cudaError_t launch_scale_rows(const double* A, int64_t lda, int m, int k, int kp,
-                              int32_t* eprime, uint8_t* rowstat, uint8_t* Abar,
-                              uint32_t* flags, cudaStream_t st);
+                              int32_t* eprime, uint8_t* rowstat, uint8_t* Abar, float* sq,
+                              bool fast, uint32_t* flags, cudaStream_t st);
 cudaError_t launch_colmax(const double* B, int64_t ldb, int k, int n,
                           unsigned long long* colmax, uint32_t* colbad, cudaStream_t st);
 cudaError_t launch_scale_cols(const double* B, int64_t ldb, int k, int n, int kp,
                               const unsigned long long* colmax, const uint32_t* colbad,
-                              int32_t* fprime, uint8_t* colstat, uint8_t* BbarT,
-                              uint32_t* flags, cudaStream_t st);
+                              int32_t* fprime, uint8_t* colstat, uint8_t* BbarT, float* part,
+                              float* sq, bool fast, uint32_t* flags, cudaStream_t st);
 cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t* fprime,
                              const uint8_t* rowstat, const uint8_t* colstat,
                              const float* R, const float* S, float pprime, float delta,

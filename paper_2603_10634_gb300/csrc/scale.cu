@@ -1,10 +1,14 @@
-// Accurate-mode scaling, Sec. III-E of the paper (workflow steps 1 and 3 of Sec. IV-B).
+// Scaling, Sec. III-E of the paper (workflow steps 1 and 3 of Sec. IV-B).
 //
 //   e'_i = 7 - floor(log2 max_h |a_ih|)             (Eq. def:mu'nu', mu'_i = 2^e'_i)
 //   Abar_ih = RU_E4M3(2^e'_i |a_ih|)                 (cast to E4M3 in round-up mode)
 //   e_i = e'_i + int(P' + delta log2 max_j cbar_ij)  (Eq. mu-computation)
 // and the same for the columns of B, whose bound operand is stored transposed
-// (n x kp, K-major) so that both GEMM operands are K-major.
+// (n x kp, K-major) so that both GEMM operands are K-major.  Fast mode replaces the bound
+// product by the Cauchy-Schwarz bound: the kernels then produce round-up sums of squares
+// of the scaled lines instead of Abar / Bbar, and the same exponent rule applies.
+// "Rows" kernels serve any operand whose lines are contiguous along k (A, or B^T), the
+// "column" kernels any operand whose lines are strided along k (B, or A^T).
 //
 // Everything up to the exponent rule is integer manipulation of the IEEE-754
 // encoding: no FP64 arithmetic and no 2^e' factor is ever formed (e' reaches 1081
@@ -55,12 +59,39 @@ __device__ __forceinline__ uint32_t ru_e4m3_scaled(unsigned long long mag, int s
   return 1;
 }
 
+// RU_fp32(|x| 2^sh) for |x| given by its (finite, nonzero) bits and |x| 2^sh < 2^8: the
+// float bit pattern is assembled from the exponent and the top 23 fraction bits, plus one
+// unit when any lower bit is set (a carry into the exponent field stays correct).
+// Results below the FP32 normal range are replaced by 2^-126, still an upper bound.
+__device__ __forceinline__ float ru_f32_scaled(unsigned long long mag, int sh) {
+  if (mag == 0) return 0.0f;
+  int be = static_cast<int>(mag >> 52);
+  unsigned long long f52 = mag & kFracMask;
+  int lg;
+  if (be == 0) {
+    const int top = 63 - __clzll(f52);
+    lg = top - 1074;
+    f52 = (f52 << (52 - top)) & kFracMask;
+  } else {
+    lg = be - 1023;
+  }
+  const int ev = lg + sh;
+  if (ev < -126) return 1.1754943508222875e-38f;  // 2^-126
+  const uint32_t bits = (static_cast<uint32_t>(ev + 127) << 23) + static_cast<uint32_t>(f52 >> 29) +
+                        ((f52 & ((1ull << 29) - 1)) != 0 ? 1u : 0u);
+  return __uint_as_float(bits);
+}
+
 // One warp per row of A: row maximum, e'_i, row status, then Abar (m x kp bytes).
+// FAST: instead of Abar, the sum of squares s_i = sum_h RU_fp32(2^e'_i |a_ih|)^2 with
+// every addition rounded up (an upper bound of ||2^e'_i a_i||_2^2), written to sq[row].
+template <bool FAST>
 __global__ void __launch_bounds__(256) scale_rows_kernel(const double* __restrict__ A, int64_t lda,
                                                          int m, int k, int kp,
                                                          int32_t* __restrict__ eprime,
                                                          uint8_t* __restrict__ rowstat,
                                                          uint8_t* __restrict__ Abar,
+                                                         float* __restrict__ sq,
                                                          uint32_t* flags) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -85,18 +116,32 @@ __global__ void __launch_bounds__(256) scale_rows_kernel(const double* __restric
     rowstat[row] = static_cast<uint8_t>((mx == 0 ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
     if (bad) atomicOr(flags, kFlagNonfinite);
   }
-  uint8_t* out = Abar + static_cast<int64_t>(row) * kp;
-  for (int h0 = lane * 4; h0 < kp; h0 += 128) {
-    uint32_t word = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int h = h0 + t;
-      if (h < k) {
-        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
-        if (b < kInfBits) word |= ru_e4m3_scaled(b, ep) << (8 * t);
+  if constexpr (FAST) {
+    float acc = 0.0f;
+    for (int h = lane; h < k; h += 32) {
+      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
+      if (b != 0 && b < kInfBits) {
+        const float v = ru_f32_scaled(b, ep);
+        acc = __fmaf_ru(v, v, acc);
       }
     }
-    *reinterpret_cast<uint32_t*>(out + h0) = word;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) acc = __fadd_ru(acc, __shfl_xor_sync(0xffffffffu, acc, off));
+    if (lane == 0) sq[row] = acc;
+  } else {
+    uint8_t* out = Abar + static_cast<int64_t>(row) * kp;
+    for (int h0 = lane * 4; h0 < kp; h0 += 128) {
+      uint32_t word = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int h = h0 + t;
+        if (h < k) {
+          const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
+          if (b < kInfBits) word |= ru_e4m3_scaled(b, ep) << (8 * t);
+        }
+      }
+      *reinterpret_cast<uint32_t*>(out + h0) = word;
+    }
   }
 }
 
@@ -124,6 +169,9 @@ __global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ 
 }
 
 // Bbar^T (n x kp bytes): thread (column j, 32 consecutive h) writes 32 bytes of row j.
+// FAST: instead, the partial sum of squares of the 32 elements (rounded up) goes to
+// part[hb * n + j]; sumsq_reduce_kernel adds the partials of a column in a fixed order.
+template <bool FAST>
 __global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restrict__ B, int64_t ldb,
                                                          int k, int n, int kp,
                                                          const unsigned long long* __restrict__ colmax,
@@ -131,6 +179,7 @@ __global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restric
                                                          int32_t* __restrict__ fprime,
                                                          uint8_t* __restrict__ colstat,
                                                          uint8_t* __restrict__ BbarT,
+                                                         float* __restrict__ part,
                                                          uint32_t* flags) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int hb = blockIdx.y;
@@ -143,21 +192,47 @@ __global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restric
     colstat[j] = static_cast<uint8_t>((mx == 0 ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
     if (bad) atomicOr(flags, kFlagNonfinite);
   }
-  uint32_t w[8];
-#pragma unroll
-  for (int q = 0; q < 8; ++q) w[q] = 0;
-#pragma unroll
-  for (int t = 0; t < 32; ++t) {
-    const int h = hb * 32 + t;
-    if (h < k) {
-      const unsigned long long b =
-          static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
-      if (b < kInfBits) w[t >> 2] |= ru_e4m3_scaled(b, fp) << (8 * (t & 3));
+  if constexpr (FAST) {
+    float acc = 0.0f;
+#pragma unroll 8
+    for (int t = 0; t < 32; ++t) {
+      const int h = hb * 32 + t;
+      if (h < k) {
+        const unsigned long long b =
+            static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
+        if (b != 0 && b < kInfBits) {
+          const float v = ru_f32_scaled(b, fp);
+          acc = __fmaf_ru(v, v, acc);
+        }
+      }
     }
+    part[static_cast<int64_t>(hb) * n + j] = acc;
+  } else {
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) w[q] = 0;
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int h = hb * 32 + t;
+      if (h < k) {
+        const unsigned long long b =
+            static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
+        if (b < kInfBits) w[t >> 2] |= ru_e4m3_scaled(b, fp) << (8 * (t & 3));
+      }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(BbarT + static_cast<int64_t>(j) * kp + hb * 32);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
   }
-  uint4* dst = reinterpret_cast<uint4*>(BbarT + static_cast<int64_t>(j) * kp + hb * 32);
-  dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-  dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// s_j = sum over blocks of part[hb][j], every addition rounded up, in block order.
+__global__ void sumsq_reduce_kernel(const float* __restrict__ part, int nblocks, int n, float* __restrict__ sq) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float acc = 0.0f;
+  for (int hb = 0; hb < nblocks; ++hb) acc = __fadd_ru(acc, part[static_cast<int64_t>(hb) * n + j]);
+  sq[j] = acc;
 }
 
 // e = e' + floor(RD(P' + RD(delta * log2 R))) [Eq. mu-computation].  log2 is the FP32
@@ -191,10 +266,14 @@ __global__ void exponents_kernel(int m, int n, const int32_t* __restrict__ eprim
 }  // namespace
 
 cudaError_t launch_scale_rows(const double* A, int64_t lda, int m, int k, int kp, int32_t* eprime,
-                              uint8_t* rowstat, uint8_t* Abar, uint32_t* flags, cudaStream_t st) {
+                              uint8_t* rowstat, uint8_t* Abar, float* sq, bool fast, uint32_t* flags,
+                              cudaStream_t st) {
   const int rows_per_block = 8;
-  scale_rows_kernel<<<(m + rows_per_block - 1) / rows_per_block, 256, 0, st>>>(
-      A, lda, m, k, kp, eprime, rowstat, Abar, flags);
+  const int grid = (m + rows_per_block - 1) / rows_per_block;
+  if (fast)
+    scale_rows_kernel<true><<<grid, 256, 0, st>>>(A, lda, m, k, kp, eprime, rowstat, Abar, sq, flags);
+  else
+    scale_rows_kernel<false><<<grid, 256, 0, st>>>(A, lda, m, k, kp, eprime, rowstat, Abar, sq, flags);
   return cudaGetLastError();
 }
 
@@ -207,11 +286,17 @@ cudaError_t launch_colmax(const double* B, int64_t ldb, int k, int n, unsigned l
 
 cudaError_t launch_scale_cols(const double* B, int64_t ldb, int k, int n, int kp,
                               const unsigned long long* colmax, const uint32_t* colbad,
-                              int32_t* fprime, uint8_t* colstat, uint8_t* BbarT, uint32_t* flags,
-                              cudaStream_t st) {
+                              int32_t* fprime, uint8_t* colstat, uint8_t* BbarT, float* part, float* sq,
+                              bool fast, uint32_t* flags, cudaStream_t st) {
   dim3 grid((n + 255) / 256, kp / 32);
-  scale_cols_kernel<<<grid, 256, 0, st>>>(B, ldb, k, n, kp, colmax, colbad, fprime, colstat, BbarT,
-                                          flags);
+  if (fast) {
+    scale_cols_kernel<true><<<grid, 256, 0, st>>>(B, ldb, k, n, kp, colmax, colbad, fprime, colstat, BbarT, part,
+                                                  flags);
+    sumsq_reduce_kernel<<<(n + 255) / 256, 256, 0, st>>>(part, kp / 32, n, sq);
+  } else {
+    scale_cols_kernel<false><<<grid, 256, 0, st>>>(B, ldb, k, n, kp, colmax, colbad, fprime, colstat, BbarT,
+                                                   part, flags);
+  }
   return cudaGetLastError();
 }
 

@@ -29,10 +29,51 @@ def _check_matrix(x, name, dtype=torch.float64):
         raise ValueError(f"{name} must live on a CUDA device")
     if x.size(1) > 1 and x.stride(1) != 1:
         raise ValueError(f"{name} must be row-major (unit stride along columns)")
+    if x.size(0) > 1 and x.stride(0) == 0:
+        raise ValueError(f"{name} has a broadcast (zero) row stride")
 
 
 def _ld(x):
-    return max(1, x.stride(0) if x.size(0) > 1 else x.size(1))
+    return x.stride(0) if x.size(0) > 1 else max(1, x.size(1))
+
+
+OP_N, OP_T = 0, 1
+MODES = {"accurate": 0, "fast": 1}
+
+
+def _operand(x, name):
+    """(op, ld) of a float64 CUDA matrix that is row-major (op N) or the transpose of a
+    row-major matrix (op T, e.g. ``Y.T``); the stored matrix is never copied."""
+    if not isinstance(x, torch.Tensor) or x.dim() != 2:
+        raise ValueError(f"{name} must be a 2-D torch tensor")
+    if x.dtype != torch.float64:
+        raise TypeError(f"{name} must be torch.float64, got {x.dtype}")
+    if not x.is_cuda:
+        raise ValueError(f"{name} must live on a CUDA device")
+    rows, cols = x.shape
+    s0, s1 = x.stride()
+    if (rows > 1 and s0 == 0) or (cols > 1 and s1 == 0):
+        raise ValueError(f"{name} has a broadcast (zero) stride; pass a materialised copy")
+    if cols <= 1 or s1 == 1:
+        return OP_N, (s0 if rows > 1 else max(1, cols))
+    if rows <= 1 or s0 == 1:
+        return OP_T, (s1 if cols > 1 else max(1, rows))
+    raise ValueError(f"{name} must be row-major or the transpose of a row-major matrix")
+
+
+def _mode(mode):
+    if mode not in MODES:
+        raise ValueError(f"mode must be one of {sorted(MODES)}")
+    return MODES[mode]
+
+
+def _block(block):
+    if block is None:
+        return 0, 0
+    bm, bn = block
+    if bm < 0 or bn < 0:
+        raise ValueError("block sizes must be >= 0")
+    return int(bm), int(bn)
 
 
 def moduli(num_moduli=12):
@@ -44,37 +85,49 @@ def moduli(num_moduli=12):
     return list(buf)
 
 
-def workspace_size(m, n, k, num_moduli=12):
-    return int(_lib.load().ozk2_workspace_size(m, n, k, num_moduli))
+def workspace_size(m, n, k, num_moduli=12, mode="accurate", block=None):
+    bm, bn = _block(block)
+    return int(_lib.load().ozk2_workspace_size_ex(m, n, k, num_moduli, _mode(mode), bm, bn))
 
 
-def dgemm(A, B, num_moduli=12, out=None, workspace=None):
-    """C = A @ B in emulated FP64 (A: m x k, B: k x n, float64 CUDA tensors, row-major).
+def dgemm(A, B, num_moduli=12, out=None, workspace=None, mode="accurate", block=None):
+    """C = A @ B in emulated FP64 (A: m x k, B: k x n, float64 CUDA tensors).
 
+    A and B may each be row-major or the transpose of a row-major matrix (``X.T``);
+    ``mode`` is "accurate" or "fast" (the two scalings of Sec. III-E); ``block`` =
+    (block_m, block_n) runs independent emulations of those blocks of C (Sec. IV-C).
     ``workspace`` may be a uint8 CUDA tensor of at least ``workspace_size`` bytes;
     otherwise the library's own per-device workspace is used."""
-    _check_matrix(A, "A")
-    _check_matrix(B, "B")
+    ta, lda = _operand(A, "A")
+    tb, ldb = _operand(B, "B")
     m, k = A.shape
     k2, n = B.shape
     if k != k2:
-        raise ValueError(f"inner dimensions differ: {A.shape} @ {B.shape}")
+        raise ValueError(f"inner dimensions differ: {tuple(A.shape)} @ {tuple(B.shape)}")
     if A.device != B.device:
         raise ValueError("A and B must be on the same device")
+    md = _mode(mode)
+    bm, bn = _block(block)
     if out is None:
         out = torch.empty((m, n), dtype=torch.float64, device=A.device)
     else:
         _check_matrix(out, "out")
         if tuple(out.shape) != (m, n):
             raise ValueError("out has the wrong shape")
+    if workspace is not None and (workspace.dtype != torch.uint8 or not workspace.is_cuda):
+        raise TypeError("workspace must be a uint8 CUDA tensor")
     lib = _lib.load()
     with torch.cuda.device(A.device):
         st = _stream(A.device)
-        if workspace is None:
-            s = lib.ozk2_dgemm(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(out), _ld(out), num_moduli, st)
+        if ta == OP_N and tb == OP_N and md == 0 and bm == 0 and bn == 0:
+            if workspace is None:
+                s = lib.ozk2_dgemm(m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(out), _ld(out), num_moduli, st)
+            else:
+                s = lib.ozk2_dgemm_ws(m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(out), _ld(out), num_moduli,
+                                      _ptr(workspace), workspace.numel(), st)
         else:
-            s = lib.ozk2_dgemm_ws(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(out), _ld(out), num_moduli,
-                                  _ptr(workspace), workspace.numel(), st)
+            s = lib.ozk2_dgemm_ex(ta, tb, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(out), _ld(out), num_moduli,
+                                  md, bm, bn, _ptr(workspace), 0 if workspace is None else workspace.numel(), st)
     _lib.check(s, "ozk2_dgemm")
     return out
 
@@ -128,10 +181,13 @@ def fp8_gemm(A8, B8, k=None):
     return D
 
 
-def scales(A, B, num_moduli=12):
-    """Scaling intermediates: dict of e, f, eprime, fprime, R, S, Abar (m x kp), BbarT (n x kp)."""
-    _check_matrix(A, "A")
-    _check_matrix(B, "B")
+def scales(A, B, num_moduli=12, mode="accurate"):
+    """Scaling intermediates: dict of e, f, eprime, fprime, R, S, and in accurate mode Abar
+    (m x kp) and BbarT (n x kp).  In fast mode R and S are the round-up sums of squares of
+    the scaled rows of A and columns of B.  A, B as for ``dgemm``."""
+    ta, lda = _operand(A, "A")
+    tb, ldb = _operand(B, "B")
+    md = _mode(mode)
     m, k = A.shape
     n = B.shape[1]
     dev = A.device
@@ -139,14 +195,15 @@ def scales(A, B, num_moduli=12):
     out = dict(e=torch.empty(m, dtype=torch.int32, device=dev), f=torch.empty(n, dtype=torch.int32, device=dev),
                eprime=torch.empty(m, dtype=torch.int32, device=dev),
                fprime=torch.empty(n, dtype=torch.int32, device=dev),
-               R=torch.empty(m, dtype=torch.float32, device=dev), S=torch.empty(n, dtype=torch.float32, device=dev),
-               Abar=torch.empty((m, kp), dtype=torch.uint8, device=dev),
-               BbarT=torch.empty((n, kp), dtype=torch.uint8, device=dev))
+               R=torch.empty(m, dtype=torch.float32, device=dev), S=torch.empty(n, dtype=torch.float32, device=dev))
+    if md == 0:
+        out["Abar"] = torch.empty((m, kp), dtype=torch.uint8, device=dev)
+        out["BbarT"] = torch.empty((n, kp), dtype=torch.uint8, device=dev)
     lib = _lib.load()
-    s = lib.ozk2_debug_scales(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), num_moduli, _ptr(out["e"]),
-                              _ptr(out["f"]), _ptr(out["eprime"]), _ptr(out["fprime"]), _ptr(out["R"]),
-                              _ptr(out["S"]), _ptr(out["Abar"]), _ptr(out["BbarT"]), _stream(dev))
-    _lib.check(s, "ozk2_debug_scales")
+    s = lib.ozk2_debug_scales_ex(ta, tb, m, n, k, _ptr(A), lda, _ptr(B), ldb, num_moduli, md, _ptr(out["e"]),
+                                 _ptr(out["f"]), _ptr(out["eprime"]), _ptr(out["fprime"]), _ptr(out["R"]),
+                                 _ptr(out["S"]), _ptr(out.get("Abar")), _ptr(out.get("BbarT")), _stream(dev))
+    _lib.check(s, "ozk2_debug_scales_ex")
     return out
 
 

@@ -35,7 +35,8 @@ def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["ozk2_dgemm", "ozk2_workspace_size", "ozk2_dgemm_ws", "ozk2_status_string",
                      "ozk2_device_status", "ozk2_moduli", "ozk2_debug_fp8_gemm", "ozk2_debug_scales",
-                     "ozk2_debug_residue_planes", "ozk2_debug_residue_products", "ozk2_debug_crt"]:
+                     "ozk2_debug_residue_planes", "ozk2_debug_residue_products", "ozk2_debug_crt",
+                     "ozk2_dgemm_ex", "ozk2_workspace_size_ex", "ozk2_debug_scales_ex", "ozk2_dgemm_noalloc"]:
         assert required in names
 
 
@@ -70,6 +71,41 @@ def test_argument_validation_is_synchronous(lib):
     assert lib.ozk2_dgemm(4, 0, 4, null, 4, null, 1, null, 1, 12, null) == 0
     assert lib.ozk2_dgemm_ws(4, 4, 4, bogus, 4, bogus, 4, bogus, 4, 12, null, 0, null) == 1
     assert lib.ozk2_debug_fp8_gemm(-1, 1, 1, bogus, 16, bogus, 16, bogus, 1, null) == 1
+
+
+def test_extended_entry_validation(lib):
+    null = ctypes.c_void_p(0)
+    bogus = ctypes.c_void_p(0x1000)
+
+    def ex(ta, tb, m, n, k, lda, ldb, ldc, N=12, mode=0, bm=0, bn=0, A=bogus, B=bogus, C=bogus):
+        return lib.ozk2_dgemm_ex(ta, tb, m, n, k, A, lda, B, ldb, C, ldc, N, mode, bm, bn, null, 0, null)
+
+    assert ex(2, 0, 4, 4, 4, 4, 4, 4) == 1  # bad op
+    assert ex(0, 7, 4, 4, 4, 4, 4, 4) == 1
+    assert ex(0, 0, 4, 4, 4, 4, 4, 4, mode=2) == 1  # bad mode
+    assert ex(0, 0, 4, 4, 4, 4, 4, 4, bm=-1) == 1  # bad block
+    # op(A) = A^T: A stored k x m, lda >= m;  op(B) = B^T: B stored n x k, ldb >= k
+    assert ex(1, 0, 6, 4, 3, 5, 4, 4) == 1  # lda 5 < m 6
+    assert ex(0, 1, 4, 6, 3, 3, 2, 6) == 1  # ldb 2 < k 3
+    assert ex(1, 1, 4, 6, 3, 4, 3, 5) == 1  # ldc 5 < n 6
+    assert ex(1, 1, 0, 6, 3, 4, 3, 6, A=null, B=null, C=null) == 0  # empty: nothing touched
+    assert ex(0, 0, 4, 4, 4, 4, 4, 4, N=21) == 1
+
+
+def test_workspace_size_ex(lib):
+    # the transposes do not enter; fast mode drops the two bound operands; blocking
+    # sizes the workspace for one block
+    m, n, k, N = 3000, 2000, 1000, 12
+    acc = lib.ozk2_workspace_size_ex(m, n, k, N, 0, 0, 0)
+    assert acc == lib.ozk2_workspace_size(m, n, k, N)
+    fast = lib.ozk2_workspace_size_ex(m, n, k, N, 1, 0, 0)
+    assert acc - fast >= (m + n) * 1024 - (m + n) * 4 * 32 - 4096
+    assert fast < acc
+    blk = lib.ozk2_workspace_size_ex(m, n, k, N, 0, 1024, 512)
+    assert blk == lib.ozk2_workspace_size(1024, 512, k, N)
+    assert lib.ozk2_workspace_size_ex(m, n, k, N, 0, 5000, 5000) == acc
+    assert lib.ozk2_workspace_size_ex(m, n, k, N, 3, 0, 0) == 0
+    assert lib.ozk2_workspace_size_ex(m, n, k, N, 0, -2, 0) == 0
 
 
 def test_library_moduli_match_oracle(lib):

@@ -134,3 +134,23 @@ def test_planted_sign_error_is_caught(monkeypatch):
     monkeypatch.setattr(oz, "delta_constant", lambda: np.float32(0.5))
     worst, P, _ = _check_condition(A, B, 12)
     assert worst >= P
+
+
+@pytest.mark.parametrize("phi", [0.5, 1.0, 2.0])
+def test_fast_mode_condition_and_cauchy_schwarz(phi):
+    """Fast mode (R15): the squared-norm bound dominates ||2^e' a_i||^2, Eq. condition
+    holds exactly, and the result is accurate, slightly below accurate mode."""
+    rng = np.random.default_rng(int(phi * 7))
+    A, B = gen((10, 45), phi, rng), gen((45, 9), phi, rng)
+    sc = oz.scaling_exponents(A, B, 13, mode="fast")
+    for i in range(10):
+        exact = sum(Fraction(float(x)) ** 2 * Fraction(2) ** (2 * int(sc["eprime"][i])) for x in A[i])
+        assert Fraction(float(sc["R"][i])) >= exact
+    r = oz.ozk2_dgemm(A, B, 13, keep=True, mode="fast")
+    P = oz.product_P(r["moduli"])
+    lhs = 2 * np.abs(r["Aint"]).astype(object).dot(np.abs(r["Bint"]).astype(object))
+    assert max(int(v) for v in lhs.flat) < P
+    # fast mode uses fewer bits than accurate mode, never more
+    acc = oz.ozk2_dgemm(A, B, 13, keep=True)
+    assert np.all(r["e"] <= acc["e"] + 1) and np.all(r["f"] <= acc["f"] + 1)
+    assert max(int(v) for v in lhs.flat) > P / 2**16
