@@ -151,6 +151,37 @@ ozk2_status ozk2_dgemm_ex(ozk2_op transa, ozk2_op transb,
 size_t ozk2_workspace_size_ex(int64_t m, int64_t n, int64_t k, int num_moduli,
                               ozk2_mode mode, int64_t block_m, int64_t block_n);
 
+/*
+ * ozk2_dgemm_host - C := op(A) * op(B) with A, B and C in HOST memory (same shapes,
+ * leading dimensions and ops as ozk2_dgemm_ex, no blocking).
+ *
+ * The library copies B and then A (in four line chunks) to the device on its own copy
+ * stream while the scaling of what has arrived runs on `stream`; after the exponents
+ * and residues, the residue products and the CRT run in output row blocks and each
+ * block is copied back while the next one is computed.  The device arithmetic is that
+ * of ozk2_dgemm_ex, so C is bit-identical to the device-buffer call.
+ *   A, B, C    host pointers.  Page-locked (pinned) memory lets the copies overlap the
+ *              kernels; pageable memory works, with less overlap.  They must stay valid
+ *              and A, B unchanged until `stream` reaches the end of the call.
+ *   workspace  device, 256-byte aligned, >= ozk2_workspace_size_host bytes (it also
+ *              holds the device copies of A, B and C), or NULL for the library-owned
+ *              workspace.
+ * Asynchronous: returns after enqueueing; C is complete when `stream` is.  k = 0
+ * synchronises `stream` and zero-fills C on the host.
+ */
+ozk2_status ozk2_dgemm_host(ozk2_op transa, ozk2_op transb,
+                            int64_t m, int64_t n, int64_t k,
+                            const double *A, int64_t lda,
+                            const double *B, int64_t ldb,
+                            double *C, int64_t ldc,
+                            int num_moduli, ozk2_mode mode,
+                            void *workspace, size_t workspace_bytes,
+                            ozk2_stream_t stream);
+
+/* ozk2_workspace_size_host - workspace bytes of one ozk2_dgemm_host call; 0 on
+ * invalid arguments. */
+size_t ozk2_workspace_size_host(int64_t m, int64_t n, int64_t k, int num_moduli, ozk2_mode mode);
+
 /* ozk2_status_string - a static, human-readable name for a status code. */
 const char *ozk2_status_string(ozk2_status status);
 

@@ -12,6 +12,7 @@ from .ozk2 import (  # noqa: F401
     crt,
     device_status,
     dgemm,
+    dgemm_host,
     fp8_gemm,
     get_timing,
     last_launch_count,
@@ -21,4 +22,5 @@ from .ozk2 import (  # noqa: F401
     scales,
     set_timing,
     workspace_size,
+    workspace_size_host,
 )

@@ -163,6 +163,7 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N, bool fast) {
 struct Ctx {
   int m, n, k, N;
   bool fast;
+  bool timed = true;  // record the per-phase timing events (sequential calls only)
   Layout L;
   uint8_t* ws;
   const Tables* tab;
@@ -216,7 +217,7 @@ std::mutex g_timing_mutex;
 thread_local int t_launches = 0;
 
 void mark(Ctx& c, int idx) {
-  if (!g_timing.enabled) return;
+  if (!g_timing.enabled || !c.timed) return;
   int dev = 0;
   cudaGetDevice(&dev);
   if (g_timing.dev != dev) {
@@ -236,39 +237,52 @@ void mark(Ctx& c, int idx) {
   } while (0)
 
 // ------------------------------------------------------------------ phases
-// e'/status and either the E4M3 bound operand (accurate) or the sums of squares (fast)
-// of one operand.
-ozk2_status scale_operand(Ctx& c, const Operand& op, int lines, size_t eprime, size_t stat, size_t bar, size_t sq,
-                          size_t part, size_t colmax, size_t colbad) {
+// Zero the bound maxima and column reductions of a call (and its flag word when
+// clear_flags: the first block of a call; later blocks keep what earlier blocks
+// recorded).
+ozk2_status zero_scratch(Ctx& c, bool clear_flags) {
   const Layout& L = c.L;
+  if (clear_flags)
+    OZK2_TRY(cudaMemsetAsync(c.ws, 0, L.zero_end, c.st));
+  else
+    OZK2_TRY(cudaMemsetAsync(c.ws + L.R, 0, L.zero_end - L.R, c.st));
+  return OZK2_OK;
+}
+
+// Which operand a scaling launch serves.
+struct Side {
+  size_t eprime, stat, bar, sq, part, colmax, colbad;
+};
+Side side_a(const Layout& L) { return Side{L.eprime, L.rowstat, L.Abar, L.R, L.partA, L.colmaxA, L.colbadA}; }
+Side side_b(const Layout& L) { return Side{L.fprime, L.colstat, L.BbarT, L.S, L.partB, L.colmaxB, L.colbadB}; }
+
+// e'/status and either the E4M3 bound operand (accurate) or the sums of squares (fast)
+// of lines [first, first + lines) of one operand (`op` points at line `first`).
+ozk2_status scale_operand(Ctx& c, const Operand& op, int64_t first, int lines, const Side& sd) {
+  const Layout& L = c.L;
+  const int64_t kb = L.kp / 32;
+  int32_t* ep = c.at<int32_t>(sd.eprime) + first;
+  uint8_t* stat = c.at<uint8_t>(sd.stat) + first;
+  uint8_t* bar = c.at<uint8_t>(sd.bar) + first * L.kp;
+  float* sq = c.at<float>(sd.sq) + first;
   if (op.kcontig) {
-    OZK2_TRY(launch_scale_rows(op.ptr, op.ld, lines, c.k, int(L.kp), c.at<int32_t>(eprime), c.at<uint8_t>(stat),
-                               c.at<uint8_t>(bar), c.at<float>(sq), c.fast, c.at<uint32_t>(L.flags), c.st));
+    OZK2_TRY(launch_scale_rows(op.ptr, op.ld, lines, c.k, int(L.kp), ep, stat, bar, sq, c.fast,
+                               c.at<uint32_t>(L.flags), c.st));
     t_launches += 1;
   } else {
-    OZK2_TRY(launch_colmax(op.ptr, op.ld, c.k, lines, c.at<unsigned long long>(colmax), c.at<uint32_t>(colbad), c.st));
-    OZK2_TRY(launch_scale_cols(op.ptr, op.ld, c.k, lines, int(L.kp), c.at<unsigned long long>(colmax),
-                               c.at<uint32_t>(colbad), c.at<int32_t>(eprime), c.at<uint8_t>(stat),
-                               c.at<uint8_t>(bar), c.at<float>(part), c.at<float>(sq), c.fast,
-                               c.at<uint32_t>(L.flags), c.st));
+    unsigned long long* cm = c.at<unsigned long long>(sd.colmax) + first;
+    uint32_t* cb = c.at<uint32_t>(sd.colbad) + first;
+    OZK2_TRY(launch_colmax(op.ptr, op.ld, c.k, lines, cm, cb, c.st));
+    OZK2_TRY(launch_scale_cols(op.ptr, op.ld, c.k, lines, int(L.kp), cm, cb, ep, stat, bar,
+                               c.at<float>(sd.part) + first * kb, sq, c.fast, c.at<uint32_t>(L.flags), c.st));
     t_launches += c.fast ? 3 : 2;
   }
   return OZK2_OK;
 }
 
-// clear_flags: start a new flag word (the first block of a call); later blocks of a
-// blocked call keep what earlier blocks recorded.
-ozk2_status phase_scales(Ctx& c, const Operand& a, const Operand& b, bool clear_flags) {
+// Bound product (accurate mode) and the exponents e, f.
+ozk2_status bound_and_exponents(Ctx& c) {
   const Layout& L = c.L;
-  ozk2_status s;
-  if (clear_flags)
-    OZK2_TRY(cudaMemsetAsync(c.ws, 0, L.zero_end, c.st));
-  else
-    OZK2_TRY(cudaMemsetAsync(c.ws + L.R, 0, L.zero_end - L.R, c.st));
-  if ((s = scale_operand(c, a, c.m, L.eprime, L.rowstat, L.Abar, L.R, L.partA, L.colmaxA, L.colbadA)) != OZK2_OK)
-    return s;
-  if ((s = scale_operand(c, b, c.n, L.fprime, L.colstat, L.BbarT, L.S, L.partB, L.colmaxB, L.colbadB)) != OZK2_OK)
-    return s;
   mark(c, 1);
   if (!c.fast) {
     GemmArgs g{};
@@ -293,6 +307,14 @@ ozk2_status phase_scales(Ctx& c, const Operand& a, const Operand& b, bool clear_
   return OZK2_OK;
 }
 
+ozk2_status phase_scales(Ctx& c, const Operand& a, const Operand& b, bool clear_flags) {
+  ozk2_status s;
+  if ((s = zero_scratch(c, clear_flags)) != OZK2_OK) return s;
+  if ((s = scale_operand(c, a, 0, c.m, side_a(c.L))) != OZK2_OK) return s;
+  if ((s = scale_operand(c, b, 0, c.n, side_b(c.L))) != OZK2_OK) return s;
+  return bound_and_exponents(c);
+}
+
 cudaError_t residues_operand(Ctx& c, const Operand& op, int lines, const int32_t* ex, uint8_t* planes) {
   if (op.kcontig)
     return launch_residues_rows(op.ptr, op.ld, lines, c.k, int(c.L.kp), ex, c.tab->mt, planes,
@@ -310,33 +332,50 @@ ozk2_status phase_residues(Ctx& c, const Operand& a, const Operand& b, const int
   return OZK2_OK;
 }
 
-ozk2_status phase_products(Ctx& c) {
+// Residue products C'_l for output rows [i0, i0 + rows).
+ozk2_status products_rows(Ctx& c, int64_t i0, int rows) {
   const Layout& L = c.L;
   GemmArgs g{};
   g.mode = kModeResidue;
-  g.m = c.m;
+  g.m = rows;
   g.n = c.n;
   g.k = c.k;
   g.num_sms = c.num_sms;
-  g.cres = c.at<int16_t>(L.cres);
+  g.cres = c.at<int16_t>(L.cres) + i0 * L.ldr;
   g.ldr = L.ldr;
   g.res_stride = int64_t(c.m) * L.ldr;
   g.scratch = c.at<uint32_t>(L.scratch);
   g.mt = &c.tab->mt;
   g.flags = c.at<uint32_t>(L.flags);
-  OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA), L.kp, L.planes, c.at<uint8_t>(L.planesB), L.kp, L.planes,
-                           c.st));
+  g.plane_stride_a = int64_t(c.m) * L.kp;
+  g.plane_stride_b = int64_t(c.n) * L.kp;
+  OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA) + i0 * L.kp, L.kp, L.planes, c.at<uint8_t>(L.planesB), L.kp,
+                           L.planes, c.st));
   t_launches += 1;
+  return OZK2_OK;
+}
+
+ozk2_status phase_products(Ctx& c) {
+  ozk2_status s = products_rows(c, 0, c.m);
+  if (s != OZK2_OK) return s;
   mark(c, 5);
+  return OZK2_OK;
+}
+
+// CRT and inverse scaling of output rows [i0, i0 + rows) into C (which points at row i0).
+ozk2_status crt_rows(Ctx& c, int64_t i0, int rows, const int32_t* e, const int32_t* f, const uint8_t* rowstat,
+                     const uint8_t* colstat, double* C, int64_t ldc) {
+  const Layout& L = c.L;
+  OZK2_TRY(launch_crt(c.at<int16_t>(L.cres) + i0 * L.ldr, L.ldr, int64_t(c.m) * L.ldr, rows, c.n, e + i0, f,
+                      rowstat ? rowstat + i0 : nullptr, colstat, C, ldc, c.tab->ct, c.st));
+  t_launches += 1;
   return OZK2_OK;
 }
 
 ozk2_status phase_crt(Ctx& c, const int32_t* e, const int32_t* f, const uint8_t* rowstat,
                       const uint8_t* colstat, double* C, int64_t ldc) {
-  const Layout& L = c.L;
-  OZK2_TRY(launch_crt(c.at<int16_t>(L.cres), L.ldr, int64_t(c.m) * L.ldr, c.m, c.n, e, f, rowstat, colstat, C, ldc,
-                      c.tab->ct, c.st));
-  t_launches += 1;
+  ozk2_status s = crt_rows(c, 0, c.m, e, f, rowstat, colstat, C, ldc);
+  if (s != OZK2_OK) return s;
   mark(c, 6);
   return OZK2_OK;
 }
@@ -371,8 +410,9 @@ ozk2_status validate_operands(ozk2_op transa, ozk2_op transb, int64_t m, int64_t
   return validate(transa, transb, m, n, k, A, lda, B, ldb, &dummy, std::max<int64_t>(1, n), N);
 }
 
+// `extra`: bytes the caller needs after the layout (256-aligned, at offset L.total).
 ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, bool fast, void* ws, size_t ws_bytes,
-                  cudaStream_t st) {
+                  cudaStream_t st, size_t extra = 0) {
   c.m = int(m);
   c.n = int(n);
   c.k = int(k);
@@ -385,11 +425,11 @@ ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, bool fast, voi
   if (!c.tab) return OZK2_ERR_INTERNAL;
   c.L = make_layout(m, n, k, N, fast);
   if (ws) {
-    if (ws_bytes < c.L.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) return OZK2_ERR_INVALID_VALUE;
+    if (ws_bytes < c.L.total + extra || (reinterpret_cast<uintptr_t>(ws) & 255u)) return OZK2_ERR_INVALID_VALUE;
     c.ws = static_cast<uint8_t*>(ws);
   } else {
     ozk2_status err = OZK2_OK;
-    c.ws = owned_workspace(c.L.total, &err);
+    c.ws = owned_workspace(c.L.total + extra, &err);
     if (!c.ws) return err;
   }
   return OZK2_OK;
@@ -446,14 +486,159 @@ ozk2_status dgemm_general(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, 
   return OZK2_OK;
 }
 
+// ------------------------------------------------------------------ host buffers
+// Device staging of a host-buffer call: A and B as stored (packed), and C.
+struct Staging {
+  size_t A, B, C, total;
+};
+
+Staging make_staging(int64_t m, int64_t n, int64_t k) {
+  Staging g;
+  size_t o = 0;
+  g.A = o;
+  o = align256(o + 8 * size_t(m) * size_t(k));
+  g.B = o;
+  o = align256(o + 8 * size_t(k) * size_t(n));
+  g.C = o;
+  o = align256(o + 8 * size_t(m) * size_t(n));
+  g.total = o;
+  return g;
+}
+
+constexpr int kHostChunks = 4;  // A arrives in this many line chunks
+constexpr int kHostBlocks = 4;  // at most this many output row blocks stream back
+constexpr int kHostEvents = 2 + kHostChunks + kHostBlocks + 1;
+
+struct CopyEngine {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev[kHostEvents] = {};
+};
+std::mutex g_copy_mutex;
+CopyEngine g_copy[64];
+
+// The library's copy stream and events of the current device (created on first use).
+CopyEngine* copy_engine(ozk2_status* err) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    *err = OZK2_ERR_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_copy_mutex);
+  CopyEngine& e = g_copy[dev];
+  if (!e.cs) {
+    if (cudaStreamCreateWithFlags(&e.cs, cudaStreamNonBlocking) != cudaSuccess) {
+      *err = OZK2_ERR_CUDA;
+      e.cs = nullptr;
+      return nullptr;
+    }
+    for (auto& ev : e.ev)
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        *err = OZK2_ERR_CUDA;
+        return nullptr;
+      }
+  }
+  return &e;
+}
+
+// Copy lines [i0, i1) of an operand stored on the host to its packed device copy.
+// kcontig lines are rows of the stored matrix (ld elements apart), otherwise columns.
+cudaError_t copy_lines_h2d(double* dst, const double* src, int64_t ld, bool kcontig, int64_t lines, int64_t k,
+                           int64_t i0, int64_t i1, cudaStream_t cs) {
+  if (i1 <= i0) return cudaSuccess;
+  if (kcontig)
+    return cudaMemcpy2DAsync(dst + i0 * k, size_t(k) * 8, src + i0 * ld, size_t(ld) * 8, size_t(k) * 8,
+                             size_t(i1 - i0), cudaMemcpyHostToDevice, cs);
+  return cudaMemcpy2DAsync(dst + i0, size_t(lines) * 8, src + i0, size_t(ld) * 8, size_t(i1 - i0) * 8, size_t(k),
+                           cudaMemcpyHostToDevice, cs);
+}
+
+// C = op(A) op(B) from host buffers: B and then A (in line chunks) go up on the copy
+// stream while the scaling of what has arrived runs on `st`; after the exponents and
+// residues, the residue products and the CRT run in output row blocks, and block b
+// streams back while block b + 1 is computed.  The device arithmetic is exactly that
+// of the device-buffer call, so the results are bit-identical.
+ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* hA,
+                     int64_t lda, const double* hB, int64_t ldb, double* hC, int64_t ldc, int N, bool fast,
+                     void* ws, size_t ws_bytes, cudaStream_t st) {
+  ozk2_status s;
+  CopyEngine* ce = copy_engine(&s);
+  if (!ce) return s;
+  Ctx c;
+  const Staging G = make_staging(m, n, k);
+  if ((s = setup(c, m, n, k, N, fast, ws, ws_bytes, st, G.total)) != OZK2_OK) return s;
+  c.timed = false;  // phases overlap with copies
+  const Layout& L = c.L;
+  double* dA = c.at<double>(L.total + G.A);
+  double* dB = c.at<double>(L.total + G.B);
+  double* dC = c.at<double>(L.total + G.C);
+  const bool a_kc = transa == OZK2_OP_N, b_kc = transb == OZK2_OP_T;
+  const Operand a = operand_a(transa, dA, a_kc ? k : m);
+  const Operand b = operand_b(transb, dB, b_kc ? k : n);
+  cudaStream_t cs = ce->cs;
+  cudaEvent_t* ev = ce->ev;
+  cudaEvent_t ev_start = ev[0], ev_b = ev[1], *ev_a = ev + 2, *ev_blk = ev + 2 + kHostChunks,
+              ev_done = ev[kHostEvents - 1];
+
+  // nothing is copied into the workspace before earlier work on `st` is done with it
+  OZK2_TRY(cudaEventRecord(ev_start, st));
+  OZK2_TRY(cudaStreamWaitEvent(cs, ev_start, 0));
+  OZK2_TRY(copy_lines_h2d(dB, hB, ldb, b_kc, n, k, 0, n, cs));
+  OZK2_TRY(cudaEventRecord(ev_b, cs));
+  const int64_t chunk = (m + kHostChunks - 1) / kHostChunks;
+  for (int q = 0; q < kHostChunks; ++q) {
+    OZK2_TRY(copy_lines_h2d(dA, hA, lda, a_kc, m, k, std::min(m, q * chunk), std::min(m, (q + 1) * chunk), cs));
+    OZK2_TRY(cudaEventRecord(ev_a[q], cs));
+  }
+
+  if ((s = zero_scratch(c, true)) != OZK2_OK) return s;
+  OZK2_TRY(cudaStreamWaitEvent(st, ev_b, 0));
+  if ((s = scale_operand(c, b, 0, int(n), side_b(L))) != OZK2_OK) return s;
+  for (int q = 0; q < kHostChunks; ++q) {
+    const int64_t i0 = std::min(m, q * chunk), i1 = std::min(m, (q + 1) * chunk);
+    OZK2_TRY(cudaStreamWaitEvent(st, ev_a[q], 0));
+    if (i1 > i0 && (s = scale_operand(c, shift_lines(a, i0), i0, int(i1 - i0), side_a(L))) != OZK2_OK) return s;
+  }
+  if ((s = bound_and_exponents(c)) != OZK2_OK) return s;
+  if ((s = phase_residues(c, a, b, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesA),
+                          c.at<uint8_t>(L.planesB))) != OZK2_OK)
+    return s;
+
+  // output row blocks: a multiple of the 128-row tile, each at least ~8 waves of tiles
+  const int64_t units = ((m + 127) / 128) * ((n + 255) / 256) * N;
+  const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(kHostBlocks, units / (8 * int64_t(c.num_sms))));
+  const int64_t rb = ((m + nblk - 1) / nblk + 127) / 128 * 128;
+  int used = 0;
+  for (int64_t i0 = 0; i0 < m; i0 += rb, ++used) {
+    const int rows = int(std::min(rb, m - i0));
+    if ((s = products_rows(c, i0, rows)) != OZK2_OK) return s;
+    if ((s = crt_rows(c, i0, rows, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.rowstat),
+                      c.at<uint8_t>(L.colstat), dC + i0 * n, n)) != OZK2_OK)
+      return s;
+    OZK2_TRY(cudaEventRecord(ev_blk[used], st));
+    OZK2_TRY(cudaStreamWaitEvent(cs, ev_blk[used], 0));
+    OZK2_TRY(cudaMemcpy2DAsync(hC + i0 * ldc, size_t(ldc) * 8, dC + i0 * n, size_t(n) * 8, size_t(n) * 8,
+                               size_t(rows), cudaMemcpyDeviceToHost, cs));
+  }
+  // the call is complete on `st` once the last block is back on the host
+  OZK2_TRY(cudaEventRecord(ev_done, cs));
+  OZK2_TRY(cudaStreamWaitEvent(st, ev_done, 0));
+  return OZK2_OK;
+}
+
+size_t host_workspace_bytes(int64_t m, int64_t n, int64_t k, int N, bool fast) {
+  return make_layout(m, n, k, N, fast).total + make_staging(m, n, k).total;
+}
+
 }  // namespace
 
 bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t planes,
-                    int64_t row_stride_bytes, int box_rows, int box_cols) {
+                    int64_t row_stride_bytes, int64_t plane_stride_bytes, int box_rows, int box_cols) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || cols < 1 || rows < 1 || planes < 1 || (box_cols != 128 && box_cols != 64)) return false;
+  if (plane_stride_bytes == 0) plane_stride_bytes = row_stride_bytes * rows;
+  if (planes > 1 && plane_stride_bytes < row_stride_bytes * rows) return false;
   const cuuint64_t dims[3] = {cuuint64_t(cols), cuuint64_t(rows), cuuint64_t(planes)};
-  const cuuint64_t strides[2] = {cuuint64_t(row_stride_bytes), cuuint64_t(row_stride_bytes) * cuuint64_t(rows)};
+  const cuuint64_t strides[2] = {cuuint64_t(row_stride_bytes), cuuint64_t(plane_stride_bytes)};
   const cuuint32_t box[3] = {cuuint32_t(box_cols), cuuint32_t(box_rows), 1u};
   const cuuint32_t estr[3] = {1u, 1u, 1u};
   const CUtensorMapSwizzle sw = (box_cols == 128) ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
@@ -488,6 +673,29 @@ ozk2_status ozk2_dgemm_ex(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, 
                           ozk2_stream_t stream) {
   return dgemm_general(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode, block_m, block_n, workspace,
                        workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ozk2_status ozk2_dgemm_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
+                            int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int num_moduli,
+                            ozk2_mode mode, void* workspace, size_t workspace_bytes, ozk2_stream_t stream) {
+  t_launches = 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!valid_mode(mode)) return OZK2_ERR_INVALID_VALUE;
+  ozk2_status s = validate(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli);
+  if (s != OZK2_OK) return s;
+  if (m == 0 || n == 0) return OZK2_OK;
+  if (k == 0) {  // C = 0 once earlier work on the stream (which may target C) is done
+    if (cudaStreamSynchronize(st) != cudaSuccess) return OZK2_ERR_CUDA;
+    for (int64_t i = 0; i < m; ++i) std::memset(C + i * ldc, 0, size_t(n) * 8);
+    return OZK2_OK;
+  }
+  return run_host(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode == OZK2_MODE_FAST, workspace,
+                  workspace_bytes, st);
+}
+
+size_t ozk2_workspace_size_host(int64_t m, int64_t n, int64_t k, int num_moduli, ozk2_mode mode) {
+  if (check_sizes(m, n, k, num_moduli) != OZK2_OK || !valid_mode(mode)) return 0;
+  return host_workspace_bytes(m, n, k, num_moduli, mode == OZK2_MODE_FAST);
 }
 
 size_t ozk2_workspace_size(int64_t m, int64_t n, int64_t k, int num_moduli) {

@@ -529,8 +529,8 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.flags = g.flags;
 
   CUtensorMap ta, tb;
-  if (!encode_fp8_map(&ta, a, g.k, g.m, planes_a, lda8, BM, BK)) return cudaErrorInvalidValue;
-  if (!encode_fp8_map(&tb, b, g.k, g.n, planes_b, ldb8, BN, BK)) return cudaErrorInvalidValue;
+  if (!encode_fp8_map(&ta, a, g.k, g.m, planes_a, lda8, g.plane_stride_a, BM, BK)) return cudaErrorInvalidValue;
+  if (!encode_fp8_map(&tb, b, g.k, g.n, planes_b, ldb8, g.plane_stride_b, BN, BK)) return cudaErrorInvalidValue;
   const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {

@@ -107,9 +107,13 @@ struct GemmArgs {
   float* D;
   int64_t ldd;
   uint32_t* flags;
+  // bytes between digit planes of A / B; 0 means rows * row stride (packed planes).  A
+  // row block of a larger plane set passes the full set's plane stride.
+  int64_t plane_stride_a;
+  int64_t plane_stride_b;
 };
-// A operand: `planes_a` digit planes (K-major, rows x k bytes, row stride lda8 bytes,
-// plane stride rows * lda8); B operand the same with n rows.
+// A operand: `planes_a` digit planes (K-major, m x k bytes, row stride lda8 bytes, plane
+// stride plane_stride_a); B operand the same with n rows.
 constexpr int kMaxGemmCtas = 192;  // persistent GEMM CTAs (scratch is sized for this many)
 size_t fp8_gemm_scratch_bytes(int num_ctas);
 cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a,
@@ -124,6 +128,7 @@ cudaError_t launch_crt(const int16_t* cres, int64_t ldr, int64_t res_stride, int
 // tensor maps (api.cu)
 // Boxes of box_rows x box_cols bytes (box_cols 128 or 64, swizzled to match).
 bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows,
-                    int64_t planes, int64_t row_stride_bytes, int box_rows, int box_cols);
+                    int64_t planes, int64_t row_stride_bytes, int64_t plane_stride_bytes,
+                    int box_rows, int box_cols);
 
 }  // namespace ozk2

@@ -41,15 +41,16 @@ OP_N, OP_T = 0, 1
 MODES = {"accurate": 0, "fast": 1}
 
 
-def _operand(x, name):
-    """(op, ld) of a float64 CUDA matrix that is row-major (op N) or the transpose of a
-    row-major matrix (op T, e.g. ``Y.T``); the stored matrix is never copied."""
+def _operand(x, name, on_host=False):
+    """(op, ld) of a float64 matrix that is row-major (op N) or the transpose of a
+    row-major matrix (op T, e.g. ``Y.T``); the stored matrix is never copied.  CUDA
+    tensors, or CPU tensors with on_host."""
     if not isinstance(x, torch.Tensor) or x.dim() != 2:
         raise ValueError(f"{name} must be a 2-D torch tensor")
     if x.dtype != torch.float64:
         raise TypeError(f"{name} must be torch.float64, got {x.dtype}")
-    if not x.is_cuda:
-        raise ValueError(f"{name} must live on a CUDA device")
+    if x.is_cuda == on_host:
+        raise ValueError(f"{name} must live {'in host memory' if on_host else 'on a CUDA device'}")
     rows, cols = x.shape
     s0, s1 = x.stride()
     if (rows > 1 and s0 == 0) or (cols > 1 and s1 == 0):
@@ -129,6 +130,44 @@ def dgemm(A, B, num_moduli=12, out=None, workspace=None, mode="accurate", block=
             s = lib.ozk2_dgemm_ex(ta, tb, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(out), _ld(out), num_moduli,
                                   md, bm, bn, _ptr(workspace), 0 if workspace is None else workspace.numel(), st)
     _lib.check(s, "ozk2_dgemm")
+    return out
+
+
+def workspace_size_host(m, n, k, num_moduli=12, mode="accurate"):
+    return int(_lib.load().ozk2_workspace_size_host(m, n, k, num_moduli, _mode(mode)))
+
+
+def dgemm_host(A, B, num_moduli=12, out=None, mode="accurate", workspace=None, device=None, sync=True):
+    """C = A @ B with A, B and C in host memory (float64 CPU tensors; A and B row-major
+    or transposed views, C row-major; pinned memory lets the copies overlap the
+    kernels).  The library moves the data and pipelines the copies with the kernels on
+    ``device`` (default: the current CUDA device) and its current stream.  With
+    ``sync`` the call waits for the stream, otherwise ``out`` is complete only once the
+    stream is."""
+    ta, lda = _operand(A, "A", on_host=True)
+    tb, ldb = _operand(B, "B", on_host=True)
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError(f"inner dimensions differ: {tuple(A.shape)} @ {tuple(B.shape)}")
+    if out is None:
+        out = torch.empty((m, n), dtype=torch.float64, pin_memory=True)
+    elif out.is_cuda or out.dtype != torch.float64 or out.dim() != 2 or tuple(out.shape) != (m, n) or (
+            n > 1 and out.stride(1) != 1) or (m > 1 and out.stride(0) == 0):
+        raise ValueError("out must be a row-major float64 host tensor of shape (m, n)")
+    ldc = out.stride(0) if m > 1 else max(1, n)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if workspace is not None and (workspace.dtype != torch.uint8 or workspace.device != dev):
+        raise TypeError("workspace must be a uint8 tensor on the device")
+    lib = _lib.load()
+    with torch.cuda.device(dev):
+        st = torch.cuda.current_stream(dev)
+        s = lib.ozk2_dgemm_host(ta, tb, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(out), ldc, num_moduli, _mode(mode),
+                                _ptr(workspace), 0 if workspace is None else workspace.numel(),
+                                ctypes.c_void_p(st.cuda_stream))
+        _lib.check(s, "ozk2_dgemm_host")
+        if sync:
+            st.synchronize()
     return out
 
 

@@ -36,7 +36,8 @@ def test_header_declares_the_boundary():
     for required in ["ozk2_dgemm", "ozk2_workspace_size", "ozk2_dgemm_ws", "ozk2_status_string",
                      "ozk2_device_status", "ozk2_moduli", "ozk2_debug_fp8_gemm", "ozk2_debug_scales",
                      "ozk2_debug_residue_planes", "ozk2_debug_residue_products", "ozk2_debug_crt",
-                     "ozk2_dgemm_ex", "ozk2_workspace_size_ex", "ozk2_debug_scales_ex", "ozk2_dgemm_noalloc"]:
+                     "ozk2_dgemm_ex", "ozk2_workspace_size_ex", "ozk2_debug_scales_ex", "ozk2_dgemm_noalloc",
+                     "ozk2_dgemm_host", "ozk2_workspace_size_host"]:
         assert required in names
 
 
@@ -135,3 +136,22 @@ def test_workspace_size(lib):
         assert dominant + gemm_scratch <= ws <= dominant + gemm_scratch + 64 * 1024 + 40 * (m + n)
     # the paper's layout needs 55 GB at 16384^3, N = 12 (Sec. IV-C); this one about 23 GB
     assert lib.ozk2_workspace_size(16384, 16384, 16384, 12) < 24e9
+
+
+def test_host_entry_validation_and_size(lib):
+    null = ctypes.c_void_p(0)
+    bogus = ctypes.c_void_p(0x1000)
+    host = lib.ozk2_dgemm_host
+    assert host(0, 0, -1, 4, 4, bogus, 4, bogus, 4, bogus, 4, 12, 0, null, 0, null) == 1
+    assert host(3, 0, 4, 4, 4, bogus, 4, bogus, 4, bogus, 4, 12, 0, null, 0, null) == 1  # bad op
+    assert host(0, 0, 4, 4, 4, bogus, 4, bogus, 4, bogus, 4, 12, 5, null, 0, null) == 1  # bad mode
+    assert host(0, 0, 4, 4, 8, bogus, 4, bogus, 4, bogus, 4, 12, 0, null, 0, null) == 1  # lda < k
+    assert host(0, 0, 4, 4, 4, null, 4, bogus, 4, bogus, 4, 12, 0, null, 0, null) == 1
+    assert host(0, 0, 0, 4, 4, null, 4, null, 4, null, 4, 12, 0, null, 0, null) == 0  # empty
+    m, n, k, N = 1000, 700, 300, 12
+    for mode in (0, 1):
+        staged = 8 * (m * k + k * n + m * n)
+        ws = lib.ozk2_workspace_size_host(m, n, k, N, mode)
+        base = lib.ozk2_workspace_size_ex(m, n, k, N, mode, 0, 0)
+        assert base + staged <= ws <= base + staged + 3 * 256
+    assert lib.ozk2_workspace_size_host(m, n, k, N, 2) == 0
