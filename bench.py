@@ -52,9 +52,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--samples", type=int, default=32, help="entries checked against the exact product")
     ap.add_argument("--mode", default="accurate", choices=["accurate", "fast"], help="scaling mode")
-    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd"],
+    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd", "batched"],
                     help="dgemm: the square product above; autograd: forward + backward of "
-                         "C = A B with A 8192 x 4096, B 4096 x 4096 and upstream gradient W ~ N(0, 1)")
+                         "C = A B with A 8192 x 4096, B 4096 x 4096 and upstream gradient W ~ N(0, 1); "
+                         "batched: 512 products with m, n, k log-uniform on [64, 2048]")
     return ap.parse_args()
 
 
@@ -374,6 +375,21 @@ def run_ours(a, rank, world):
                "ms_per_step": ems,
                "path": "ozk2_dgemm_host: pinned host A, B, C; the library's copies overlap its kernels"}
         e2e["matches_device_call"] = bool(torch.equal(hC, Cdev))
+        # the link itself on this machine: one plain pinned copy each way
+        c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        dA = torch.empty_like(A)
+        c0.record(stream)
+        dA.copy_(hA, non_blocking=True)
+        c1.record(stream)
+        hA.copy_(dA, non_blocking=True)
+        c2.record(stream)
+        torch.cuda.synchronize(dev)
+        nb = hA.numel() * 8
+        e2e["link_h2d_gbs"] = nb / c0.elapsed_time(c1) / 1e6
+        e2e["link_d2h_gbs"] = nb / c1.elapsed_time(c2) / 1e6
+        e2e["copy_floor_ms"] = (hA.numel() * 8 + hB.numel() * 8) / e2e["link_h2d_gbs"] / 1e6 + \
+            hC.numel() * 8 / e2e["link_d2h_gbs"] / 1e6
+        del dA
         del hA, hB, hC, Cdev
 
     # ---- roofline of the dominant kernel (the residue-product GEMM)
@@ -477,6 +493,84 @@ def run_autograd(a, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_batched(a, rank, world):
+    """512 uneven products as one batch plan (one launch per phase), against the same
+    products issued as 512 single calls and against a CUDA graph of the plan."""
+    import torch
+
+    import paper_2603_10634_gb300 as ozk
+    from paper_2603_10634_gb300 import _lib, workloads
+
+    _lib.load()
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N = a.moduli
+    shapes = workloads.batch_shapes(512, 64, 2048, seed=0)
+    As, Bs = workloads.batch_problems(shapes, a.phi, seed=0, device=dev)
+    flops = sum(2.0 * m * n * k for (m, n, k) in shapes)
+    stream = torch.cuda.current_stream(dev)
+    plan = ozk.BatchPlan(As, Bs, num_moduli=N, mode=a.mode)
+
+    def timed(fn, steps):
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        s0.record(stream)
+        for _ in range(steps):
+            fn()
+        s1.record(stream)
+        torch.cuda.synchronize(dev)
+        return s0.elapsed_time(s1) / steps
+
+    for _ in range(a.warmup):
+        plan.execute()
+    torch.cuda.synchronize(dev)
+    launches = ozk.last_launch_count()
+    barrier(world)
+    with ClockSampler(local) as clk:
+        ms = timed(plan.execute, a.steps)
+    barrier(world)
+    ms = max_over_ranks(ms, world, dev)
+    status = plan.status()
+
+    singles = [torch.empty((m, n), dtype=torch.float64, device=dev) for (m, n, k) in shapes]
+
+    def plain():
+        for A, B, C in zip(As, Bs, singles):
+            ozk.dgemm(A, B, num_moduli=N, out=C, mode=a.mode)
+
+    plain()
+    single_launches = ozk.last_launch_count()
+    plain_ms = timed(plain, max(1, a.steps // 2))
+    same = all(torch.equal(C, D) for C, D in zip(plan.outs, singles))
+
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        plan.execute()
+        with torch.cuda.graph(graph, stream=side):
+            plan.execute()
+    stream.wait_stream(side)
+    graph_ms = timed(graph.replay, a.steps)
+    if rank == 0:
+        line = {
+            "metric": "batched emulated DGEMM TFLOP/s (sum 2mnk / t), 512 uneven products",
+            "value": world * flops / ms / 1e9, "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f8e4m3", "emulates": "f64", "data": "synthetic",
+            "config": {"workload": f"512 products, m, n, k log-uniform on [64, 2048] (seed 0), phi={a.phi}, "
+                                   f"N={N}, {a.mode} mode", "total_flop": flops,
+                       "l2": "operands (2.7 GB) larger than L2, no flush"},
+            "gpu_launches": launches * a.steps, "clocks": clk.summary(), "device_status": status,
+            "plain_calls": {"ms_per_step": plain_ms, "tflops": flops / plain_ms / 1e9, "launches": 512 * single_launches,
+                            "bit_identical": bool(same)},
+            "cuda_graph": {"ms_per_step": graph_ms, "tflops": flops / graph_ms / 1e9},
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
 def main():
     a = parse()
     rank, world = dist_init(a)
@@ -484,6 +578,8 @@ def main():
         run_reference(a, rank, world)
     elif a.workload == "autograd":
         run_autograd(a, rank, world)
+    elif a.workload == "batched":
+        run_batched(a, rank, world)
     else:
         run_ours(a, rank, world)
     if world > 1:

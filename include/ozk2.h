@@ -182,6 +182,66 @@ ozk2_status ozk2_dgemm_host(ozk2_op transa, ozk2_op transb,
  * invalid arguments. */
 size_t ozk2_workspace_size_host(int64_t m, int64_t n, int64_t k, int num_moduli, ozk2_mode mode);
 
+/*
+ * Batches of independent products C_i := A_i * B_i (row-major, as ozk2_dgemm), all with
+ * the same N and mode, of any mix of shapes.  Each phase of the method runs as ONE
+ * launch over the whole batch: the scaling, exponent, residue and CRT kernels map their
+ * blocks to problems through a descriptor table, and the two FP8 product kernels are
+ * persistent grouped GEMMs over the tiles of every problem (longest reductions first),
+ * with each problem's operand tensor maps in device memory.  Every C_i is bit-identical
+ * to ozk2_dgemm on the same inputs.  Problems with m or n = 0 are skipped; k = 0 gives
+ * C_i = 0.  This is the batching the paper's small-size results call for (Sec. V).
+ *
+ * m, n, k, A, lda, B, ldb, C, ldc are HOST arrays of `count` entries; A[i], B[i], C[i]
+ * are device pointers.
+ */
+typedef struct ozk2_batch_plan_st *ozk2_batch_plan;
+
+/* ozk2_workspace_size_batched - workspace bytes of a batch plan; 0 on invalid sizes. */
+size_t ozk2_workspace_size_batched(int count, const int64_t *m, const int64_t *n, const int64_t *k,
+                                   int num_moduli, ozk2_mode mode);
+
+/*
+ * ozk2_batch_plan_create - validates the batch, lays out its workspace, encodes every
+ * problem's descriptors on the host and enqueues their upload on `stream`.
+ *   workspace  device, 256-byte aligned, >= ozk2_workspace_size_batched bytes, reserved
+ *              for the plan until it is destroyed; NULL: the plan allocates its own.
+ * The plan records the operand pointers: executing it reads A_i, B_i and writes C_i at
+ * those addresses.  Not capturable (it copies from host memory); execute is.
+ */
+ozk2_status ozk2_batch_plan_create(ozk2_batch_plan *plan, int count,
+                                   const int64_t *m, const int64_t *n, const int64_t *k,
+                                   const double *const *A, const int64_t *lda,
+                                   const double *const *B, const int64_t *ldb,
+                                   double *const *C, const int64_t *ldc,
+                                   int num_moduli, ozk2_mode mode,
+                                   void *workspace, size_t workspace_bytes,
+                                   ozk2_stream_t stream);
+
+/* ozk2_batch_plan_execute - enqueues the whole batch on `stream` (device work only: a
+ * few memsets and one launch per phase; capturable into a CUDA graph).  Must be called
+ * on the device the plan was created on; executions of one plan must not overlap. */
+ozk2_status ozk2_batch_plan_execute(ozk2_batch_plan plan, ozk2_stream_t stream);
+
+/* ozk2_batch_plan_workspace - the plan's device workspace (for ozk2_device_status). */
+void *ozk2_batch_plan_workspace(ozk2_batch_plan plan);
+
+/* ozk2_batch_plan_destroy - waits for the descriptor upload, frees what the plan
+ * allocated.  Work already enqueued by execute must be complete if the plan owns its
+ * workspace. */
+void ozk2_batch_plan_destroy(ozk2_batch_plan plan);
+
+/* ozk2_dgemm_batched - create (on the library-owned workspace when `workspace` is
+ * NULL), execute and destroy a plan in one call. */
+ozk2_status ozk2_dgemm_batched(int count,
+                               const int64_t *m, const int64_t *n, const int64_t *k,
+                               const double *const *A, const int64_t *lda,
+                               const double *const *B, const int64_t *ldb,
+                               double *const *C, const int64_t *ldc,
+                               int num_moduli, ozk2_mode mode,
+                               void *workspace, size_t workspace_bytes,
+                               ozk2_stream_t stream);
+
 /* ozk2_status_string - a static, human-readable name for a status code. */
 const char *ozk2_status_string(ozk2_status status);
 

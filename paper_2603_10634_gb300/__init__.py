@@ -8,6 +8,9 @@ from ._lib import Ozk2Error  # noqa: F401
 from .autograd import OzakiMatmul, matmul  # noqa: F401
 from .ozk2 import (  # noqa: F401
     MODES,
+    BatchPlan,
+    dgemm_batched,
+    workspace_size_batched,
     PHASES,
     crt,
     device_status,

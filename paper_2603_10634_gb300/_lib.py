@@ -32,6 +32,14 @@ SIGNATURES = {
     "ozk2_debug_scales_ex": (c_int, [c_int, c_int, c_i64, c_i64, c_i64, c_void_p, c_i64, c_void_p, c_i64, c_int, c_int,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                      c_void_p]),
+    "ozk2_workspace_size_batched": (c_size_t, [c_int, c_void_p, c_void_p, c_void_p, c_int, c_int]),
+    "ozk2_batch_plan_create": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                       c_void_p, c_void_p, c_void_p, c_int, c_int, c_void_p, c_size_t, c_void_p]),
+    "ozk2_batch_plan_execute": (c_int, [c_void_p, c_void_p]),
+    "ozk2_batch_plan_workspace": (c_void_p, [c_void_p]),
+    "ozk2_batch_plan_destroy": (None, [c_void_p]),
+    "ozk2_dgemm_batched": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_int, c_int, c_void_p, c_size_t, c_void_p]),
     "ozk2_status_string": (ctypes.c_char_p, [c_int]),
     "ozk2_device_status": (c_int, [c_void_p, c_void_p]),
     "ozk2_moduli": (c_int, [c_int, ctypes.POINTER(ctypes.c_int32)]),

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 #include "internal.h"
 #include "ozk2.h"
@@ -629,6 +630,338 @@ size_t host_workspace_bytes(int64_t m, int64_t n, int64_t k, int N, bool fast) {
   return make_layout(m, n, k, N, fast).total + make_staging(m, n, k).total;
 }
 
+// ------------------------------------------------------------------ batches
+// A batch plan: the descriptors of every problem, uploaded once into a device workspace,
+// and the totals of each grouped launch.  Executing it issues one launch per phase for
+// the whole batch (plus one memset of the bound maxima), with no host work, so it can
+// be captured into a CUDA graph.
+struct ZeroK {
+  double* C;
+  int64_t ldc, m, n;
+};
+
+struct BatchLayout {
+  size_t flags, probs, gbound, gres, zero_begin, zero_end, scratch, total;
+};
+
+}  // namespace
+}  // namespace ozk2
+
+struct ozk2_batch_plan_st {
+  int dev = -1;
+  int N = 0;
+  bool fast = false;
+  int cnt = 0;  // problems with m, n, k > 0
+  std::vector<ozk2::ZeroK> zero_k;
+  uint8_t* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool owns_ws = false;
+  ozk2::BatchLayout L{};
+  int64_t totals[ozk2::kBatchKernels] = {};
+  int64_t units_bound = 0, units_res = 0;
+  int num_sms = 0;
+  const void* tab = nullptr;  // ozk2::Tables
+  uint8_t* host = nullptr;    // pinned copy of the uploaded descriptors
+  size_t host_bytes = 0;
+  cudaEvent_t uploaded = nullptr;
+};
+
+namespace ozk2 {
+namespace {
+
+ozk2_status validate_batch(int count, const int64_t* m, const int64_t* n, const int64_t* k, const double* const* A,
+                           const int64_t* lda, const double* const* B, const int64_t* ldb, double* const* C,
+                           const int64_t* ldc, int N, int mode) {
+  if (count < 0 || !valid_mode(mode) || N < 1 || N > kMaxModuli) return OZK2_ERR_INVALID_VALUE;
+  if (count == 0) return OZK2_OK;
+  if (!m || !n || !k || !A || !lda || !B || !ldb || !C || !ldc) return OZK2_ERR_INVALID_VALUE;
+  for (int i = 0; i < count; ++i) {
+    const ozk2_status s = validate(OZK2_OP_N, OZK2_OP_N, m[i], n[i], k[i], A[i], lda[i], B[i], ldb[i], C[i], ldc[i], N);
+    if (s != OZK2_OK) return s;
+  }
+  return OZK2_OK;
+}
+
+bool active_problem(int64_t m, int64_t n, int64_t k) { return m > 0 && n > 0 && k > 0; }
+
+// Offsets of the batch workspace; with `probs`, also the per-problem pointers (relative
+// to a null base, rebased by the caller).
+BatchLayout batch_layout(int count, const int64_t* m, const int64_t* n, const int64_t* k, int N, bool fast,
+                         std::vector<BatchProblem>* probs) {
+  BatchLayout L{};
+  const int planes = (N <= kNumSquares) ? 2 * N : 3 * N - kNumSquares;
+  int cnt = 0;
+  for (int i = 0; i < count; ++i) cnt += active_problem(m[i], n[i], k[i]) ? 1 : 0;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.flags = take(256);
+  L.probs = take(sizeof(BatchProblem) * size_t(cnt));
+  L.gbound = fast ? o : take(sizeof(GemmProblem) * size_t(cnt));
+  L.gres = take(sizeof(GemmProblem) * size_t(cnt));
+  if (probs) probs->assign(size_t(cnt), BatchProblem{});
+  auto P = [&](int j) -> BatchProblem& { return (*probs)[size_t(j)]; };
+  auto at = [](size_t off) { return reinterpret_cast<uint8_t*>(off); };
+  L.zero_begin = o;
+  for (int i = 0, j = 0; i < count; ++i) {
+    if (!active_problem(m[i], n[i], k[i])) continue;
+    const size_t R = take(4 * size_t(m[i])), S = take(4 * size_t(n[i]));
+    const size_t cm = take(8 * size_t(n[i])), cb = take(4 * size_t(n[i]));
+    if (probs) {
+      P(j).R = reinterpret_cast<float*>(at(R));
+      P(j).S = reinterpret_cast<float*>(at(S));
+      P(j).colmaxB = reinterpret_cast<unsigned long long*>(at(cm));
+      P(j).colbadB = reinterpret_cast<uint32_t*>(at(cb));
+    }
+    ++j;
+  }
+  L.zero_end = o;
+  for (int i = 0, j = 0; i < count; ++i) {
+    if (!active_problem(m[i], n[i], k[i])) continue;
+    const int64_t mi = m[i], ni = n[i], kp = ((k[i] + 31) / 32) * 32, ldr = ((ni + 7) / 8) * 8;
+    const size_t ep = take(4 * size_t(mi)), fp = take(4 * size_t(ni)), e = take(4 * size_t(mi)),
+                 f = take(4 * size_t(ni)), rs = take(size_t(mi)), cs = take(size_t(ni));
+    const size_t abar = fast ? 0 : take(size_t(mi) * kp), bbar = fast ? 0 : take(size_t(ni) * kp);
+    const size_t part = fast ? take(4 * size_t(ni) * size_t(kp / 32)) : 0;
+    const size_t pa = take(size_t(planes) * mi * kp), pb = take(size_t(planes) * ni * kp);
+    const size_t cres = take(2 * size_t(N) * mi * ldr);
+    if (probs) {
+      BatchProblem& q = P(j);
+      q.m = int(mi);
+      q.n = int(ni);
+      q.k = int(k[i]);
+      q.kp = int(kp);
+      q.ldr = ldr;
+      q.eprime = reinterpret_cast<int32_t*>(at(ep));
+      q.fprime = reinterpret_cast<int32_t*>(at(fp));
+      q.e = reinterpret_cast<int32_t*>(at(e));
+      q.f = reinterpret_cast<int32_t*>(at(f));
+      q.rowstat = at(rs);
+      q.colstat = at(cs);
+      q.Abar = fast ? nullptr : at(abar);
+      q.BbarT = fast ? nullptr : at(bbar);
+      q.partB = fast ? reinterpret_cast<float*>(at(part)) : nullptr;
+      q.planesA = at(pa);
+      q.planesB = at(pb);
+      q.cres = reinterpret_cast<int16_t*>(at(cres));
+    }
+    ++j;
+  }
+  L.scratch = take(fp8_gemm_scratch_bytes(kMaxGemmCtas));
+  L.total = o;
+  return L;
+}
+
+template <typename T>
+T* rebase(T* rel, uint8_t* base) {
+  return rel ? reinterpret_cast<T*>(base + reinterpret_cast<uintptr_t>(rel)) : nullptr;
+}
+
+void destroy_plan(ozk2_batch_plan plan) {
+  if (!plan) return;
+  if (plan->uploaded) {
+    cudaEventSynchronize(plan->uploaded);
+    cudaEventDestroy(plan->uploaded);
+  }
+  if (plan->host) cudaFreeHost(plan->host);
+  if (plan->owns_ws && plan->ws) cudaFree(plan->ws);
+  delete plan;
+}
+
+// Builds the plan and enqueues the descriptor upload on `st`.  ws == nullptr with
+// use_owned: the library-owned workspace; ws == nullptr otherwise: a private allocation.
+ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                        const double* const* A, const int64_t* lda, const double* const* B, const int64_t* ldb,
+                        double* const* C, const int64_t* ldc, int N, int mode, void* ws, size_t ws_bytes,
+                        bool use_owned, cudaStream_t st) {
+  if (!out) return OZK2_ERR_INVALID_VALUE;
+  *out = nullptr;
+  ozk2_status s = validate_batch(count, m, n, k, A, lda, B, ldb, C, ldc, N, mode);
+  if (s != OZK2_OK) return s;
+  int sms = 0;
+  if (!device_info(&sms)) return OZK2_ERR_UNSUPPORTED;
+  if (!encode_fn()) return OZK2_ERR_CUDA;
+  const Tables* tab = tables_for(N);
+  if (!tab) return OZK2_ERR_INTERNAL;
+  const bool fast = mode == OZK2_MODE_FAST;
+  ozk2_batch_plan plan = new ozk2_batch_plan_st;
+  cudaGetDevice(&plan->dev);
+  plan->N = N;
+  plan->fast = fast;
+  plan->num_sms = sms;
+  plan->tab = tab;
+  for (int i = 0; i < count; ++i)
+    if (m[i] > 0 && n[i] > 0 && k[i] == 0) plan->zero_k.push_back(ZeroK{C[i], ldc[i], m[i], n[i]});
+  std::vector<BatchProblem> probs;
+  plan->L = batch_layout(count, m, n, k, N, fast, &probs);
+  plan->cnt = int(probs.size());
+  const BatchLayout& L = plan->L;
+  if (ws) {
+    if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) {
+      destroy_plan(plan);
+      return OZK2_ERR_INVALID_VALUE;
+    }
+    plan->ws = static_cast<uint8_t*>(ws);
+  } else if (use_owned) {
+    ozk2_status err = OZK2_OK;
+    plan->ws = owned_workspace(L.total, &err);
+    if (!plan->ws) {
+      destroy_plan(plan);
+      return err;
+    }
+  } else {
+    void* p = nullptr;
+    if (cudaMalloc(&p, L.total) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_plan(plan);
+      return OZK2_ERR_ALLOC;
+    }
+    plan->ws = static_cast<uint8_t*>(p);
+    plan->owns_ws = true;
+  }
+  plan->ws_bytes = L.total;
+  uint8_t* base = plan->ws;
+  // operands, pointers, block prefixes; GEMM problems sorted by k (longest units first)
+  std::vector<int> order;
+  int64_t running[kBatchKernels] = {};
+  for (int i = 0, j = 0; i < count; ++i) {
+    if (!active_problem(m[i], n[i], k[i])) continue;
+    BatchProblem& q = probs[size_t(j)];
+    q.A = A[i];
+    q.lda = lda[i];
+    q.B = B[i];
+    q.ldb = ldb[i];
+    q.C = C[i];
+    q.ldc = ldc[i];
+    q.R = rebase(q.R, base);
+    q.S = rebase(q.S, base);
+    q.colmaxB = rebase(q.colmaxB, base);
+    q.colbadB = rebase(q.colbadB, base);
+    q.eprime = rebase(q.eprime, base);
+    q.fprime = rebase(q.fprime, base);
+    q.e = rebase(q.e, base);
+    q.f = rebase(q.f, base);
+    q.rowstat = rebase(q.rowstat, base);
+    q.colstat = rebase(q.colstat, base);
+    q.Abar = rebase(q.Abar, base);
+    q.BbarT = rebase(q.BbarT, base);
+    q.partB = rebase(q.partB, base);
+    q.planesA = rebase(q.planesA, base);
+    q.planesB = rebase(q.planesB, base);
+    q.cres = rebase(q.cres, base);
+    batch_block_counts(q.m, q.n, q.k, q.kp, fast, q.nblocks);
+    for (int w = 0; w < kBatchKernels; ++w) {
+      q.first_block[w] = running[w];
+      running[w] += q.nblocks[w];
+    }
+    order.push_back(j);
+    ++j;
+  }
+  for (int w = 0; w < kBatchKernels; ++w) plan->totals[w] = running[w];
+  std::stable_sort(order.begin(), order.end(), [&probs](int a, int b) { return probs[a].k > probs[b].k; });
+  std::vector<GemmProblem> gres(probs.size()), gbound(fast ? 0 : probs.size());
+  int64_t ures = 0, ubound = 0;
+  for (size_t r = 0; r < order.size(); ++r) {
+    const BatchProblem& q = probs[size_t(order[r])];
+    GemmProblem& g = gres[r];
+    std::memset(&g, 0, sizeof(g));
+    if (!encode_gemm_problem(&g, q.planesA, q.planesB, q.kp, tab->mt.num_planes, q.m, q.n, q.k)) {
+      destroy_plan(plan);
+      return OZK2_ERR_INTERNAL;
+    }
+    // the products of one problem are addressed like those of a single call, but the
+    // planes of the B operand have n rows: the map was encoded with the packed strides
+    g.unit_start = ures;
+    g.cres = q.cres;
+    g.ldr = q.ldr;
+    g.res_stride = int64_t(q.m) * q.ldr;
+    ures += fp8_gemm_units(kModeResidue, q.m, q.n, N);
+    if (!fast) {
+      GemmProblem& b = gbound[r];
+      std::memset(&b, 0, sizeof(b));
+      if (!encode_gemm_problem(&b, q.Abar, q.BbarT, q.kp, 1, q.m, q.n, q.k)) {
+        destroy_plan(plan);
+        return OZK2_ERR_INTERNAL;
+      }
+      b.unit_start = ubound;
+      b.factor = bound_factor_f32(q.k);
+      b.R = q.R;
+      b.S = q.S;
+      ubound += fp8_gemm_units(kModeBound, q.m, q.n, N);
+    }
+  }
+  plan->units_res = ures;
+  plan->units_bound = ubound;
+  if (plan->cnt > 0) {
+    if (ures > 0x7FFFFFFFll) {
+      destroy_plan(plan);
+      return OZK2_ERR_UNSUPPORTED;
+    }
+    // one pinned staging copy of everything the device reads: problems, then the maps
+    const size_t nb = (L.gres - L.probs) + sizeof(GemmProblem) * probs.size();
+    if (cudaMallocHost(reinterpret_cast<void**>(&plan->host), nb) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->uploaded, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_plan(plan);
+      return OZK2_ERR_ALLOC;
+    }
+    plan->host_bytes = nb;
+    std::memset(plan->host, 0, nb);
+    std::memcpy(plan->host, probs.data(), sizeof(BatchProblem) * probs.size());
+    if (!fast) std::memcpy(plan->host + (L.gbound - L.probs), gbound.data(), sizeof(GemmProblem) * gbound.size());
+    std::memcpy(plan->host + (L.gres - L.probs), gres.data(), sizeof(GemmProblem) * gres.size());
+    if (cudaMemcpyAsync(base + L.probs, plan->host, nb, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaEventRecord(plan->uploaded, st) != cudaSuccess) {
+      destroy_plan(plan);
+      return OZK2_ERR_CUDA;
+    }
+  }
+  *out = plan;
+  return OZK2_OK;
+}
+
+ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
+  t_launches = 0;
+  if (!plan) return OZK2_ERR_INVALID_VALUE;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != plan->dev) return OZK2_ERR_INVALID_VALUE;
+  for (const ZeroK& z : plan->zero_k)
+    OZK2_TRY(cudaMemset2DAsync(z.C, size_t(z.ldc) * 8, 0, size_t(z.n) * 8, size_t(z.m), st));
+  if (plan->cnt == 0) return OZK2_OK;
+  const BatchLayout& L = plan->L;
+  const Tables* tab = static_cast<const Tables*>(plan->tab);
+  uint8_t* ws = plan->ws;
+  const BatchProblem* probs = reinterpret_cast<const BatchProblem*>(ws + L.probs);
+  uint32_t* flags = reinterpret_cast<uint32_t*>(ws + L.flags);
+  OZK2_TRY(cudaMemsetAsync(ws + L.flags, 0, 256, st));
+  OZK2_TRY(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, st));
+  OZK2_TRY(launch_scale_batch(probs, plan->cnt, plan->totals, plan->fast, flags, st));
+  t_launches += plan->fast ? 4 : 3;
+  GemmArgs g{};
+  g.num_sms = plan->num_sms;
+  g.flags = flags;
+  if (!plan->fast) {
+    g.mode = kModeBound;
+    OZK2_TRY(launch_fp8_gemm_grouped(g, reinterpret_cast<const GemmProblem*>(ws + L.gbound), plan->cnt,
+                                     plan->units_bound, st));
+    t_launches += 1;
+  }
+  OZK2_TRY(launch_exponents_batch(probs, plan->cnt, plan->totals[kBkExponents], tab->pprime, delta_f32(), st));
+  OZK2_TRY(launch_residues_batch(probs, plan->cnt, plan->totals[kBkResidRows], plan->totals[kBkResidCols], tab->mt,
+                                 flags, st));
+  g.mode = kModeResidue;
+  g.mt = &tab->mt;
+  g.scratch = reinterpret_cast<uint32_t*>(ws + L.scratch);
+  OZK2_TRY(launch_fp8_gemm_grouped(g, reinterpret_cast<const GemmProblem*>(ws + L.gres), plan->cnt, plan->units_res,
+                                   st));
+  OZK2_TRY(launch_crt_batch(probs, plan->cnt, plan->totals[kBkCrt], tab->ct, st));
+  t_launches += 5;
+  return OZK2_OK;
+}
+
 }  // namespace
 
 bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t planes,
@@ -696,6 +1029,48 @@ ozk2_status ozk2_dgemm_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n
 size_t ozk2_workspace_size_host(int64_t m, int64_t n, int64_t k, int num_moduli, ozk2_mode mode) {
   if (check_sizes(m, n, k, num_moduli) != OZK2_OK || !valid_mode(mode)) return 0;
   return host_workspace_bytes(m, n, k, num_moduli, mode == OZK2_MODE_FAST);
+}
+
+size_t ozk2_workspace_size_batched(int count, const int64_t* m, const int64_t* n, const int64_t* k, int num_moduli,
+                                   ozk2_mode mode) {
+  if (count < 0 || !valid_mode(mode) || num_moduli < 1 || num_moduli > kMaxModuli) return 0;
+  if (count > 0 && (!m || !n || !k)) return 0;
+  for (int i = 0; i < count; ++i)
+    if (check_sizes(m[i], n[i], k[i], num_moduli) != OZK2_OK) return 0;
+  return batch_layout(count, m, n, k, num_moduli, mode == OZK2_MODE_FAST, nullptr).total;
+}
+
+ozk2_status ozk2_batch_plan_create(ozk2_batch_plan* plan, int count, const int64_t* m, const int64_t* n,
+                                   const int64_t* k, const double* const* A, const int64_t* lda,
+                                   const double* const* B, const int64_t* ldb, double* const* C,
+                                   const int64_t* ldc, int num_moduli, ozk2_mode mode, void* workspace,
+                                   size_t workspace_bytes, ozk2_stream_t stream) {
+  return create_plan(plan, count, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode, workspace, workspace_bytes,
+                     false, reinterpret_cast<cudaStream_t>(stream));
+}
+
+ozk2_status ozk2_batch_plan_execute(ozk2_batch_plan plan, ozk2_stream_t stream) {
+  return execute_plan(plan, reinterpret_cast<cudaStream_t>(stream));
+}
+
+void* ozk2_batch_plan_workspace(ozk2_batch_plan plan) { return plan ? plan->ws : nullptr; }
+
+void ozk2_batch_plan_destroy(ozk2_batch_plan plan) { destroy_plan(plan); }
+
+ozk2_status ozk2_dgemm_batched(int count, const int64_t* m, const int64_t* n, const int64_t* k,
+                               const double* const* A, const int64_t* lda, const double* const* B,
+                               const int64_t* ldb, double* const* C, const int64_t* ldc, int num_moduli,
+                               ozk2_mode mode, void* workspace, size_t workspace_bytes, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ozk2_status s = validate_batch(count, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode);
+  if (s != OZK2_OK || count == 0) return s;
+  ozk2_batch_plan plan = nullptr;
+  s = create_plan(&plan, count, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode, workspace,
+                              workspace_bytes, true, st);
+  if (s != OZK2_OK) return s;
+  s = execute_plan(plan, st);
+  destroy_plan(plan);  // waits for the descriptor upload only
+  return s;
 }
 
 size_t ozk2_workspace_size(int64_t m, int64_t n, int64_t k, int num_moduli) {

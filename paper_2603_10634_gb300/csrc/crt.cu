@@ -119,17 +119,16 @@ __host__ __device__ constexpr int limbs_for(int N) { return N <= 13 ? 4 : (N <= 
 // Thread (row i, 2 consecutive columns).  One instance per N, so the modulus loop is
 // unrolled and the N residue loads of a thread can be issued together.
 template <int N>
-__global__ void __launch_bounds__(256, 2)
-    crt_kernel(const int16_t* __restrict__ cres, int64_t ldr, int64_t rstride, int m, int n,
-               const int32_t* __restrict__ e, const int32_t* __restrict__ f,
-               const uint8_t* __restrict__ rowstat, const uint8_t* __restrict__ colstat,
-               double* __restrict__ C, int64_t ldc, const __grid_constant__ CrtTable ct) {
+__device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64_t ldr, int64_t rstride, int m,
+                                         int n, const int32_t* __restrict__ e, const int32_t* __restrict__ f,
+                                         const uint8_t* __restrict__ rowstat, const uint8_t* __restrict__ colstat,
+                                         double* __restrict__ C, int64_t ldc, const CrtTable& ct, int64_t vblock,
+                                         int64_t vgrid) {
   constexpr int L = limbs_for(N);
   constexpr int L16 = 2 * L;
   const int nq = (n + 1) >> 1;
   const int64_t total = static_cast<int64_t>(m) * nq;
-  for (int64_t it = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; it < total;
-       it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+  for (int64_t it = vblock * blockDim.x + threadIdx.x; it < total; it += vgrid * blockDim.x) {
     const int i = static_cast<int>(it / nq);
     const int j0 = static_cast<int>(it % nq) * 2;
     const int16_t* src = cres + static_cast<int64_t>(i) * ldr + j0;
@@ -182,6 +181,34 @@ __global__ void __launch_bounds__(256, 2)
 }
 
 template <int N>
+__global__ void __launch_bounds__(256, 2)
+    crt_kernel(const int16_t* __restrict__ cres, int64_t ldr, int64_t rstride, int m, int n,
+               const int32_t* __restrict__ e, const int32_t* __restrict__ f,
+               const uint8_t* __restrict__ rowstat, const uint8_t* __restrict__ colstat,
+               double* __restrict__ C, int64_t ldc, const __grid_constant__ CrtTable ct) {
+  crt_body<N>(cres, ldr, rstride, m, n, e, f, rowstat, colstat, C, ldc, ct, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int64_t b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].first_block[kBkCrt] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256, 2)
+    crt_batch(const BatchProblem* __restrict__ probs, int count, const __grid_constant__ CrtTable ct) {
+  const int p = batch_problem(probs, count, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  crt_body<N>(P.cres, P.ldr, static_cast<int64_t>(P.m) * P.ldr, P.m, P.n, P.e, P.f, P.rowstat, P.colstat, P.C,
+              P.ldc, ct, blockIdx.x - P.first_block[kBkCrt], P.nblocks[kBkCrt]);
+}
+
+template <int N>
 cudaError_t launch_N(const int16_t* cres, int64_t ldr, int64_t rs, int m, int n, const int32_t* e,
                      const int32_t* f, const uint8_t* rowstat, const uint8_t* colstat, double* C,
                      int64_t ldc, const CrtTable& ct, cudaStream_t st) {
@@ -196,7 +223,30 @@ cudaError_t launch_N(const int16_t* cres, int64_t ldr, int64_t rs, int m, int n,
   return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t launch_batch_N(const BatchProblem* probs, int count, int64_t blocks, const CrtTable& ct,
+                           cudaStream_t st) {
+  crt_batch<N><<<static_cast<unsigned>(blocks), 256, 0, st>>>(probs, count, ct);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_crt_batch(const BatchProblem* probs, int count, int64_t total_blocks, const CrtTable& ct,
+                             cudaStream_t st) {
+  if (ct.limbs > limbs_for(ct.N) || total_blocks < 1 || total_blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  switch (ct.N) {
+#define OZK2_CASE(nn) \
+  case nn:            \
+    return launch_batch_N<nn>(probs, count, total_blocks, ct, st);
+    OZK2_CASE(1) OZK2_CASE(2) OZK2_CASE(3) OZK2_CASE(4) OZK2_CASE(5) OZK2_CASE(6) OZK2_CASE(7)
+    OZK2_CASE(8) OZK2_CASE(9) OZK2_CASE(10) OZK2_CASE(11) OZK2_CASE(12) OZK2_CASE(13) OZK2_CASE(14)
+    OZK2_CASE(15) OZK2_CASE(16) OZK2_CASE(17) OZK2_CASE(18) OZK2_CASE(19) OZK2_CASE(20)
+#undef OZK2_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_crt(const int16_t* cres, int64_t ldr, int64_t res_stride, int m, int n,
                        const int32_t* e, const int32_t* f, const uint8_t* rowstat,

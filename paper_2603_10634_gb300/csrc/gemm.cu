@@ -34,6 +34,8 @@
 // Every wait is bounded (device.cuh); a wait that gives up raises a CTA-wide abort
 // flag and the global timeout flag, drains the copies and products this CTA has in
 // flight, frees TMEM and returns.
+#include <cstring>
+
 #include "device.cuh"
 
 namespace ozk2 {
@@ -79,16 +81,79 @@ struct GemmParams {
   uint32_t* flags;
 };
 
-__device__ __forceinline__ void decode_unit(const GemmParams& P, int u, int& mod, int& tm, int& tn) {
-  mod = u / P.tiles;
-  const int t = u - mod * P.tiles;
-  const int per_group = kGroupM * P.tiles_n;
+__device__ __forceinline__ void decode_unit(int tiles_m, int tiles_n, int tiles, int u, int& mod, int& tm,
+                                            int& tn) {
+  mod = u / tiles;
+  const int t = u - mod * tiles;
+  const int per_group = kGroupM * tiles_n;
   const int g = t / per_group;
   const int first_m = g * kGroupM;
-  const int gsz = min(P.tiles_m - first_m, kGroupM);
+  const int gsz = min(tiles_m - first_m, kGroupM);
   const int r = t - g * per_group;
   tm = first_m + r % gsz;
   tn = r / gsz;
+}
+
+// Everything a role needs about one unit (a tile of one modulus of one problem).
+struct UnitCtx {
+  const CUtensorMap* ta;
+  const CUtensorMap* tb;
+  int m, n, k;
+  int mod, tm, tn;
+  int prob;
+  int16_t* cres;
+  int64_t ldr, res_stride;
+  float factor;
+  float* R;
+  float* S;
+};
+
+template <bool GROUPED>
+__device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensorMap* tmA, const CUtensorMap* tmB,
+                                             const GemmProblem* __restrict__ probs, int nprobs, int u,
+                                             UnitCtx& c) {
+  if constexpr (!GROUPED) {
+    c.ta = tmA;
+    c.tb = tmB;
+    c.m = P.m;
+    c.n = P.n;
+    c.k = P.k;
+    c.prob = 0;
+    decode_unit(P.tiles_m, P.tiles_n, P.tiles, u, c.mod, c.tm, c.tn);
+    c.cres = P.cres;
+    c.ldr = P.ldr;
+    c.res_stride = P.res_stride;
+    c.factor = P.factor;
+    c.R = P.R;
+    c.S = P.S;
+  } else {
+    int lo = 0, hi = nprobs - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (probs[mid].unit_start <= u) lo = mid;
+      else hi = mid - 1;
+    }
+    const GemmProblem& G = probs[lo];
+    c.ta = &G.ta;
+    c.tb = &G.tb;
+    c.m = G.m;
+    c.n = G.n;
+    c.k = G.k;
+    c.prob = lo;
+    decode_unit(G.tiles_m, G.tiles_n, G.tiles, static_cast<int>(u - G.unit_start), c.mod, c.tm, c.tn);
+    c.cres = G.cres;
+    c.ldr = G.ldr;
+    c.res_stride = G.res_stride;
+    c.factor = G.factor;
+    c.R = G.R;
+    c.S = G.S;
+  }
+}
+
+// Tensor maps written to global memory before the launch: order the tensormap proxy's
+// reads of this map after the generic writes.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
+  asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 
 // Round structure of a unit.
@@ -99,17 +164,17 @@ struct UnitPlan {
 };
 
 template <int MODE>
-__device__ __forceinline__ UnitPlan plan_of(const GemmParams& P, int mod) {
+__device__ __forceinline__ UnitPlan plan_of(int k, int mod) {
   UnitPlan u;
   if (MODE == kModeResidue) {
     const bool square = mod < kNumSquares;
     u.chunk_len = square ? kChunkSquare : kChunkKaratsuba;
     u.nphases = square ? 1 : 2;
   } else {
-    u.chunk_len = ((P.k + BK - 1) / BK) * BK;
+    u.chunk_len = ((k + BK - 1) / BK) * BK;
     u.nphases = 1;
   }
-  u.nchunks = (P.k + u.chunk_len - 1) / u.chunk_len;
+  u.nchunks = (k + u.chunk_len - 1) / u.chunk_len;
   return u;
 }
 
@@ -198,10 +263,11 @@ __device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int 
   }
 }
 
-template <int MODE>
+// GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).
+template <int MODE, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                    const __grid_constant__ GemmParams prm) {
+                    const __grid_constant__ GemmParams prm, const GemmProblem* __restrict__ probs, int nprobs) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;
@@ -227,7 +293,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     *abort_flag = 0;
     fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
+  if (!GROUPED && warp == 0 && lane == 0) {
     tma_prefetch_map(&tmA);
     tma_prefetch_map(&tmB);
   }
@@ -247,13 +313,20 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       uint32_t issued = 0, issued_phase = 0;
       bool ok = true;
+      int last_prob = -1;
       for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
-        int mod, tm, tn;
-        decode_unit(prm, u, mod, tm, tn);
-        const UnitPlan up = plan_of<MODE>(prm, mod);
+        UnitCtx uc;
+        resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
+        if (GROUPED && uc.prob != last_prob) {
+          tensormap_acquire(uc.ta);
+          tensormap_acquire(uc.tb);
+          last_prob = uc.prob;
+        }
+        const int mod = uc.mod;
+        const UnitPlan up = plan_of<MODE>(uc.k, mod);
         for (int c = 0; ok && c < up.nchunks; ++c) {
           const int k0 = c * up.chunk_len;
-          const int ksteps = (min(prm.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
+          const int ksteps = (min(uc.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
           for (int ph = 0; ok && ph < up.nphases; ++ph) {
             const int np = num_products<MODE>(mod, ph);
             for (int s = 0; ok && s < ksteps; ++s) {
@@ -267,8 +340,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 product_of<MODE>(mod, ph, x, pa, pb, acc, first);
                 uint8_t* dst = tiles + stage * kStageBytes;
                 mbar_arrive_expect_tx(full + stage, kStageBytes);
-                tma_load_3d(dst, &tmA, full + stage, k0 + s * BK, tm * BM, pa);
-                tma_load_3d(dst + kATileBytes, &tmB, full + stage, k0 + s * BK, tn * BN, pb);
+                tma_load_3d(dst, uc.ta, full + stage, k0 + s * BK, uc.tm * BM, pa);
+                tma_load_3d(dst + kATileBytes, uc.tb, full + stage, k0 + s * BK, uc.tn * BN, pb);
                 issued |= 1u << stage;
                 issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                 if (++stage == kStages) {
@@ -296,12 +369,13 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0, rc = 0;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
-        int mod, tm, tn;
-        decode_unit(prm, u, mod, tm, tn);
-        const UnitPlan up = plan_of<MODE>(prm, mod);
+        UnitCtx uc;
+        resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
+        const int mod = uc.mod;
+        const UnitPlan up = plan_of<MODE>(uc.k, mod);
         for (int c = 0; ok && c < up.nchunks; ++c) {
           const int k0 = c * up.chunk_len;
-          const int ksteps = (min(prm.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
+          const int ksteps = (min(uc.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
           for (int ph = 0; ok && ph < up.nphases; ++ph) {
             if (!mbar_wait_bounded(tempty, (rc & 1u) ^ 1u, abort_flag)) {
               ok = false;
@@ -357,10 +431,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t rc = 0;
     bool ok = true;
     for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
-      int mod, tm, tn;
-      decode_unit(prm, u, mod, tm, tn);
-      const UnitPlan up = plan_of<MODE>(prm, mod);
-      const int gi = tm * BM + row;
+      UnitCtx uc;
+      resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
+      const int mod = uc.mod, tn = uc.tn;
+      const UnitPlan up = plan_of<MODE>(uc.k, mod);
+      const int gi = uc.tm * BM + row;
       for (int c = 0; ok && c < up.nchunks; ++c) {
         for (int ph = 0; ok && ph < up.nphases; ++ph) {
           ok = mbar_wait_bounded(tfull, rc & 1u, abort_flag);
@@ -370,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if constexpr (MODE == kModeResidue) {
             const int p = prm.mod.p[mod], h = prm.mod.half[mod], sq = prm.mod.s[mod];
             const float ip = prm.mod.inv_p[mod];
-            int16_t* dst = prm.cres + static_cast<int64_t>(mod) * prm.res_stride + static_cast<int64_t>(gi) * prm.ldr;
+            int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
 #pragma unroll 1
             for (int cb = 0; cb < BN / 64; ++cb) {
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
@@ -418,7 +493,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   }
                 }
               }
-              if (gi < prm.m) store_residues(dst, gc, prm.n, res, c > 0, p, h);
+              if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
             }
           } else if constexpr (MODE == kModeBound) {
             float rmax = 0.0f;
@@ -431,16 +506,16 @@ __global__ void __launch_bounds__(kThreads, 1)
               float cv[32];
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
-                float cj = __fmul_ru(prm.factor, __uint_as_float(v0[j]));
-                cj = (gi < prm.m && gc + j < prm.n) ? cj : 0.0f;
+                float cj = __fmul_ru(uc.factor, __uint_as_float(v0[j]));
+                cj = (gi < uc.m && gc + j < uc.n) ? cj : 0.0f;
                 rmax = fmaxf(rmax, cj);
                 cv[j] = cj;
               }
               const float cm = warp_column_max(cv, lane);
-              if (gc + lane < prm.n && cm > 0.0f)
-                atomicMax(reinterpret_cast<int*>(prm.S) + gc + lane, __float_as_int(cm));
+              if (gc + lane < uc.n && cm > 0.0f)
+                atomicMax(reinterpret_cast<int*>(uc.S) + gc + lane, __float_as_int(cm));
             }
-            if (gi < prm.m && rmax > 0.0f) atomicMax(reinterpret_cast<int*>(prm.R) + gi, __float_as_int(rmax));
+            if (gi < uc.m && rmax > 0.0f) atomicMax(reinterpret_cast<int*>(uc.R) + gi, __float_as_int(rmax));
           } else {
 #pragma unroll 1
             for (int cb = 0; cb < BN / 64; ++cb) {
@@ -448,11 +523,11 @@ __global__ void __launch_bounds__(kThreads, 1)
               tmem_ld_32cols(tq + cb * 32, v0);
               tmem_ld_wait();
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
-              if (gi < prm.m) {
+              if (gi < uc.m) {
                 float* o = prm.D + static_cast<int64_t>(gi) * prm.ldd;
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                  if (gc + j < prm.n) o[gc + j] = __uint_as_float(v0[j]);
+                  if (gc + j < uc.n) o[gc + j] = __uint_as_float(v0[j]);
               }
             }
           }
@@ -476,20 +551,29 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int MODE>
+template <int MODE, bool GROUPED>
 cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
-                        cudaStream_t st) {
+                        const GemmProblem* probs, int nprobs, cudaStream_t st) {
   static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           static_cast<int>(kSmemBytes));
+    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
     if (err != cudaSuccess) return err;
     configured[dev] = true;
   }
-  fp8_gemm_kernel<MODE><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, prm);
+  fp8_gemm_kernel<MODE, GROUPED><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, prm, probs, nprobs);
   return cudaGetLastError();
+}
+
+void fill_mod(GemmParams& prm, const ModTable& mt) {
+  for (int l = 0; l < mt.N; ++l) {
+    prm.mod.p[l] = mt.p[l];
+    prm.mod.half[l] = mt.half[l];
+    prm.mod.s[l] = mt.s[l];
+    prm.mod.inv_p[l] = mt.inv_p[l];
+  }
 }
 
 }  // namespace
@@ -513,12 +597,7 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.res_stride = g.res_stride;
   prm.scratch = g.scratch;
   if (g.mode == kModeResidue) {
-    for (int l = 0; l < g.mt->N; ++l) {
-      prm.mod.p[l] = g.mt->p[l];
-      prm.mod.half[l] = g.mt->half[l];
-      prm.mod.s[l] = g.mt->s[l];
-      prm.mod.inv_p[l] = g.mt->inv_p[l];
-    }
+    fill_mod(prm, *g.mt);
     if (!g.scratch) return cudaErrorInvalidValue;
   }
   prm.factor = g.factor;
@@ -535,12 +614,52 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {
     case kModeResidue:
-      return launch_mode<kModeResidue>(prm, ta, tb, grid, st);
+      return launch_mode<kModeResidue, false>(prm, ta, tb, grid, nullptr, 0, st);
     case kModeBound:
-      return launch_mode<kModeBound>(prm, ta, tb, grid, st);
+      return launch_mode<kModeBound, false>(prm, ta, tb, grid, nullptr, 0, st);
     default:
-      return launch_mode<kModeRaw>(prm, ta, tb, grid, st);
+      return launch_mode<kModeRaw, false>(prm, ta, tb, grid, nullptr, 0, st);
   }
+}
+
+int64_t fp8_gemm_units(int mode, int m, int n, int N) {
+  const int64_t tiles = static_cast<int64_t>((m + BM - 1) / BM) * ((n + BN - 1) / BN);
+  return tiles * (mode == kModeResidue ? N : 1);
+}
+
+bool encode_gemm_problem(GemmProblem* gp, const uint8_t* a, const uint8_t* b, int64_t ld8, int planes, int m, int n,
+                         int k) {
+  if (!encode_fp8_map(&gp->ta, a, k, m, planes, ld8, 0, BM, BK)) return false;
+  if (!encode_fp8_map(&gp->tb, b, k, n, planes, ld8, 0, BN, BK)) return false;
+  gp->m = m;
+  gp->n = n;
+  gp->k = k;
+  gp->tiles_m = (m + BM - 1) / BM;
+  gp->tiles_n = (n + BN - 1) / BN;
+  gp->tiles = gp->tiles_m * gp->tiles_n;
+  return true;
+}
+
+cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs, int count, int64_t total_units,
+                                    cudaStream_t st) {
+  if (count < 1 || total_units < 1 || total_units > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+  if (g.mode != kModeResidue && g.mode != kModeBound) return cudaErrorInvalidValue;
+  GemmParams prm{};
+  prm.mode = g.mode;
+  prm.num_units = static_cast<int>(total_units);
+  prm.scratch = g.scratch;
+  prm.flags = g.flags;
+  if (g.mode == kModeResidue) {
+    fill_mod(prm, *g.mt);
+    if (!g.scratch) return cudaErrorInvalidValue;
+  }
+  CUtensorMap unused;
+  std::memset(&unused, 0, sizeof(unused));
+  const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
+  const int grid = prm.num_units < ctas ? prm.num_units : ctas;
+  if (g.mode == kModeResidue)
+    return launch_mode<kModeResidue, true>(prm, unused, unused, grid, probs, count, st);
+  return launch_mode<kModeBound, true>(prm, unused, unused, grid, probs, count, st);
 }
 
 }  // namespace ozk2

@@ -125,6 +125,90 @@ cudaError_t launch_crt(const int16_t* cres, int64_t ldr, int64_t res_stride, int
                        const uint8_t* colstat, double* C, int64_t ldc, const CrtTable& ct,
                        cudaStream_t st);
 
+// ---------------------------------------------------------------------------
+// Grouped launches: one launch of a kernel serves every problem of a batch.  Problem p
+// owns blocks [first_block[w], first_block[w] + nblocks[w]) of grouped launch w; a block
+// finds its problem by binary search over first_block[w].
+// ---------------------------------------------------------------------------
+enum BatchKernel {
+  kBkScaleRows = 0,  // rows of A
+  kBkColmax,         // columns of B: maxima
+  kBkScaleCols,      // columns of B: Bbar^T or partial sums of squares
+  kBkSumsq,          // columns of B: sums of squares (fast mode)
+  kBkExponents,
+  kBkResidRows,
+  kBkResidCols,
+  kBkCrt,
+  kBatchKernels
+};
+
+struct BatchProblem {
+  const double* A;
+  int64_t lda;
+  const double* B;
+  int64_t ldb;
+  double* C;
+  int64_t ldc;
+  int m, n, k, kp;
+  int64_t ldr;
+  int32_t* eprime;
+  int32_t* fprime;
+  int32_t* e;
+  int32_t* f;
+  uint8_t* rowstat;
+  uint8_t* colstat;
+  uint8_t* Abar;
+  uint8_t* BbarT;
+  float* R;
+  float* S;
+  float* partB;
+  unsigned long long* colmaxB;
+  uint32_t* colbadB;
+  uint8_t* planesA;
+  uint8_t* planesB;
+  int16_t* cres;
+  int64_t first_block[kBatchKernels];
+  int64_t nblocks[kBatchKernels];
+};
+
+// Blocks of each grouped launch for one problem (the same decomposition the
+// single-problem launchers use, without their grid caps).
+void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nblocks)[kBatchKernels]);
+
+cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64_t (&total)[kBatchKernels],
+                               bool fast, uint32_t* flags, cudaStream_t st);
+cudaError_t launch_exponents_batch(const BatchProblem* probs, int count, int64_t total_blocks, float pprime,
+                                   float delta, cudaStream_t st);
+cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t rows_blocks,
+                                  int64_t cols_blocks, const ModTable& mt, uint32_t* flags, cudaStream_t st);
+cudaError_t launch_crt_batch(const BatchProblem* probs, int count, int64_t total_blocks, const CrtTable& ct,
+                             cudaStream_t st);
+
+// One problem of a grouped GEMM launch: its operand maps and outputs.  Units (tile x
+// modulus) of all problems are numbered consecutively from unit_start.
+struct GemmProblem {  // CUtensorMap carries the 64-byte alignment TMA needs
+  CUtensorMap ta;
+  CUtensorMap tb;
+  int m, n, k;
+  int tiles_m, tiles_n, tiles;
+  int64_t unit_start;
+  int16_t* cres;
+  int64_t ldr;
+  int64_t res_stride;
+  float factor;
+  float* R;
+  float* S;
+};
+// Units of one problem in a GEMM of mode `mode` with N moduli.
+int64_t fp8_gemm_units(int mode, int m, int n, int N);
+// g supplies mode, num_sms, scratch, mt and flags; the problems (device memory, built on
+// the host with encode_gemm_problem) supply everything else.
+cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs, int count, int64_t total_units,
+                                    cudaStream_t st);
+// Fills the maps and tiling of one problem (the rest is the caller's).
+bool encode_gemm_problem(GemmProblem* gp, const uint8_t* a, const uint8_t* b, int64_t ld8, int planes, int m,
+                         int n, int k);
+
 // tensor maps (api.cu)
 // Boxes of box_rows x box_cols bytes (box_cols 128 or 64, swizzled to match).
 bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows,

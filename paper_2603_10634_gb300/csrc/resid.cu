@@ -192,16 +192,16 @@ __device__ __forceinline__ void digits_of(const float (&c)[kElems][kPieces], con
 // base + 128 g + 4 l + {0..3}, g = 0, 1, so loads and 4-byte plane stores coalesce.
 constexpr int kRowSpan = 256;
 
-__global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
-  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
-  load_table(mt, pow2_s);
+// vblock / vgrid: the block's index among, and the number of, the blocks serving this
+// operand (the warps stride over its items).
+__device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const ModTable& mt, const int16_t* pow2_s,
+                                                   int64_t vblock, int64_t vgrid) {
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
   const int nkw = (a.kp + kRowSpan - 1) / kRowSpan;
   const int64_t items = static_cast<int64_t>(a.lines) * nkw;
   bool range_err = false;
-  for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); it < items;
-       it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
+  for (int64_t it = vblock * warps_per_block + (threadIdx.x >> 5); it < items; it += vgrid * warps_per_block) {
     const int row = static_cast<int>(it / nkw);
     const int base = static_cast<int>(it % nkw) * kRowSpan;
     const double* x = a.X + static_cast<int64_t>(row) * a.ldx;
@@ -242,9 +242,8 @@ __global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a, const _
 // Columns of B.  A warp covers 8 columns x 32 consecutive h: lane 4 jj + qq takes
 // column j0 + jj, rows h0 + 8 qq .. h0 + 8 qq + 7.  Each group of four lanes writes one
 // full 32-byte sector of row j of every plane.
-__global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
-  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
-  load_table(mt, pow2_s);
+__device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const ModTable& mt, const int16_t* pow2_s,
+                                                   int64_t vblock, int64_t vgrid) {
   const int lane = threadIdx.x & 31;
   const int jj = lane >> 2, qq = lane & 3;
   const int warps_per_block = blockDim.x >> 5;
@@ -252,8 +251,7 @@ __global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a, const _
   const int nkb = a.kp / 32;
   const int64_t items = static_cast<int64_t>(ncg) * nkb;
   bool range_err = false;
-  for (int64_t it = static_cast<int64_t>(blockIdx.x) * warps_per_block + (threadIdx.x >> 5); it < items;
-       it += static_cast<int64_t>(gridDim.x) * warps_per_block) {
+  for (int64_t it = vblock * warps_per_block + (threadIdx.x >> 5); it < items; it += vgrid * warps_per_block) {
     const int hb = static_cast<int>(it / ncg);
     const int j = static_cast<int>(it % ncg) * 8 + jj;
     const bool active = j < a.lines;
@@ -286,6 +284,47 @@ __global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a, const _
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
+__global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
+  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
+  load_table(mt, pow2_s);
+  residues_rows_body(a, mt, pow2_s, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
+  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
+  load_table(mt, pow2_s);
+  residues_cols_body(a, mt, pow2_s, blockIdx.x, gridDim.x);
+}
+
+__device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].first_block[w] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Grouped: rows of every A, then (second launch) columns of every B.
+template <bool ROWS>
+__global__ void __launch_bounds__(256) residues_batch(const BatchProblem* __restrict__ probs, int count,
+                                                      uint32_t* flags, const __grid_constant__ ModTable mt) {
+  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
+  load_table(mt, pow2_s);
+  constexpr int w = ROWS ? kBkResidRows : kBkResidCols;
+  const int p = batch_problem(probs, count, w, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  const int64_t vb = blockIdx.x - P.first_block[w];
+  if constexpr (ROWS) {
+    const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.kp, flags};
+    residues_rows_body(a, mt, pow2_s, vb, P.nblocks[w]);
+  } else {
+    const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.kp, flags};
+    residues_cols_body(a, mt, pow2_s, vb, P.nblocks[w]);
+  }
+}
+
 int grid_for(int64_t warps) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -310,6 +349,15 @@ cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int
   ResidArgs a{B, ldb, n, k, kp, f, planes, static_cast<int64_t>(n) * kp, flags};
   const int64_t warps = static_cast<int64_t>((n + 7) / 8) * (kp / 32);
   residues_cols_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t rows_blocks, int64_t cols_blocks,
+                                  const ModTable& mt, uint32_t* flags, cudaStream_t st) {
+  if (rows_blocks < 1 || cols_blocks < 1 || rows_blocks > 0x7FFFFFFFll || cols_blocks > 0x7FFFFFFFll)
+    return cudaErrorInvalidValue;
+  residues_batch<true><<<static_cast<unsigned>(rows_blocks), 256, 0, st>>>(probs, count, flags, mt);
+  residues_batch<false><<<static_cast<unsigned>(cols_blocks), 256, 0, st>>>(probs, count, flags, mt);
   return cudaGetLastError();
 }
 

@@ -85,16 +85,14 @@ __device__ __forceinline__ float ru_f32_scaled(unsigned long long mag, int sh) {
 // One warp per row of A: row maximum, e'_i, row status, then Abar (m x kp bytes).
 // FAST: instead of Abar, the sum of squares s_i = sum_h RU_fp32(2^e'_i |a_ih|)^2 with
 // every addition rounded up (an upper bound of ||2^e'_i a_i||_2^2), written to sq[row].
+// vblock: the block's index among the blocks of this problem (8 rows each).
 template <bool FAST>
-__global__ void __launch_bounds__(256) scale_rows_kernel(const double* __restrict__ A, int64_t lda,
-                                                         int m, int k, int kp,
-                                                         int32_t* __restrict__ eprime,
-                                                         uint8_t* __restrict__ rowstat,
-                                                         uint8_t* __restrict__ Abar,
-                                                         float* __restrict__ sq,
-                                                         uint32_t* flags) {
+__device__ __forceinline__ void scale_rows_body(const double* __restrict__ A, int64_t lda, int m, int k, int kp,
+                                                int32_t* __restrict__ eprime, uint8_t* __restrict__ rowstat,
+                                                uint8_t* __restrict__ Abar, float* __restrict__ sq,
+                                                uint32_t* flags, int64_t vblock) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int row = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int row = static_cast<int>(vblock) * (blockDim.x >> 5) + warp;
   if (row >= m) return;
   const double* a = A + static_cast<int64_t>(row) * lda;
   unsigned long long mx = 0;
@@ -145,16 +143,24 @@ __global__ void __launch_bounds__(256) scale_rows_kernel(const double* __restric
   }
 }
 
+template <bool FAST>
+__global__ void __launch_bounds__(256) scale_rows_kernel(const double* __restrict__ A, int64_t lda, int m, int k,
+                                                         int kp, int32_t* __restrict__ eprime,
+                                                         uint8_t* __restrict__ rowstat, uint8_t* __restrict__ Abar,
+                                                         float* __restrict__ sq, uint32_t* flags) {
+  scale_rows_body<FAST>(A, lda, m, k, kp, eprime, rowstat, Abar, sq, flags, blockIdx.x);
+}
+
 constexpr int kColRows = 256;
 
-// Column maxima of |B| (as ordered IEEE bit patterns) and non-finite flags.
-__global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ B, int64_t ldb,
-                                                     int k, int n,
-                                                     unsigned long long* __restrict__ colmax,
-                                                     uint32_t* __restrict__ colbad) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// Column maxima of |B| (as ordered IEEE bit patterns) and non-finite flags.  Block
+// (bx, by): columns 256 bx .. 256 bx + 255, rows kColRows by ...
+__device__ __forceinline__ void colmax_body(const double* __restrict__ B, int64_t ldb, int k, int n,
+                                            unsigned long long* __restrict__ colmax, uint32_t* __restrict__ colbad,
+                                            int bx, int by) {
+  const int j = bx * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const int h0 = blockIdx.y * kColRows;
+  const int h0 = by * kColRows;
   const int h1 = min(k, h0 + kColRows);
   unsigned long long mx = 0;
   bool bad = false;
@@ -168,21 +174,22 @@ __global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ 
   if (bad) atomicOr(colbad + j, 1u);
 }
 
+__global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ B, int64_t ldb, int k, int n,
+                                                     unsigned long long* __restrict__ colmax,
+                                                     uint32_t* __restrict__ colbad) {
+  colmax_body(B, ldb, k, n, colmax, colbad, blockIdx.x, blockIdx.y);
+}
+
 // Bbar^T (n x kp bytes): thread (column j, 32 consecutive h) writes 32 bytes of row j.
 // FAST: instead, the partial sum of squares of the 32 elements (rounded up) goes to
 // part[hb * n + j]; sumsq_reduce_kernel adds the partials of a column in a fixed order.
 template <bool FAST>
-__global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restrict__ B, int64_t ldb,
-                                                         int k, int n, int kp,
-                                                         const unsigned long long* __restrict__ colmax,
-                                                         const uint32_t* __restrict__ colbad,
-                                                         int32_t* __restrict__ fprime,
-                                                         uint8_t* __restrict__ colstat,
-                                                         uint8_t* __restrict__ BbarT,
-                                                         float* __restrict__ part,
-                                                         uint32_t* flags) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  const int hb = blockIdx.y;
+__device__ __forceinline__ void scale_cols_body(const double* __restrict__ B, int64_t ldb, int k, int n, int kp,
+                                                const unsigned long long* __restrict__ colmax,
+                                                const uint32_t* __restrict__ colbad, int32_t* __restrict__ fprime,
+                                                uint8_t* __restrict__ colstat, uint8_t* __restrict__ BbarT,
+                                                float* __restrict__ part, uint32_t* flags, int bx, int hb) {
+  const int j = bx * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const unsigned long long mx = colmax[j];
   const bool bad = colbad[j] != 0;
@@ -226,13 +233,29 @@ __global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restric
   }
 }
 
+template <bool FAST>
+__global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restrict__ B, int64_t ldb, int k, int n,
+                                                         int kp, const unsigned long long* __restrict__ colmax,
+                                                         const uint32_t* __restrict__ colbad,
+                                                         int32_t* __restrict__ fprime, uint8_t* __restrict__ colstat,
+                                                         uint8_t* __restrict__ BbarT, float* __restrict__ part,
+                                                         uint32_t* flags) {
+  scale_cols_body<FAST>(B, ldb, k, n, kp, colmax, colbad, fprime, colstat, BbarT, part, flags, blockIdx.x,
+                        blockIdx.y);
+}
+
 // s_j = sum over blocks of part[hb][j], every addition rounded up, in block order.
-__global__ void sumsq_reduce_kernel(const float* __restrict__ part, int nblocks, int n, float* __restrict__ sq) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sumsq_body(const float* __restrict__ part, int nblocks, int n,
+                                           float* __restrict__ sq, int64_t vblock) {
+  const int j = static_cast<int>(vblock) * blockDim.x + threadIdx.x;
   if (j >= n) return;
   float acc = 0.0f;
   for (int hb = 0; hb < nblocks; ++hb) acc = __fadd_ru(acc, part[static_cast<int64_t>(hb) * n + j]);
   sq[j] = acc;
+}
+
+__global__ void sumsq_reduce_kernel(const float* __restrict__ part, int nblocks, int n, float* __restrict__ sq) {
+  sumsq_body(part, nblocks, n, sq, blockIdx.x);
 }
 
 // e = e' + floor(RD(P' + RD(delta * log2 R))) [Eq. mu-computation].  log2 is the FP32
@@ -248,13 +271,13 @@ __device__ __forceinline__ int final_exponent(int ep, uint8_t stat, float rmax, 
   return ep + static_cast<int>(floorf(t2));
 }
 
-__global__ void exponents_kernel(int m, int n, const int32_t* __restrict__ eprime,
-                                 const int32_t* __restrict__ fprime,
-                                 const uint8_t* __restrict__ rowstat,
-                                 const uint8_t* __restrict__ colstat, const float* __restrict__ R,
-                                 const float* __restrict__ S, float pprime, float delta,
-                                 int32_t* __restrict__ e, int32_t* __restrict__ f) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void exponents_body(int m, int n, const int32_t* __restrict__ eprime,
+                                               const int32_t* __restrict__ fprime,
+                                               const uint8_t* __restrict__ rowstat,
+                                               const uint8_t* __restrict__ colstat, const float* __restrict__ R,
+                                               const float* __restrict__ S, float pprime, float delta,
+                                               int32_t* __restrict__ e, int32_t* __restrict__ f, int64_t vblock) {
+  const int t = static_cast<int>(vblock) * blockDim.x + threadIdx.x;
   if (t < m) {
     e[t] = final_exponent(eprime[t], rowstat[t], R[t], pprime, delta);
   } else if (t < m + n) {
@@ -263,7 +286,109 @@ __global__ void exponents_kernel(int m, int n, const int32_t* __restrict__ eprim
   }
 }
 
+__global__ void exponents_kernel(int m, int n, const int32_t* __restrict__ eprime,
+                                 const int32_t* __restrict__ fprime, const uint8_t* __restrict__ rowstat,
+                                 const uint8_t* __restrict__ colstat, const float* __restrict__ R,
+                                 const float* __restrict__ S, float pprime, float delta, int32_t* __restrict__ e,
+                                 int32_t* __restrict__ f) {
+  exponents_body(m, n, eprime, fprime, rowstat, colstat, R, S, pprime, delta, e, f, blockIdx.x);
+}
+
+// ------------------------------------------------------------------ grouped launches
+// Problem of block `b` of grouped launch `w`: the last p with first_block[w] <= b.
+__device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].first_block[w] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <bool FAST>
+__global__ void __launch_bounds__(256) scale_rows_batch(const BatchProblem* __restrict__ probs, int count,
+                                                        uint32_t* flags) {
+  const int p = batch_problem(probs, count, kBkScaleRows, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  scale_rows_body<FAST>(P.A, P.lda, P.m, P.k, P.kp, P.eprime, P.rowstat, P.Abar, P.R, flags,
+                        blockIdx.x - P.first_block[kBkScaleRows]);
+}
+
+__global__ void __launch_bounds__(256) colmax_batch(const BatchProblem* __restrict__ probs, int count) {
+  const int p = batch_problem(probs, count, kBkColmax, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  const int64_t v = blockIdx.x - P.first_block[kBkColmax];
+  const int gx = (P.n + 255) / 256;
+  colmax_body(P.B, P.ldb, P.k, P.n, P.colmaxB, P.colbadB, static_cast<int>(v % gx), static_cast<int>(v / gx));
+}
+
+template <bool FAST>
+__global__ void __launch_bounds__(256) scale_cols_batch(const BatchProblem* __restrict__ probs, int count,
+                                                        uint32_t* flags) {
+  const int p = batch_problem(probs, count, kBkScaleCols, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  const int64_t v = blockIdx.x - P.first_block[kBkScaleCols];
+  const int gx = (P.n + 255) / 256;
+  scale_cols_body<FAST>(P.B, P.ldb, P.k, P.n, P.kp, P.colmaxB, P.colbadB, P.fprime, P.colstat, P.BbarT, P.partB,
+                        flags, static_cast<int>(v % gx), static_cast<int>(v / gx));
+}
+
+__global__ void __launch_bounds__(256) sumsq_batch(const BatchProblem* __restrict__ probs, int count) {
+  const int p = batch_problem(probs, count, kBkSumsq, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  sumsq_body(P.partB, P.kp / 32, P.n, P.S, blockIdx.x - P.first_block[kBkSumsq]);
+}
+
+__global__ void __launch_bounds__(256) exponents_batch(const BatchProblem* __restrict__ probs, int count,
+                                                       float pprime, float delta) {
+  const int p = batch_problem(probs, count, kBkExponents, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  exponents_body(P.m, P.n, P.eprime, P.fprime, P.rowstat, P.colstat, P.R, P.S, pprime, delta, P.e, P.f,
+                 blockIdx.x - P.first_block[kBkExponents]);
+}
+
+bool grid_ok(int64_t blocks) { return blocks > 0 && blocks <= 0x7FFFFFFFll; }
+
 }  // namespace
+
+void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nb)[kBatchKernels]) {
+  const int64_t gx = (n + 255) / 256;
+  nb[kBkScaleRows] = (m + 7) / 8;
+  nb[kBkColmax] = gx * ((k + kColRows - 1) / kColRows);
+  nb[kBkScaleCols] = gx * (kp / 32);
+  nb[kBkSumsq] = fast ? gx : 0;
+  nb[kBkExponents] = (static_cast<int64_t>(m) + n + 255) / 256;
+  nb[kBkResidRows] = (static_cast<int64_t>(m) * ((kp + 255) / 256) + 7) / 8;
+  nb[kBkResidCols] = (static_cast<int64_t>((n + 7) / 8) * (kp / 32) + 7) / 8;
+  nb[kBkCrt] = (static_cast<int64_t>(m) * ((n + 1) / 2) + 255) / 256;
+}
+
+cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64_t (&total)[kBatchKernels],
+                               bool fast, uint32_t* flags, cudaStream_t st) {
+  for (int w : {int(kBkScaleRows), int(kBkColmax), int(kBkScaleCols), int(kBkExponents)})
+    if (!grid_ok(total[w])) return cudaErrorInvalidValue;
+  if (fast && !grid_ok(total[kBkSumsq])) return cudaErrorInvalidValue;
+  if (fast)
+    scale_rows_batch<true><<<static_cast<unsigned>(total[kBkScaleRows]), 256, 0, st>>>(probs, count, flags);
+  else
+    scale_rows_batch<false><<<static_cast<unsigned>(total[kBkScaleRows]), 256, 0, st>>>(probs, count, flags);
+  colmax_batch<<<static_cast<unsigned>(total[kBkColmax]), 256, 0, st>>>(probs, count);
+  if (fast) {
+    scale_cols_batch<true><<<static_cast<unsigned>(total[kBkScaleCols]), 256, 0, st>>>(probs, count, flags);
+    sumsq_batch<<<static_cast<unsigned>(total[kBkSumsq]), 256, 0, st>>>(probs, count);
+  } else {
+    scale_cols_batch<false><<<static_cast<unsigned>(total[kBkScaleCols]), 256, 0, st>>>(probs, count, flags);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exponents_batch(const BatchProblem* probs, int count, int64_t total_blocks, float pprime,
+                                   float delta, cudaStream_t st) {
+  if (!grid_ok(total_blocks)) return cudaErrorInvalidValue;
+  exponents_batch<<<static_cast<unsigned>(total_blocks), 256, 0, st>>>(probs, count, pprime, delta);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scale_rows(const double* A, int64_t lda, int m, int k, int kp, int32_t* eprime,
                               uint8_t* rowstat, uint8_t* Abar, float* sq, bool fast, uint32_t* flags,

@@ -171,6 +171,105 @@ def dgemm_host(A, B, num_moduli=12, out=None, mode="accurate", workspace=None, d
     return out
 
 
+def _batch_arrays(As, Bs, outs):
+    """Host arrays (ctypes) of a batch of row-major device problems."""
+    count = len(As)
+    if len(Bs) != count or (outs is not None and len(outs) != count):
+        raise ValueError("As, Bs (and outs) must have the same length")
+    I64 = ctypes.c_int64 * count
+    P = ctypes.c_void_p * count
+    m, n, k, lda, ldb, ldc = I64(), I64(), I64(), I64(), I64(), I64()
+    pa, pb, pc = P(), P(), P()
+    dev = As[0].device if count else None
+    res = []
+    for i, (A, B) in enumerate(zip(As, Bs)):
+        _check_matrix(A, f"As[{i}]")
+        _check_matrix(B, f"Bs[{i}]")
+        if A.shape[1] != B.shape[0]:
+            raise ValueError(f"problem {i}: inner dimensions differ")
+        if A.device != dev or B.device != dev:
+            raise ValueError("every operand must be on the same device")
+        C = torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64, device=dev) if outs is None else outs[i]
+        _check_matrix(C, f"outs[{i}]")
+        if tuple(C.shape) != (A.shape[0], B.shape[1]):
+            raise ValueError(f"outs[{i}] has the wrong shape")
+        m[i], k[i], n[i] = A.shape[0], A.shape[1], B.shape[1]
+        lda[i], ldb[i], ldc[i] = _ld(A), _ld(B), _ld(C)
+        pa[i], pb[i], pc[i] = A.data_ptr(), B.data_ptr(), C.data_ptr()
+        res.append(C)
+    return count, (m, n, k, pa, lda, pb, ldb, pc, ldc), res, dev
+
+
+def workspace_size_batched(shapes, num_moduli=12, mode="accurate"):
+    """Workspace bytes of a batch of (m, n, k) shapes."""
+    count = len(shapes)
+    I64 = ctypes.c_int64 * count
+    m, n, k = I64(*[s[0] for s in shapes]), I64(*[s[1] for s in shapes]), I64(*[s[2] for s in shapes])
+    return int(_lib.load().ozk2_workspace_size_batched(count, m, n, k, num_moduli, _mode(mode)))
+
+
+class BatchPlan:
+    """A batch of independent products C_i = A_i @ B_i (row-major float64 CUDA tensors)
+    prepared once and executed with one launch per phase.  ``execute`` only enqueues
+    device work, so it can be captured into a CUDA graph.  The plan keeps references to
+    the operands and outputs it was built for."""
+
+    def __init__(self, As, Bs, num_moduli=12, outs=None, mode="accurate", workspace=None):
+        self._lib = _lib.load()
+        count, arrs, self.outs, dev = _batch_arrays(As, Bs, outs)
+        if count == 0:
+            raise ValueError("empty batch")
+        self.device = dev
+        self._keep = (list(As), list(Bs), workspace)
+        self._arrs = arrs
+        self._plan = ctypes.c_void_p(0)
+        with torch.cuda.device(dev):
+            s = self._lib.ozk2_batch_plan_create(ctypes.byref(self._plan), count, *arrs, num_moduli, _mode(mode),
+                                                 _ptr(workspace), 0 if workspace is None else workspace.numel(),
+                                                 _stream(dev))
+        _lib.check(s, "ozk2_batch_plan_create")
+
+    def execute(self):
+        with torch.cuda.device(self.device):
+            s = self._lib.ozk2_batch_plan_execute(self._plan, _stream(self.device))
+        _lib.check(s, "ozk2_batch_plan_execute")
+        return self.outs
+
+    def workspace_ptr(self):
+        return self._lib.ozk2_batch_plan_workspace(self._plan)
+
+    def status(self):
+        """Device flag status of the plan's workspace (synchronises the current stream)."""
+        s = self._lib.ozk2_device_status(ctypes.c_void_p(self.workspace_ptr()), _stream(self.device))
+        return _lib.STATUS.get(s, s)
+
+    def close(self):
+        if self._plan:
+            torch.cuda.synchronize(self.device)
+            self._lib.ozk2_batch_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dgemm_batched(As, Bs, num_moduli=12, outs=None, mode="accurate", workspace=None):
+    """[A_i @ B_i] for lists of row-major float64 CUDA tensors, one launch per phase for
+    the whole batch (ozk2_dgemm_batched)."""
+    count, arrs, res, dev = _batch_arrays(As, Bs, outs)
+    if count == 0:
+        return res
+    lib = _lib.load()
+    with torch.cuda.device(dev):
+        s = lib.ozk2_dgemm_batched(count, *arrs, num_moduli, _mode(mode), _ptr(workspace),
+                                   0 if workspace is None else workspace.numel(), _stream(dev))
+    _lib.check(s, "ozk2_dgemm_batched")
+    return res
+
+
 def device_status(workspace=None, device=None):
     """Synchronise the current stream and return (and clear) the device flag status name."""
     lib = _lib.load()

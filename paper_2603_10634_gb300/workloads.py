@@ -31,3 +31,26 @@ def normal_matrix(rows, cols, seed, device="cpu"):
 def problem(m, n, k, phi, seed=0, device="cpu"):
     """A (m x k) with seed `seed` and B (k x n) with seed `seed + 1`."""
     return phi_matrix(m, k, phi, seed, device), phi_matrix(k, n, phi, seed + 1, device)
+
+
+def batch_shapes(count=512, lo=64, hi=2048, seed=0):
+    """`count` (m, n, k) triples, each dimension log-uniform on [lo, hi] (rounded to an
+    integer), from one seeded torch generator: the uneven batch of many small products
+    the method's small-size behaviour is about."""
+    import math
+
+    g = torch.Generator()
+    g.manual_seed(int(seed))
+    u = torch.rand((count, 3), generator=g, dtype=torch.float64)
+    dims = torch.exp(math.log(lo) + u * (math.log(hi) - math.log(lo))).round().to(torch.int64)
+    return [tuple(int(x) for x in row) for row in dims.clamp(lo, hi)]
+
+
+def batch_problems(shapes, phi, seed=0, device="cpu"):
+    """Operands of a batch: problem i uses seeds seed + 2 i (A) and seed + 2 i + 1 (B)."""
+    As, Bs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A, B = problem(m, n, k, phi, seed=seed + 2 * i, device=device)
+        As.append(A)
+        Bs.append(B)
+    return As, Bs

@@ -37,7 +37,9 @@ def test_header_declares_the_boundary():
                      "ozk2_device_status", "ozk2_moduli", "ozk2_debug_fp8_gemm", "ozk2_debug_scales",
                      "ozk2_debug_residue_planes", "ozk2_debug_residue_products", "ozk2_debug_crt",
                      "ozk2_dgemm_ex", "ozk2_workspace_size_ex", "ozk2_debug_scales_ex", "ozk2_dgemm_noalloc",
-                     "ozk2_dgemm_host", "ozk2_workspace_size_host"]:
+                     "ozk2_dgemm_host", "ozk2_workspace_size_host", "ozk2_dgemm_batched",
+                     "ozk2_batch_plan_create", "ozk2_batch_plan_execute", "ozk2_batch_plan_destroy",
+                     "ozk2_workspace_size_batched"]:
         assert required in names
 
 
@@ -155,3 +157,27 @@ def test_host_entry_validation_and_size(lib):
         base = lib.ozk2_workspace_size_ex(m, n, k, N, mode, 0, 0)
         assert base + staged <= ws <= base + staged + 3 * 256
     assert lib.ozk2_workspace_size_host(m, n, k, N, 2) == 0
+
+
+def test_batch_validation_and_size(lib):
+    null = ctypes.c_void_p(0)
+    I64 = ctypes.c_int64 * 3
+    P = ctypes.c_void_p * 3
+    m, n, k = I64(10, 20, 30), I64(5, 6, 7), I64(8, 9, 10)
+    ld_ok_a, ld_ok_b = I64(8, 9, 10), I64(5, 6, 7)
+    ptr = P(0x1000, 0x2000, 0x3000)
+    batched = lib.ozk2_dgemm_batched
+    assert batched(-1, m, n, k, ptr, ld_ok_a, ptr, ld_ok_b, ptr, ld_ok_b, 12, 0, null, 0, null) == 1
+    assert batched(3, null, n, k, ptr, ld_ok_a, ptr, ld_ok_b, ptr, ld_ok_b, 12, 0, null, 0, null) == 1
+    assert batched(3, m, n, k, ptr, I64(8, 8, 10), ptr, ld_ok_b, ptr, ld_ok_b, 12, 0, null, 0, null) == 1
+    assert batched(3, m, n, k, ptr, ld_ok_a, ptr, ld_ok_b, P(0x1000, 0, 0x3000), ld_ok_b, 12, 0, null, 0,
+                   null) == 1
+    assert batched(3, m, n, k, ptr, ld_ok_a, ptr, ld_ok_b, ptr, ld_ok_b, 21, 0, null, 0, null) == 1
+    assert batched(0, null, null, null, null, null, null, null, null, null, 12, 0, null, 0, null) == 0
+    # the batch layout: per-problem arrays plus one shared GEMM scratch and descriptors
+    single = sum(lib.ozk2_workspace_size(int(m[i]), int(n[i]), int(k[i]), 12) for i in range(3))
+    scratch = 192 * 128 * 256 * 4
+    ws = lib.ozk2_workspace_size_batched(3, m, n, k, 12, 0)
+    assert single - 2 * scratch - 3 * 64 * 1024 <= ws <= single - 2 * scratch + 64 * 1024
+    assert lib.ozk2_workspace_size_batched(3, m, n, k, 12, 0) > lib.ozk2_workspace_size_batched(3, m, n, k, 12, 1)
+    assert lib.ozk2_workspace_size_batched(3, m, I64(5, -6, 7), k, 12, 0) == 0
