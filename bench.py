@@ -52,10 +52,15 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end timing")
     ap.add_argument("--samples", type=int, default=32, help="entries checked against the exact product")
     ap.add_argument("--mode", default="accurate", choices=["accurate", "fast"], help="scaling mode")
-    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd", "batched"],
+    ap.add_argument("--sizes", default="1024,4096,8192,16384", help="sweep: square sizes")
+    ap.add_argument("--phis", default="0.5,1,2", help="sweep: phi values")
+    ap.add_argument("--moduli-list", default="8,9,10,11,12,13,14,16,18,20", help="sweep: N values")
+    ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd", "batched", "sweep", "rect"],
                     help="dgemm: the square product above; autograd: forward + backward of "
                          "C = A B with A 8192 x 4096, B 4096 x 4096 and upstream gradient W ~ N(0, 1); "
-                         "batched: 512 products with m, n, k log-uniform on [64, 2048]")
+                         "batched: 512 products with m, n, k log-uniform on [64, 2048]; "
+                         "sweep: error and TFLOP/s over sizes x phi x N (one JSON line each); "
+                         "rect: 4096 x 4096 x 65536 and 65536 x 1024 x 1024")
     return ap.parse_args()
 
 
@@ -571,6 +576,133 @@ def run_batched(a, rank, world):
     plan.close()
 
 
+def exact_samples(A, B, samples, seed=7):
+    """Sampled entries (i, j) with their exact value and (|A||B|)_ij, as Python numbers."""
+    import numpy as np
+    import torch
+
+    m, n = A.shape[0], B.shape[1]
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, m, samples)
+    cols = rng.integers(0, n, samples)
+    Ar = A[torch.as_tensor(rows, device=A.device)].cpu().numpy()
+    Bc = B[:, torch.as_tensor(cols, device=A.device)].cpu().numpy()
+    out = []
+    for t in range(samples):
+        out.append((int(rows[t]), int(cols[t]), _exact_dot(Ar[t], Bc[:, t]), _exact_dot(abs(Ar[t]), abs(Bc[:, t]))))
+    return out
+
+
+def sample_error(C, ex):
+    """max over the samples of |C_ij - exact| / (|A||B|)_ij."""
+    import torch
+
+    idx_r = torch.as_tensor([e[0] for e in ex], device=C.device)
+    idx_c = torch.as_tensor([e[1] for e in ex], device=C.device)
+    vals = C[idx_r, idx_c].cpu().tolist()
+    worst = 0.0
+    for v, (_, _, (num, den), (anum, aden)) in zip(vals, ex):
+        if v != v:  # NaN
+            return float("nan")
+        cn, cd = float(v).as_integer_ratio()
+        err = abs(num * cd - cn * den) / (den * cd)
+        worst = max(worst, err / (anum / aden) if anum else 0.0)
+    return worst
+
+
+def time_calls(fn, steps, warmup, dev):
+    import torch
+
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize(dev)
+    stream = torch.cuda.current_stream(dev)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(steps):
+        fn()
+    s1.record(stream)
+    torch.cuda.synchronize(dev)
+    return s0.elapsed_time(s1) / steps
+
+
+def measure_shape(m, n, k, phi, Ns, mode, steps, warmup, samples, dev, seed=0):
+    """TFLOP/s and sampled error of the emulated product for each N in Ns, and of native
+    FP64, on one seeded instance; one dict per N plus the native figures."""
+    import torch
+
+    import paper_2603_10634_gb300 as ozk
+    from paper_2603_10634_gb300 import workloads
+
+    A, B = workloads.problem(m, n, k, phi, seed=seed, device=dev)
+    flops = 2.0 * m * n * k
+    ex = exact_samples(A, B, samples)
+    C = torch.empty((m, n), dtype=torch.float64, device=dev)
+    nat_ms = time_calls(lambda: torch.matmul(A, B, out=C), max(1, steps), 1, dev)
+    nat_err = sample_error(C, ex)
+    rows = []
+    for N in Ns:
+        ms = time_calls(lambda: ozk.dgemm(A, B, num_moduli=N, out=C, mode=mode), steps, warmup, dev)
+        err = sample_error(C, ex)
+        planes = 2 * N if N <= 6 else 3 * N - 6
+        t_roof = ((3 * N + (0 if mode == "fast" else 1)) * flops / (NOMINAL_FP8_TFLOPS * 1e12) +
+                  ((16 + (0 if mode == "fast" else 1) + planes) * (m * k + k * n) + 8 * m * n) / (NOMINAL_HBM_GBS * 1e9))
+        rows.append({"m": m, "n": n, "k": k, "phi": phi, "num_moduli": N, "mode": mode, "ms": ms,
+                     "tflops": flops / ms / 1e9, "fp8_count_roofline_frac": (flops / ms / 1e9) / (flops / t_roof / 1e12),
+                     "max_rel_err_vs_absAB": err, "native_fp64_err": nat_err,
+                     "within_2x_native": bool(err <= 2 * max(nat_err, 2.0**-53)),
+                     "bound_k_2^-52_holds": bool(err <= k * 2.0**-52), "native_fp64_tflops": flops / nat_ms / 1e9,
+                     "device_status": ozk.device_status()})
+    del A, B, C
+    torch.cuda.empty_cache()
+    return rows
+
+
+def run_sweep(a, rank, world):
+    """Error against the exact product and TFLOP/s over sizes x phi x N (one JSON line per
+    point), then the smallest N within 2x of native FP64 per (size, phi)."""
+    import torch
+
+    from paper_2603_10634_gb300 import _lib
+
+    _lib.load()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    sizes = [int(x) for x in a.sizes.split(",")]
+    phis = [float(x) for x in a.phis.split(",")]
+    Ns = [int(x) for x in a.moduli_list.split(",")]
+    best = {}
+    for size in sizes:
+        for phi in phis:
+            for r in measure_shape(size, size, size, phi, Ns, a.mode, a.steps, a.warmup, a.samples, dev):
+                print(json.dumps(r), flush=True)
+                key = (size, phi)
+                if r["within_2x_native"] and key not in best:
+                    best[key] = r
+    for (size, phi), r in best.items():
+        print(json.dumps({"smallest_N_within_2x_native": r["num_moduli"], "size": size, "phi": phi,
+                          "tflops": r["tflops"], "err": r["max_rel_err_vs_absAB"], "native_err": r["native_fp64_err"]}),
+              flush=True)
+
+
+def run_rect(a, rank, world):
+    """The long-reduction and tall-skinny shapes at the headline accuracy."""
+    import torch
+
+    from paper_2603_10634_gb300 import _lib
+
+    _lib.load()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    for (m, n, k) in [(4096, 4096, 65536), (65536, 1024, 1024)]:
+        for r in measure_shape(m, n, k, a.phi, [a.moduli], a.mode, a.steps, a.warmup, a.samples, dev):
+            print(json.dumps(r), flush=True)
+
+
 def main():
     a = parse()
     rank, world = dist_init(a)
@@ -580,6 +712,10 @@ def main():
         run_autograd(a, rank, world)
     elif a.workload == "batched":
         run_batched(a, rank, world)
+    elif a.workload == "sweep":
+        run_sweep(a, rank, world)
+    elif a.workload == "rect":
+        run_rect(a, rank, world)
     else:
         run_ours(a, rank, world)
     if world > 1:

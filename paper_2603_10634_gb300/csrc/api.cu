@@ -115,7 +115,7 @@ Operand shift_lines(const Operand& o, int64_t first) {
 
 // ------------------------------------------------------------------ workspace layout
 struct Layout {
-  int64_t kp, ldr;
+  int64_t kp, ldp, ldr;  // kp: bytes of k per row; ldp: digit-plane row pitch
   int planes;
   size_t flags, R, S, colmaxA, colbadA, colmaxB, colbadB, zero_end;
   size_t eprime, fprime, e, f, rowstat, colstat;
@@ -127,6 +127,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 Layout make_layout(int64_t m, int64_t n, int64_t k, int N, bool fast) {
   Layout L;
   L.kp = ((k + 31) / 32) * 32;
+  L.ldp = plane_pitch(L.kp);
   L.ldr = ((n + 7) / 8) * 8;
   L.planes = (N <= kNumSquares) ? 2 * N : 3 * N - kNumSquares;
   size_t o = 0;
@@ -153,8 +154,8 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N, bool fast) {
   L.BbarT = fast ? o : take(size_t(n) * L.kp);
   L.partA = fast ? take(4 * size_t(m) * (L.kp / 32)) : o;
   L.partB = fast ? take(4 * size_t(n) * (L.kp / 32)) : o;
-  L.planesA = take(size_t(L.planes) * m * L.kp);
-  L.planesB = take(size_t(L.planes) * n * L.kp);
+  L.planesA = take(size_t(L.planes) * m * L.ldp);
+  L.planesB = take(size_t(L.planes) * n * L.ldp);
   L.cres = take(2 * size_t(N) * m * L.ldr);
   L.scratch = take(fp8_gemm_scratch_bytes(kMaxGemmCtas));
   L.total = o;
@@ -316,18 +317,21 @@ ozk2_status phase_scales(Ctx& c, const Operand& a, const Operand& b, bool clear_
   return bound_and_exponents(c);
 }
 
-cudaError_t residues_operand(Ctx& c, const Operand& op, int lines, const int32_t* ex, uint8_t* planes) {
+cudaError_t residues_operand(Ctx& c, const Operand& op, int lines, const int32_t* ex, uint8_t* planes,
+                             int64_t pitch) {
   if (op.kcontig)
-    return launch_residues_rows(op.ptr, op.ld, lines, c.k, int(c.L.kp), ex, c.tab->mt, planes,
+    return launch_residues_rows(op.ptr, op.ld, lines, c.k, int(c.L.kp), pitch, ex, c.tab->mt, planes,
                                 c.at<uint32_t>(c.L.flags), c.st);
-  return launch_residues_cols(op.ptr, op.ld, c.k, lines, int(c.L.kp), ex, c.tab->mt, planes,
+  return launch_residues_cols(op.ptr, op.ld, c.k, lines, int(c.L.kp), pitch, ex, c.tab->mt, planes,
                               c.at<uint32_t>(c.L.flags), c.st);
 }
 
+// pitch: row pitch of the destination planes (0: the workspace pitch L.ldp).
 ozk2_status phase_residues(Ctx& c, const Operand& a, const Operand& b, const int32_t* e, const int32_t* f,
-                           uint8_t* planesA, uint8_t* planesB) {
-  OZK2_TRY(residues_operand(c, a, c.m, e, planesA));
-  OZK2_TRY(residues_operand(c, b, c.n, f, planesB));
+                           uint8_t* planesA, uint8_t* planesB, int64_t pitch = 0) {
+  if (pitch == 0) pitch = c.L.ldp;
+  OZK2_TRY(residues_operand(c, a, c.m, e, planesA, pitch));
+  OZK2_TRY(residues_operand(c, b, c.n, f, planesB, pitch));
   t_launches += 2;
   mark(c, 4);
   return OZK2_OK;
@@ -348,10 +352,10 @@ ozk2_status products_rows(Ctx& c, int64_t i0, int rows) {
   g.scratch = c.at<uint32_t>(L.scratch);
   g.mt = &c.tab->mt;
   g.flags = c.at<uint32_t>(L.flags);
-  g.plane_stride_a = int64_t(c.m) * L.kp;
-  g.plane_stride_b = int64_t(c.n) * L.kp;
-  OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA) + i0 * L.kp, L.kp, L.planes, c.at<uint8_t>(L.planesB), L.kp,
-                           L.planes, c.st));
+  g.plane_stride_a = int64_t(c.m) * L.ldp;
+  g.plane_stride_b = int64_t(c.n) * L.ldp;
+  OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA) + i0 * L.ldp, L.ldp, L.planes, c.at<uint8_t>(L.planesB),
+                           L.ldp, L.planes, c.st));
   t_launches += 1;
   return OZK2_OK;
 }
@@ -721,12 +725,13 @@ BatchLayout batch_layout(int count, const int64_t* m, const int64_t* n, const in
   L.zero_end = o;
   for (int i = 0, j = 0; i < count; ++i) {
     if (!active_problem(m[i], n[i], k[i])) continue;
-    const int64_t mi = m[i], ni = n[i], kp = ((k[i] + 31) / 32) * 32, ldr = ((ni + 7) / 8) * 8;
+    const int64_t mi = m[i], ni = n[i], kp = ((k[i] + 31) / 32) * 32, ldp = plane_pitch(kp),
+                  ldr = ((ni + 7) / 8) * 8;
     const size_t ep = take(4 * size_t(mi)), fp = take(4 * size_t(ni)), e = take(4 * size_t(mi)),
                  f = take(4 * size_t(ni)), rs = take(size_t(mi)), cs = take(size_t(ni));
     const size_t abar = fast ? 0 : take(size_t(mi) * kp), bbar = fast ? 0 : take(size_t(ni) * kp);
     const size_t part = fast ? take(4 * size_t(ni) * size_t(kp / 32)) : 0;
-    const size_t pa = take(size_t(planes) * mi * kp), pb = take(size_t(planes) * ni * kp);
+    const size_t pa = take(size_t(planes) * mi * ldp), pb = take(size_t(planes) * ni * ldp);
     const size_t cres = take(2 * size_t(N) * mi * ldr);
     if (probs) {
       BatchProblem& q = P(j);
@@ -734,6 +739,7 @@ BatchLayout batch_layout(int count, const int64_t* m, const int64_t* n, const in
       q.n = int(ni);
       q.k = int(k[i]);
       q.kp = int(kp);
+      q.ldp = ldp;
       q.ldr = ldr;
       q.eprime = reinterpret_cast<int32_t*>(at(ep));
       q.fprime = reinterpret_cast<int32_t*>(at(fp));
@@ -868,7 +874,7 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
     const BatchProblem& q = probs[size_t(order[r])];
     GemmProblem& g = gres[r];
     std::memset(&g, 0, sizeof(g));
-    if (!encode_gemm_problem(&g, q.planesA, q.planesB, q.kp, tab->mt.num_planes, q.m, q.n, q.k)) {
+    if (!encode_gemm_problem(&g, q.planesA, q.planesB, q.ldp, tab->mt.num_planes, q.m, q.n, q.k)) {
       destroy_plan(plan);
       return OZK2_ERR_INTERNAL;
     }
@@ -1224,7 +1230,8 @@ ozk2_status ozk2_debug_residue_planes(int64_t m, int64_t n, int64_t k, const dou
     return OZK2_ERR_INVALID_VALUE;
   Ctx c;
   if ((s = setup(c, m, n, k, num_moduli, false, nullptr, 0, st)) != OZK2_OK) return s;
-  return phase_residues(c, operand_a(OZK2_OP_N, A, lda), operand_b(OZK2_OP_N, B, ldb), e, f, planesA, planesB);
+  return phase_residues(c, operand_a(OZK2_OP_N, A, lda), operand_b(OZK2_OP_N, B, ldb), e, f, planesA, planesB,
+                        c.L.kp);  // the caller's planes are packed (pitch kp)
 }
 
 ozk2_status ozk2_debug_residue_products(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,

@@ -53,7 +53,7 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kChunkKaratsuba = 65536;  // 2^16 * 16 * 16 = 2^24
 constexpr int kChunkSquare = 32768;     // shared accumulator: 2 * 2^15 * 16 * 16 = 2^24
-constexpr int kGroupM = 8;              // tile rasterisation: bands of 8 tile rows
+constexpr int kGroupM = 16;             // tile rasterisation: bands of 16 tile rows (2048 rows of A)
 constexpr size_t kSmemBytes = 1024 + static_cast<size_t>(kStages) * kStageBytes + 256;
 
 struct EpiMod {

@@ -35,7 +35,7 @@ struct ModTable {
   int plane0[kMaxModuli];         // first digit plane of the modulus
   float inv_p[kMaxModuli];        // RN(1 / p)
   float inv_s[kMaxModuli];        // RN(1 / s)
-  float w8[kMaxModuli][7];        // 2^(8 j) mod p, symmetric representative, j = 0..6
+  float w11[kMaxModuli][5];       // 2^(11 j) mod p, symmetric representative, j = 0..4
   int16_t pow2[kMaxModuli][kPow2Table];  // 2^t mod p, symmetric representative
 };
 
@@ -49,6 +49,11 @@ struct CrtTable {
   uint32_t P[kMaxLimbs];
   uint32_t halfP[kMaxLimbs];               // P / 2 (P is even: 1024 is a modulus)
 };
+
+// Row pitch in bytes of the digit planes for kp (a multiple of 32) bytes of data per row.
+// Packed: rows padded away from power-of-two pitches measured no change in the DRAM
+// traffic of the residue products (the L2 hashes such strides well).
+__host__ __device__ inline int64_t plane_pitch(int64_t kp) { return kp; }
 
 // Host-side constant generation (moduli.cpp)
 bool build_mod_table(int N, ModTable* mt);
@@ -78,11 +83,12 @@ cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t*
                              const float* R, const float* S, float pprime, float delta,
                              int32_t* e, int32_t* f, cudaStream_t st);
 
-// resid.cu
-cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp,
+// resid.cu.  Planes: M_N planes of lines x kp bytes, row pitch ldp bytes (>= kp, a
+// multiple of 16), plane stride lines * ldp.
+cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp, int64_t ldp,
                                  const int32_t* e, const ModTable& mt, uint8_t* planes,
                                  uint32_t* flags, cudaStream_t st);
-cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp,
+cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, int64_t ldp,
                                  const int32_t* f, const ModTable& mt, uint8_t* planes,
                                  uint32_t* flags, cudaStream_t st);
 
@@ -150,6 +156,7 @@ struct BatchProblem {
   double* C;
   int64_t ldc;
   int m, n, k, kp;
+  int64_t ldp;  // digit-plane row pitch
   int64_t ldr;
   int32_t* eprime;
   int32_t* fprime;

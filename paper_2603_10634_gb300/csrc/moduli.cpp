@@ -171,7 +171,7 @@ bool build_mod_table(int N, ModTable* mt) {
     int v = 1 % p;
     for (int t = 0; t < kPow2Table; ++t) {
       mt->pow2[l][t] = static_cast<int16_t>(sym(v));
-      if (t % 8 == 0 && t / 8 < 7) mt->w8[l][t / 8] = static_cast<float>(sym(v));
+      if (t % 11 == 0 && t / 11 < 5) mt->w11[l][t / 11] = static_cast<float>(sym(v));
       v = (2 * v) % p;
     }
   }

@@ -10,12 +10,12 @@
 //
 // a' is never formed as a wide integer or a double.  With a = M 2^E (M the 53-bit
 // significand) and t = E + e: a' = M' 2^t', where M' = M >> -t, t' = 0 if t < 0 and
-// M' = M, t' = t otherwise.  M' is split once into seven signed byte pieces c_j
+// M' = M, t' = t otherwise.  M' is split once into five signed 11-bit pieces c_j
 // (exact floats), and for each modulus
-//   x = sum_j c_j w_j,   w_j = 2^(8j) mod p in [-p/2, p/2],   |x| < 2^20
+//   x = sum_j c_j w_j,   w_j = 2^(11j) mod p in [-p/2, p/2],   |x| <= 5 (2^11 - 1) 544 < 2^23
 // is formed with exact FP32 fused multiply-adds.  For odd p the exact product x (1/p)
-// (rounded once, see reduce) is within 1.4e-4 of x / p (|x| < 2^20, p >= 443), closer
-// than any half-integer can be (1/(2p) >= 4.6e-4), so q is the nearest integer to x / p
+// rounded once (see reduce) differs from x / p by at most |x| 2^-24 / p < 1/(2p), less
+// than the distance from x / p to any half-integer, so q is the nearest integer to x / p
 // and r = x - q p (one exact FMA) is the symmetric remainder with no correction step.
 // p = 1024 uses q = floor((x + 512) / 1024), exact.  No conversion instruction is used:
 // every rounding is an FP32 add of 1.5 2^23.  When t' > 0 the remainder is
@@ -33,7 +33,7 @@ namespace {
 
 constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
-constexpr int kPieces = 7;
+constexpr int kPieces = 5;  // 11-bit pieces of the 53-bit shifted significand
 constexpr int kElems = 8;  // elements per thread
 
 // Signed byte pieces of a' (as floats) and t'.
@@ -58,15 +58,15 @@ __device__ __forceinline__ void decode_element(double a, int e, float (&c)[kPiec
       tp = 0;
     }
   }
-  // byte b -> float via the bit pattern of 2^23 + b (exact), sign folded into one FMA:
-  // sg (2^23 + b) - sg 2^23 = sg b
+  // piece b (< 2^11) -> float via the bit pattern of 2^23 + b (exact), sign folded into
+  // one FMA: sg (2^23 + b) - sg 2^23 = sg b
   const uint32_t lo = static_cast<uint32_t>(Mp), hi = static_cast<uint32_t>(Mp >> 32);
   const float sg = (bits >> 63) ? -1.0f : 1.0f;
   const float off = -sg * 8388608.0f;
-  const uint32_t bytes[kPieces] = {lo & 0xFFu, (lo >> 8) & 0xFFu, (lo >> 16) & 0xFFu, lo >> 24,
-                                   hi & 0xFFu, (hi >> 8) & 0xFFu, hi >> 16};
+  const uint32_t pieces[kPieces] = {lo & 0x7FFu, (lo >> 11) & 0x7FFu, __funnelshift_r(lo, hi, 22) & 0x7FFu,
+                                    (hi >> 1) & 0x7FFu, hi >> 12};
 #pragma unroll
-  for (int j = 0; j < kPieces; ++j) c[j] = fmaf(sg, __uint_as_float(0x4B000000u | bytes[j]), off);
+  for (int j = 0; j < kPieces; ++j) c[j] = fmaf(sg, __uint_as_float(0x4B000000u | pieces[j]), off);
 }
 
 struct ModF {
@@ -78,7 +78,7 @@ struct ModF {
 // Rounding to an integer without a conversion instruction: for |y| < 2^22, y + 1.5 2^23
 // rounds (to nearest, ties to even) to an integer-valued float, and subtracting
 // 1.5 2^23 is exact.  fmaf(x, inv_p, kMagic) rounds the exact product x (1/p), so the
-// quotient estimate carries only the error of inv_p: |x| (1/p) 2^-24 < 1.4e-4 < 1/(2p).
+// quotient estimate carries only the error of inv_p: |x| (1/p) 2^-24 < 1/(2p) for |x| < 2^23.
 // Inputs are never -0 (the pieces c_j come out of an exact FMA as +0 when zero), so
 // no remainder or digit is -0 (E4M3 0x80).
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
@@ -129,9 +129,10 @@ struct ResidArgs {
   int64_t ldx;
   int lines;  // rows of A or columns of B
   int k, kp;
+  int64_t ldp;  // row pitch of a plane (bytes)
   const int32_t* exps;
   uint8_t* planes;
-  int64_t plane_stride;  // lines * kp
+  int64_t plane_stride;  // lines * ldp
   uint32_t* flags;
 };
 
@@ -146,7 +147,7 @@ __device__ __forceinline__ ModF consts_of(const ModTable& mt, int l) {
   m.p = static_cast<float>(mt.p[l]);
   m.inv_p = mt.inv_p[l];
 #pragma unroll
-  for (int j = 0; j < kPieces; ++j) m.w[j] = mt.w8[l][j];
+  for (int j = 0; j < kPieces; ++j) m.w[j] = mt.w11[l][j];
   m.pow2_modulus = (mt.p[l] == 1024);
   return m;
 }
@@ -219,7 +220,7 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const Mod
       }
     }
     const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
-    uint8_t* rowp = a.planes + static_cast<int64_t>(row) * a.kp;
+    uint8_t* rowp = a.planes + static_cast<int64_t>(row) * a.ldp;
     for (int l = 0; l < mt.N; ++l) {
       uint32_t words[3][2];
       digits_of(c, tp, mt, l, pow2_s, use_pow2, words);
@@ -268,7 +269,7 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
       any_tp |= tp[t];
     }
     const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
-    uint8_t* colp = a.planes + static_cast<int64_t>(active ? j : 0) * a.kp + h0;
+    uint8_t* colp = a.planes + static_cast<int64_t>(active ? j : 0) * a.ldp + h0;
     for (int l = 0; l < mt.N; ++l) {
       uint32_t words[3][2];
       digits_of(c, tp, mt, l, pow2_s, use_pow2, words);
@@ -317,10 +318,10 @@ __global__ void __launch_bounds__(256) residues_batch(const BatchProblem* __rest
   const BatchProblem& P = probs[p];
   const int64_t vb = blockIdx.x - P.first_block[w];
   if constexpr (ROWS) {
-    const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.kp, flags};
+    const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.ldp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.ldp, flags};
     residues_rows_body(a, mt, pow2_s, vb, P.nblocks[w]);
   } else {
-    const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.kp, flags};
+    const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.ldp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.ldp, flags};
     residues_cols_body(a, mt, pow2_s, vb, P.nblocks[w]);
   }
 }
@@ -336,17 +337,17 @@ int grid_for(int64_t warps) {
 
 }  // namespace
 
-cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp, const int32_t* e,
+cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp, int64_t ldp, const int32_t* e,
                                  const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st) {
-  ResidArgs a{A, lda, m, k, kp, e, planes, static_cast<int64_t>(m) * kp, flags};
+  ResidArgs a{A, lda, m, k, kp, ldp, e, planes, static_cast<int64_t>(m) * ldp, flags};
   const int64_t warps = static_cast<int64_t>(m) * ((kp + kRowSpan - 1) / kRowSpan);
   residues_rows_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
 
-cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, const int32_t* f,
+cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, int64_t ldp, const int32_t* f,
                                  const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st) {
-  ResidArgs a{B, ldb, n, k, kp, f, planes, static_cast<int64_t>(n) * kp, flags};
+  ResidArgs a{B, ldb, n, k, kp, ldp, f, planes, static_cast<int64_t>(n) * ldp, flags};
   const int64_t warps = static_cast<int64_t>((n + 7) / 8) * (kp / 32);
   residues_cols_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
