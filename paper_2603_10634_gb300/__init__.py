@@ -6,6 +6,7 @@ include/ozk2.h); this package is its thin binding.
 """
 from ._lib import Ozk2Error  # noqa: F401
 from .autograd import OzakiMatmul, matmul  # noqa: F401
+from .tune import choose_moduli, choose_moduli_batch  # noqa: F401
 from .ozk2 import (  # noqa: F401
     MODES,
     BatchPlan,

@@ -5,8 +5,9 @@
 //   C_ij  = RN(C'_ij 2^-(e_i + f_j))
 //
 // The sum is formed exactly in integer arithmetic: with u_l = C'_l mod p_l in [0, p_l)
-// and the weights split into 16-bit limbs, limb t of sum_l u_l w_l accumulates in a
-// 32-bit integer (each term < 2^27, N <= 20 terms, sum < 2^31.4), one IMAD per limb.
+// and the weights split into 32-bit limbs, limb t of sum_l u_l w_l accumulates in a
+// 64-bit integer (each term < 2^43, N <= 20 terms, sum < 2^48), one wide multiply-add
+// per limb.
 // The quotient Q = round(V / P) comes from the fixed-point estimate
 // sum_l u_l round(2^16 w_l / P) (error < 0.17); V - Q P is normalised to L signed
 // 32-bit limbs.  When the estimate is at least 0.3 away from a rounding boundary the
@@ -125,19 +126,18 @@ __device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64
                                          double* __restrict__ C, int64_t ldc, const CrtTable& ct, int64_t vblock,
                                          int64_t vgrid) {
   constexpr int L = limbs_for(N);
-  constexpr int L16 = 2 * L;
   const int nq = (n + 1) >> 1;
   const int64_t total = static_cast<int64_t>(m) * nq;
   for (int64_t it = vblock * blockDim.x + threadIdx.x; it < total; it += vgrid * blockDim.x) {
     const int i = static_cast<int>(it / nq);
     const int j0 = static_cast<int>(it % nq) * 2;
     const int16_t* src = cres + static_cast<int64_t>(i) * ldr + j0;
-    uint32_t acc[2][L16];
+    uint64_t acc[2][L];
     uint32_t est[2] = {0u, 0u};
 #pragma unroll
     for (int z = 0; z < 2; ++z)
 #pragma unroll
-      for (int t = 0; t < L16; ++t) acc[z][t] = 0u;
+      for (int t = 0; t < L; ++t) acc[z][t] = 0ull;
 #pragma unroll
     for (int l = 0; l < N; ++l) {
       const int p = ct.p[l];
@@ -147,7 +147,7 @@ __device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64
       for (int z = 0; z < 2; ++z) {
         const uint32_t u = static_cast<uint32_t>(cz[z] < 0 ? cz[z] + p : cz[z]);
 #pragma unroll
-        for (int t = 0; t < L16; ++t) acc[z][t] += u * static_cast<uint32_t>(ct.w16[l][t]);
+        for (int t = 0; t < L; ++t) acc[z][t] += static_cast<uint64_t>(u) * ct.w32[l][t];
         est[z] += u * ct.frac16[l];
       }
     }
@@ -162,14 +162,13 @@ __device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64
         const uint32_t q = (est[z] + 0x8000u) >> 16;
         const int32_t off = static_cast<int32_t>(est[z] - (q << 16));  // in [-2^15, 2^15)
         const bool exact_check = (off > 19660 || off < -19660);        // |est - Q| > 0.3
-        // v = V - Q P from the 16-bit-limb sums, normalised to 32-bit limbs
+        // v = V - Q P from the 64-bit limb sums, normalised to 32-bit limbs
         uint32_t v[L];
         int64_t carry = 0;
 #pragma unroll
         for (int t = 0; t < L; ++t) {
-          const int64_t lo = static_cast<int64_t>(acc[z][2 * t]) - static_cast<int64_t>(q) * ct.P16[2 * t];
-          const int64_t hi = static_cast<int64_t>(acc[z][2 * t + 1]) - static_cast<int64_t>(q) * ct.P16[2 * t + 1];
-          const int64_t x = carry + lo + hi * 65536;
+          const int64_t x = carry + static_cast<int64_t>(acc[z][t]) -
+                            static_cast<int64_t>(static_cast<uint64_t>(q) * ct.P[t]);
           v[t] = static_cast<uint32_t>(x);
           carry = x >> 32;  // arithmetic: signed carry
         }

@@ -43,9 +43,8 @@ struct CrtTable {
   int N;
   int limbs;                               // L, 32-bit limbs of the signed result
   int p[kMaxModuli];
-  uint16_t w16[kMaxModuli][2 * kMaxLimbs]; // q_l P / p_l mod P in 16-bit limbs
+  uint32_t w32[kMaxModuli][kMaxLimbs];     // q_l P / p_l mod P in 32-bit limbs
   uint32_t frac16[kMaxModuli];             // round(2^16 w_l / P) (quotient estimate)
-  uint16_t P16[2 * kMaxLimbs];             // P in 16-bit limbs
   uint32_t P[kMaxLimbs];
   uint32_t halfP[kMaxLimbs];               // P / 2 (P is even: 1024 is a modulus)
 };

@@ -198,19 +198,12 @@ bool build_crt_table(int N, CrtTable* ct) {
     div_small(Pl, static_cast<uint32_t>(p), &rem);
     const int q = modinv(static_cast<int>(rem), p);
     const Big w = mul_small(Pl, static_cast<uint32_t>(q));  // < P, already reduced
-    for (size_t t = 0; t < w.size() && t < static_cast<size_t>(kMaxLimbs); ++t) {
-      ct->w16[l][2 * t] = static_cast<uint16_t>(w[t] & 0xFFFFu);
-      ct->w16[l][2 * t + 1] = static_cast<uint16_t>(w[t] >> 16);
-    }
+    for (size_t t = 0; t < w.size() && t < static_cast<size_t>(kMaxLimbs); ++t) ct->w32[l][t] = w[t];
     int ew;
     const double wtop = w.empty() ? 0.0 : top_as_double(w, &ew);
     ct->frac16[l] = w.empty() ? 0u : static_cast<uint32_t>(std::llround(std::ldexp(wtop / Ptop, ew - eP + 16)));
   }
-  for (size_t t = 0; t < P.size(); ++t) {
-    ct->P[t] = P[t];
-    ct->P16[2 * t] = static_cast<uint16_t>(P[t] & 0xFFFFu);
-    ct->P16[2 * t + 1] = static_cast<uint16_t>(P[t] >> 16);
-  }
+  for (size_t t = 0; t < P.size(); ++t) ct->P[t] = P[t];
   uint32_t dummy;
   const Big half = div_small(P, 2u, &dummy);
   for (size_t t = 0; t < half.size(); ++t) ct->halfP[t] = half[t];
