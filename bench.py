@@ -174,8 +174,10 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the residue-product kernel's own sources (its translation unit and the
+    PTX helpers it includes)."""
     h = hashlib.sha256()
-    for f in ["gemm.cu", "device.cuh", "internal.h"]:
+    for f in ["gemm.cu", "device.cuh"]:
         with open(os.path.join(ROOT, "paper_2603_10634_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -368,17 +370,26 @@ def run_ours(a, rank, world):
         torch.cuda.synchronize(dev)
         barrier(world)
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ozk.set_timing(True)
+        ends = {}
         s0.record(stream)
         for _ in range(a.steps):
             e2e_step()
+            tl = ozk.timeline()  # waits for this call's last event (host-side)
+            for key, v in (tl or {}).items():
+                ends[key] = ends.get(key, 0.0) + v / a.steps
         s1.record(stream)
         torch.cuda.synchronize(dev)
+        ozk.set_timing(False)
         barrier(world)
         ems = max_over_ranks(s0.elapsed_time(s1) / a.steps, world, dev)
         e2e = {"value": world * flops / (ems * 1e-3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": hA.numel() * 8 + hB.numel() * 8, "d2h_bytes_per_step": hC.numel() * 8,
                "ms_per_step": ems,
-               "path": "ozk2_dgemm_host: pinned host A, B, C; the library's copies overlap its kernels"}
+               "path": "ozk2_dgemm_host: pinned host A, B, C; the library's copies overlap its kernels",
+               "phase_ends_ms": {"scaled (uploads done)": ends.get("scale"), "exponents": ends.get("exponents"),
+                                 "residues": ends.get("residues"), "last CRT": ends.get("residue_gemm"),
+                                 "last block back": ends.get("crt")}}
         e2e["matches_device_call"] = bool(torch.equal(hC, Cdev))
         # the link itself on this machine: one plain pinned copy each way
         c0, c1, c2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))

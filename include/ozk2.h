@@ -275,6 +275,11 @@ int ozk2_get_timing(float *ms, int max);
  * call on this thread (host-side count). */
 int ozk2_last_launch_count(void);
 
+/* ozk2_debug_timeline - of the last timed call: milliseconds from its start to the end
+ * of each of the six phases (as ozk2_get_timing orders them).  Returns the number of
+ * values written (6), or -1 if there is no timed call or max < 6. */
+int ozk2_debug_timeline(float *ms, int max);
+
 /* ---------------------------------------------------------------------------
  * Parity hooks.  Each runs one step (or a prefix) of the method on its own so the
  * CPU oracle can check it.  Same conventions as above; all arrays are device

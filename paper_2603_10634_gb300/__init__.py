@@ -25,6 +25,7 @@ from .ozk2 import (  # noqa: F401
     residue_products,
     scales,
     set_timing,
+    timeline,
     workspace_size,
     workspace_size_host,
 )

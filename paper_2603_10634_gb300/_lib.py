@@ -40,6 +40,7 @@ SIGNATURES = {
     "ozk2_batch_plan_destroy": (None, [c_void_p]),
     "ozk2_dgemm_batched": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_int, c_int, c_void_p, c_size_t, c_void_p]),
+    "ozk2_debug_timeline": (c_int, [c_void_p, c_int]),
     "ozk2_status_string": (ctypes.c_char_p, [c_int]),
     "ozk2_device_status": (c_int, [c_void_p, c_void_p]),
     "ozk2_moduli": (c_int, [c_int, ctypes.POINTER(ctypes.c_int32)]),

@@ -208,6 +208,8 @@ uint8_t* owned_workspace(size_t need, ozk2_status* err) {
 }
 
 // ------------------------------------------------------------------ timing
+constexpr int kMaxRowBlocks = 4;  // output row blocks of a host-buffer call
+
 struct Timing {
   bool enabled = false;
   bool have = false;
@@ -218,8 +220,7 @@ Timing g_timing;
 std::mutex g_timing_mutex;
 thread_local int t_launches = 0;
 
-void mark(Ctx& c, int idx) {
-  if (!g_timing.enabled || !c.timed) return;
+void timing_events() {
   int dev = 0;
   cudaGetDevice(&dev);
   if (g_timing.dev != dev) {
@@ -228,6 +229,12 @@ void mark(Ctx& c, int idx) {
     for (auto& e : g_timing.ev) cudaEventCreate(&e);
     g_timing.dev = dev;
   }
+}
+
+// Phase boundary idx (0..6) of the call, on its stream.
+void mark(Ctx& c, int idx) {
+  if (!g_timing.enabled || !c.timed) return;
+  timing_events();
   cudaEventRecord(g_timing.ev[idx], c.st);
   if (idx == 6) g_timing.have = true;
 }
@@ -337,8 +344,8 @@ ozk2_status phase_residues(Ctx& c, const Operand& a, const Operand& b, const int
   return OZK2_OK;
 }
 
-// Residue products C'_l for output rows [i0, i0 + rows).
-ozk2_status products_rows(Ctx& c, int64_t i0, int rows) {
+// Residue products C'_l for output rows [i0, i0 + rows), on stream `st`.
+ozk2_status products_rows(Ctx& c, int64_t i0, int rows, cudaStream_t st) {
   const Layout& L = c.L;
   GemmArgs g{};
   g.mode = kModeResidue;
@@ -355,13 +362,13 @@ ozk2_status products_rows(Ctx& c, int64_t i0, int rows) {
   g.plane_stride_a = int64_t(c.m) * L.ldp;
   g.plane_stride_b = int64_t(c.n) * L.ldp;
   OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA) + i0 * L.ldp, L.ldp, L.planes, c.at<uint8_t>(L.planesB),
-                           L.ldp, L.planes, c.st));
+                           L.ldp, L.planes, st));
   t_launches += 1;
   return OZK2_OK;
 }
 
 ozk2_status phase_products(Ctx& c) {
-  ozk2_status s = products_rows(c, 0, c.m);
+  ozk2_status s = products_rows(c, 0, c.m, c.st);
   if (s != OZK2_OK) return s;
   mark(c, 5);
   return OZK2_OK;
@@ -369,17 +376,17 @@ ozk2_status phase_products(Ctx& c) {
 
 // CRT and inverse scaling of output rows [i0, i0 + rows) into C (which points at row i0).
 ozk2_status crt_rows(Ctx& c, int64_t i0, int rows, const int32_t* e, const int32_t* f, const uint8_t* rowstat,
-                     const uint8_t* colstat, double* C, int64_t ldc) {
+                     const uint8_t* colstat, double* C, int64_t ldc, cudaStream_t st) {
   const Layout& L = c.L;
   OZK2_TRY(launch_crt(c.at<int16_t>(L.cres) + i0 * L.ldr, L.ldr, int64_t(c.m) * L.ldr, rows, c.n, e + i0, f,
-                      rowstat ? rowstat + i0 : nullptr, colstat, C, ldc, c.tab->ct, c.st));
+                      rowstat ? rowstat + i0 : nullptr, colstat, C, ldc, c.tab->ct, st));
   t_launches += 1;
   return OZK2_OK;
 }
 
 ozk2_status phase_crt(Ctx& c, const int32_t* e, const int32_t* f, const uint8_t* rowstat,
                       const uint8_t* colstat, double* C, int64_t ldc) {
-  ozk2_status s = crt_rows(c, 0, c.m, e, f, rowstat, colstat, C, ldc);
+  ozk2_status s = crt_rows(c, 0, c.m, e, f, rowstat, colstat, C, ldc, c.st);
   if (s != OZK2_OK) return s;
   mark(c, 6);
   return OZK2_OK;
@@ -440,6 +447,56 @@ ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, bool fast, voi
   return OZK2_OK;
 }
 
+// ------------------------------------------------------------------ products and CRT
+// Copy of finished output row blocks to the host (the host-buffer call).
+struct CopyBack {
+  double* hC;
+  int64_t ldc;
+  cudaStream_t cs;
+  cudaEvent_t* done;  // one event per row block
+};
+
+// Row blocks of a host-buffer call: each at least 16 waves of GEMM units (a persistent
+// launch loses up to one wave at its end), at most kMaxRowBlocks, 128-row aligned.
+int64_t row_blocks(const Ctx& c) {
+  const int64_t units = ((int64_t(c.m) + 127) / 128) * ((int64_t(c.n) + 255) / 256) * c.N;
+  return std::max<int64_t>(1, std::min<int64_t>(kMaxRowBlocks, units / (16 * int64_t(c.num_sms))));
+}
+
+// After the scaling, the exponents and B's residues (all on c.st): A's residues, the
+// residue products and the CRT, in order on c.st.  C (device, row-major, ldc) receives
+// the result.  With cb the products and the CRT run in output row blocks, and block b is
+// copied to cb->hC on cb->cs while block b + 1 is computed.  (Running the conversion
+// kernels on a second stream beside the persistent GEMM was measured and gains nothing:
+// they get too little of an SM next to it.)
+ozk2_status products_and_crt(Ctx& c, const Operand& a, double* C, int64_t ldc, const CopyBack* cb) {
+  const Layout& L = c.L;
+  const int32_t* e = c.at<int32_t>(L.e);
+  const int32_t* f = c.at<int32_t>(L.f);
+  const uint8_t* rs = c.at<uint8_t>(L.rowstat);
+  const uint8_t* cs = c.at<uint8_t>(L.colstat);
+  OZK2_TRY(residues_operand(c, a, c.m, e, c.at<uint8_t>(L.planesA), L.ldp));
+  t_launches += 1;
+  mark(c, 4);
+  ozk2_status s;
+  if (!cb) {
+    if ((s = phase_products(c)) != OZK2_OK) return s;
+    return phase_crt(c, e, f, rs, cs, C, ldc);
+  }
+  const int64_t nb = row_blocks(c);
+  const int64_t rb = ((c.m + nb - 1) / nb + 127) / 128 * 128;
+  for (int64_t i0 = 0, b = 0; i0 < c.m; i0 += rb, ++b) {
+    const int rows = int(std::min(rb, int64_t(c.m) - i0));
+    if ((s = products_rows(c, i0, rows, c.st)) != OZK2_OK) return s;
+    if ((s = crt_rows(c, i0, rows, e, f, rs, cs, C + i0 * ldc, ldc, c.st)) != OZK2_OK) return s;
+    OZK2_TRY(cudaEventRecord(cb->done[b], c.st));
+    OZK2_TRY(cudaStreamWaitEvent(cb->cs, cb->done[b], 0));
+    OZK2_TRY(cudaMemcpy2DAsync(cb->hC + i0 * cb->ldc, size_t(cb->ldc) * 8, C + i0 * ldc, size_t(ldc) * 8,
+                               size_t(c.n) * 8, size_t(rows), cudaMemcpyDeviceToHost, cb->cs));
+  }
+  return OZK2_OK;
+}
+
 // One emulated product over whole operands (no blocking); arguments already validated,
 // m, n, k > 0.
 ozk2_status run_one(const Operand& a, const Operand& b, int64_t m, int64_t n, int64_t k, double* C, int64_t ldc,
@@ -450,12 +507,9 @@ ozk2_status run_one(const Operand& a, const Operand& b, int64_t m, int64_t n, in
   mark(c, 0);
   const Layout& L = c.L;
   if ((s = phase_scales(c, a, b, first)) != OZK2_OK) return s;
-  if ((s = phase_residues(c, a, b, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesA),
-                          c.at<uint8_t>(L.planesB))) != OZK2_OK)
-    return s;
-  if ((s = phase_products(c)) != OZK2_OK) return s;
-  return phase_crt(c, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.rowstat), c.at<uint8_t>(L.colstat), C,
-                   ldc);
+  OZK2_TRY(residues_operand(c, b, c.n, c.at<int32_t>(L.f), c.at<uint8_t>(L.planesB), L.ldp));
+  t_launches += 1;
+  return products_and_crt(c, a, C, ldc, nullptr);
 }
 
 int64_t block_or_all(int64_t b, int64_t total) { return (b <= 0 || b >= total) ? total : b; }
@@ -511,8 +565,7 @@ Staging make_staging(int64_t m, int64_t n, int64_t k) {
 }
 
 constexpr int kHostChunks = 4;  // A arrives in this many line chunks
-constexpr int kHostBlocks = 4;  // at most this many output row blocks stream back
-constexpr int kHostEvents = 2 + kHostChunks + kHostBlocks + 1;
+constexpr int kHostEvents = 2 + kHostChunks + kMaxRowBlocks + 1;
 
 struct CopyEngine {
   cudaStream_t cs = nullptr;
@@ -571,7 +624,9 @@ ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64
   Ctx c;
   const Staging G = make_staging(m, n, k);
   if ((s = setup(c, m, n, k, N, fast, ws, ws_bytes, st, G.total)) != OZK2_OK) return s;
-  c.timed = false;  // phases overlap with copies
+  // Timed phases on `st`: 0 start, 1 scaling done (after the uploads it waits for), 2-3
+  // bound product and exponents, 4 residues, 5 last block's CRT, 6 last block back.
+  mark(c, 0);
   const Layout& L = c.L;
   double* dA = c.at<double>(L.total + G.A);
   double* dB = c.at<double>(L.total + G.B);
@@ -604,29 +659,16 @@ ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64
     if (i1 > i0 && (s = scale_operand(c, shift_lines(a, i0), i0, int(i1 - i0), side_a(L))) != OZK2_OK) return s;
   }
   if ((s = bound_and_exponents(c)) != OZK2_OK) return s;
-  if ((s = phase_residues(c, a, b, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesA),
-                          c.at<uint8_t>(L.planesB))) != OZK2_OK)
-    return s;
-
-  // output row blocks: a multiple of the 128-row tile, each at least ~8 waves of tiles
-  const int64_t units = ((m + 127) / 128) * ((n + 255) / 256) * N;
-  const int64_t nblk = std::max<int64_t>(1, std::min<int64_t>(kHostBlocks, units / (8 * int64_t(c.num_sms))));
-  const int64_t rb = ((m + nblk - 1) / nblk + 127) / 128 * 128;
-  int used = 0;
-  for (int64_t i0 = 0; i0 < m; i0 += rb, ++used) {
-    const int rows = int(std::min(rb, m - i0));
-    if ((s = products_rows(c, i0, rows)) != OZK2_OK) return s;
-    if ((s = crt_rows(c, i0, rows, c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.at<uint8_t>(L.rowstat),
-                      c.at<uint8_t>(L.colstat), dC + i0 * n, n)) != OZK2_OK)
-      return s;
-    OZK2_TRY(cudaEventRecord(ev_blk[used], st));
-    OZK2_TRY(cudaStreamWaitEvent(cs, ev_blk[used], 0));
-    OZK2_TRY(cudaMemcpy2DAsync(hC + i0 * ldc, size_t(ldc) * 8, dC + i0 * n, size_t(n) * 8, size_t(n) * 8,
-                               size_t(rows), cudaMemcpyDeviceToHost, cs));
-  }
+  OZK2_TRY(residues_operand(c, b, int(n), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesB), L.ldp));
+  t_launches += 1;
+  // residue products and CRT in output row blocks; each finished block streams back
+  const CopyBack cb{hC, ldc, cs, ev_blk};
+  if ((s = products_and_crt(c, a, dC, n, &cb)) != OZK2_OK) return s;
+  mark(c, 5);
   // the call is complete on `st` once the last block is back on the host
   OZK2_TRY(cudaEventRecord(ev_done, cs));
   OZK2_TRY(cudaStreamWaitEvent(st, ev_done, 0));
+  mark(c, 6);
   return OZK2_OK;
 }
 
@@ -1144,6 +1186,15 @@ int ozk2_get_timing(float* ms, int max) {
   if (cudaEventSynchronize(g_timing.ev[6]) != cudaSuccess) return -1;
   int w = 0;
   for (int i = 0; i < 6 && w < max; ++i, ++w) cudaEventElapsedTime(&ms[i], g_timing.ev[i], g_timing.ev[i + 1]);
+  return w;
+}
+
+int ozk2_debug_timeline(float* ms, int max) {
+  std::lock_guard<std::mutex> lk(g_timing_mutex);
+  if (!g_timing.have || !ms || max < 6) return -1;
+  if (cudaEventSynchronize(g_timing.ev[6]) != cudaSuccess) return -1;
+  int w = 0;
+  for (int i = 1; i <= 6 && w < max; ++i) cudaEventElapsedTime(&ms[w++], g_timing.ev[0], g_timing.ev[i]);
   return w;
 }
 

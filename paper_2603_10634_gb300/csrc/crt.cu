@@ -211,10 +211,10 @@ template <int N>
 cudaError_t launch_N(const int16_t* cres, int64_t ldr, int64_t rs, int m, int n, const int32_t* e,
                      const int32_t* f, const uint8_t* rowstat, const uint8_t* colstat, double* C,
                      int64_t ldc, const CrtTable& ct, cudaStream_t st) {
+  const int64_t threads = static_cast<int64_t>(m) * ((n + 1) / 2);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t threads = static_cast<int64_t>(m) * ((n + 1) / 2);
   int64_t blocks = (threads + 255) / 256;
   if (blocks > static_cast<int64_t>(sms) * 16) blocks = static_cast<int64_t>(sms) * 16;
   if (blocks < 1) blocks = 1;

@@ -293,6 +293,15 @@ def get_timing():
     return {PHASES[i]: float(buf[i]) for i in range(n)}
 
 
+def timeline():
+    """Milliseconds from the start of the last timed call to the end of each phase."""
+    buf = (ctypes.c_float * 6)()
+    n = _lib.load().ozk2_debug_timeline(buf, 6)
+    if n < 0:
+        return None
+    return dict(zip(PHASES, list(buf)[:n]))
+
+
 def last_launch_count():
     return int(_lib.load().ozk2_last_launch_count())
 
