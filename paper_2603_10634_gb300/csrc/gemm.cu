@@ -16,19 +16,27 @@
 //             (Eq. barCupper); Cbar itself is never stored.
 //   raw     : D = A B^T in FP32 (a parity hook for the tensor-core path).
 //
-// Tiles are 128 x 256 (M x N) with two 256-column FP32 accumulators, the whole 512
-// columns of TMEM.  A square modulus is one round (X, Z).  A Karatsuba modulus is
-// two rounds: (D1, D2), whose epilogue parks mod(15 D1 - D2, p) and mod(D2, p) as an
-// int16 pair in a CTA-private scratch tile (L2-resident), then (D3), whose epilogue
-// finishes the residue.  The wide tile halves the operand bytes each SM pulls per
-// flop compared with 128 x 128.
+// Tiles are 128 x 256 (M x N); TMEM holds two 256-column FP32 accumulator slots (the
+// whole 512 columns).  A unit (one tile of one modulus) is a sequence of passes over
+// the k-block:
+//   square p = s^2 : one pass over BOTH slots, the products interleaved per k-step,
+//                    X = A1 B2 + A2 B1 -> slot 0, Z = A2 B2 -> slot 1 (A2 and B2 are
+//                    loaded while still in L2), C'_l = mod(s X + Z, p);
+//   Karatsuba      : three passes over ONE slot each, alternating slots, so the
+//                    epilogue drains one slot while the tensor cores fill the other:
+//                    D1, park d1 = mod(D1, p); D2, park u1 = mod(15 d1 - D2, p) and
+//                    r2 = mod(D2, p); D3, C'_l = mod(16 mod(u1 + D3, p) + r2, p).
+// Parked values are int16 pairs in a CTA-private scratch tile (L2-resident).  The
+// bound and raw products are one single-slot pass per unit.  The wide tile halves the
+// operand bytes each SM pulls per flop compared with 128 x 128.
 //
 // Roles (320 threads, one persistent CTA per SM):
 //   warp 0      TMA producer: 128-row A and 256-row B^T boxes of 128 bytes along K
 //               (K-major, 128-byte swizzle, zero fill past m, n, k) into a 4-stage
 //               ring of 48 KiB stages, mbarrier complete_tx.
 //   warp 1      TMEM allocation and the single MMA-issuing thread:
-//               tcgen05.mma.cta_group::1.kind::f8f6f4, M = 128, N = 256, K = 32.
+//               tcgen05.mma.cta_group::1.kind::f8f6f4, M = 128, N = 256, K = 32; a pass
+//               starts once the epilogue has released the slot(s) it writes.
 //   warps 2-9   epilogue: warp w reads TMEM lane quadrant w % 4, column half
 //               (w - 2) / 4, with tcgen05.ld; integer math; global stores.
 // Every wait is bounded (device.cuh); a wait that gives up raises a CTA-wide abort
@@ -156,11 +164,11 @@ __device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
 }
 
-// Round structure of a unit.
+// Pass structure of a unit.
 struct UnitPlan {
   int chunk_len;  // k per exactness block
   int nchunks;
-  int nphases;    // rounds per block
+  int npasses;    // passes per block
 };
 
 template <int MODE>
@@ -169,45 +177,56 @@ __device__ __forceinline__ UnitPlan plan_of(int k, int mod) {
   if (MODE == kModeResidue) {
     const bool square = mod < kNumSquares;
     u.chunk_len = square ? kChunkSquare : kChunkKaratsuba;
-    u.nphases = square ? 1 : 2;
+    u.npasses = square ? 1 : 3;
   } else {
     u.chunk_len = ((k + BK - 1) / BK) * BK;
-    u.nphases = 1;
+    u.npasses = 1;
   }
   u.nchunks = (k + u.chunk_len - 1) / u.chunk_len;
   return u;
 }
 
-// Products of one round: count, digit planes (pa, pb), target accumulator and whether
-// the product is the first writer of that accumulator in the round.
+// A pass uses both slots (a square modulus) or one.
 template <int MODE>
-__device__ __forceinline__ int num_products(int mod, int phase) {
-  if (MODE != kModeResidue) return 1;
-  if (mod < kNumSquares) return 3;
-  return phase == 0 ? 2 : 1;
+__device__ __forceinline__ bool pair_pass(int mod) {
+  return MODE == kModeResidue && mod < kNumSquares;
+}
+
+// Products of one pass per k-step, the digit planes (pa, pb) of product x and the
+// accumulator (0: the pass's first slot, 1: slot 1 of a pair pass) it adds to.
+template <int MODE>
+__device__ __forceinline__ int num_products(int mod) {
+  return pair_pass<MODE>(mod) ? 3 : 1;
 }
 
 template <int MODE>
-__device__ __forceinline__ void product_of(int mod, int phase, int x, int& pa, int& pb, int& acc,
-                                           bool& first) {
+__device__ __forceinline__ void product_of(int mod, int pass, int x, int& pa, int& pb, int& acc) {
   if (MODE != kModeResidue) {
     pa = pb = 0;
     acc = 0;
-    first = true;
   } else if (mod < kNumSquares) {
     const int a0 = 2 * mod;  // (A1, B2) -> X, (A2, B1) -> X, (A2, B2) -> Z
     pa = (x == 0) ? a0 : a0 + 1;
     pb = (x == 1) ? a0 : a0 + 1;
     acc = (x == 2) ? 1 : 0;
-    first = (x != 1);
   } else {
-    const int a0 = 2 * kNumSquares + 3 * (mod - kNumSquares);
-    const int plane = (phase == 0) ? x : 2;  // (A1,B1) -> 0, (A2,B2) -> 1 ; then (A3,B3) -> 0
-    pa = pb = a0 + plane;
-    acc = (phase == 0) ? x : 0;
-    first = true;
+    pa = pb = 2 * kNumSquares + 3 * (mod - kNumSquares) + pass;  // (Ax, Bx) -> Dx
+    acc = 0;
   }
 }
+
+// Slot bookkeeping shared by the MMA thread and the epilogue, which walk the same pass
+// sequence: a single-slot pass takes slot `next` and flips it; a pair pass takes both
+// (X in slot 0, Z in slot 1).  uses[j] counts the passes that used slot j before.
+struct Slots {
+  uint32_t u0 = 0u, u1 = 0u;  // passes that used slot 0 / slot 1
+  uint32_t next = 0u;
+  __device__ __forceinline__ uint32_t uses(uint32_t j) const { return j ? u1 : u0; }
+  __device__ __forceinline__ void bump(uint32_t j) {
+    u0 += (j == 0u) ? 1u : 0u;
+    u1 += (j == 1u) ? 1u : 0u;
+  }
+};
 
 // Lane l of the warp ends with the maximum of column l over the 32 lanes.
 __device__ __forceinline__ float warp_column_max(float (&v)[32], int lane) {
@@ -273,9 +292,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint8_t* tiles = smem;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* tfull = empty + kStages;
-  uint64_t* tempty = tfull + 1;
-  uint64_t* done = tempty + 1;
+  uint64_t* tfull = empty + kStages;  // [2]: slot filled by the tensor cores
+  uint64_t* tempty = tfull + 2;       // [2]: slot drained by the epilogue
+  uint64_t* done = tempty + 2;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -287,8 +306,10 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    mbar_init(tfull, 1);
-    mbar_init(tempty, 32 * kEpiWarps);
+    for (int j = 0; j < 2; ++j) {
+      mbar_init(tfull + j, 1);
+      mbar_init(tempty + j, 32 * kEpiWarps);
+    }
     mbar_init(done, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -327,8 +348,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; ok && c < up.nchunks; ++c) {
           const int k0 = c * up.chunk_len;
           const int ksteps = (min(uc.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
-          for (int ph = 0; ok && ph < up.nphases; ++ph) {
-            const int np = num_products<MODE>(mod, ph);
+          for (int ps = 0; ok && ps < up.npasses; ++ps) {
+            const int np = num_products<MODE>(mod);
             for (int s = 0; ok && s < ksteps; ++s) {
               for (int x = 0; x < np; ++x) {
                 if (!mbar_wait_bounded(empty + stage, phase ^ 1u, abort_flag)) {
@@ -336,8 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   break;
                 }
                 int pa, pb, acc;
-                bool first;
-                product_of<MODE>(mod, ph, x, pa, pb, acc, first);
+                product_of<MODE>(mod, ps, x, pa, pb, acc);
                 uint8_t* dst = tiles + stage * kStageBytes;
                 mbar_arrive_expect_tx(full + stage, kStageBytes);
                 tma_load_3d(dst, uc.ta, full + stage, k0 + s * BK, uc.tm * BM, pa);
@@ -366,7 +386,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = fp8_idesc(BM, BN);
       int stage = 0;
-      uint32_t phase = 0, rc = 0;
+      uint32_t phase = 0;
+      Slots sl;
       bool ok = true;
       for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
         UnitCtx uc;
@@ -376,13 +397,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; ok && c < up.nchunks; ++c) {
           const int k0 = c * up.chunk_len;
           const int ksteps = (min(uc.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
-          for (int ph = 0; ok && ph < up.nphases; ++ph) {
-            if (!mbar_wait_bounded(tempty, (rc & 1u) ^ 1u, abort_flag)) {
-              ok = false;
-              break;
+          for (int ps = 0; ok && ps < up.npasses; ++ps) {
+            const bool pair = pair_pass<MODE>(mod);
+            const uint32_t first_slot = pair ? 0u : sl.next;
+            for (uint32_t j = 0; j < 2 && ok; ++j) {
+              if (!pair && j != first_slot) continue;
+              ok = mbar_wait_bounded(tempty + j, (sl.uses(j) & 1u) ^ 1u, abort_flag);
             }
+            if (!ok) break;
             tc_fence_after();
-            const int np = num_products<MODE>(mod, ph);
+            const int np = num_products<MODE>(mod);
             for (int s = 0; ok && s < ksteps; ++s) {
               for (int x = 0; x < np; ++x) {
                 if (!mbar_wait_bounded(full + stage, phase, abort_flag)) {
@@ -391,16 +415,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 int pa, pb, acc;
-                bool first;
-                product_of<MODE>(mod, ph, x, pa, pb, acc, first);
+                product_of<MODE>(mod, ps, x, pa, pb, acc);
+                const bool first = (x == 0 || x == 2) && s == 0;  // first product into its slot
+                const uint32_t dtm = tmem_base + (first_slot + static_cast<uint32_t>(acc)) * static_cast<uint32_t>(BN);
                 const uint32_t sa = smem_addr(tiles + stage * kStageBytes);
                 const uint64_t adesc = sw128_kmajor_desc(sa);
                 const uint64_t bdesc = sw128_kmajor_desc(sa + kATileBytes);
-                const uint32_t dtm = tmem_base + static_cast<uint32_t>(acc * BN);
 #pragma unroll
                 for (int kk = 0; kk < BK / 32; ++kk)
-                  mma_fp8(dtm, adesc + 2ull * kk, bdesc + 2ull * kk, idesc,
-                          (first && s == 0 && kk == 0) ? 0u : 1u);
+                  mma_fp8(dtm, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (first && kk == 0) ? 0u : 1u);
                 mma_commit(empty + stage);
                 if (++stage == kStages) {
                   stage = 0;
@@ -408,8 +431,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
               }
             }
-            if (ok) mma_commit(tfull);
-            ++rc;
+            if (pair) {
+              if (ok) {
+                mma_commit(tfull + 0);
+                mma_commit(tfull + 1);
+              }
+              sl.bump(0u);
+              sl.bump(1u);
+            } else {
+              if (ok) mma_commit(tfull + first_slot);
+              sl.bump(first_slot);
+              sl.next ^= 1u;
+            }
           }
         }
       }
@@ -428,7 +461,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
     uint32_t* scr = prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BN) + row * BN + chalf * (BN / 2);
-    uint32_t rc = 0;
+    Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
     for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
       UnitCtx uc;
@@ -437,60 +470,81 @@ __global__ void __launch_bounds__(kThreads, 1)
       const UnitPlan up = plan_of<MODE>(uc.k, mod);
       const int gi = uc.tm * BM + row;
       for (int c = 0; ok && c < up.nchunks; ++c) {
-        for (int ph = 0; ok && ph < up.nphases; ++ph) {
-          ok = mbar_wait_bounded(tfull, rc & 1u, abort_flag);
+        for (int ps = 0; ok && ps < up.npasses; ++ps) {
+          const bool pair = pair_pass<MODE>(mod);
+          const uint32_t slot = pair ? 0u : sl.next;
+          for (uint32_t j = 0; j < 2 && ok; ++j) {
+            if (!pair && j != slot) continue;
+            ok = mbar_wait_bounded(tfull + j, sl.uses(j) & 1u, abort_flag);
+          }
           ok = __all_sync(0xffffffffu, ok);
           if (!ok) break;
           tc_fence_after();
+          const uint32_t ts = tq + slot * static_cast<uint32_t>(BN);
           if constexpr (MODE == kModeResidue) {
             const int p = prm.mod.p[mod], h = prm.mod.half[mod], sq = prm.mod.s[mod];
             const float ip = prm.mod.inv_p[mod];
+            const bool last = ps == up.npasses - 1;
             int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
 #pragma unroll 1
             for (int cb = 0; cb < BN / 64; ++cb) {
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
-              int res[32];
-              if (mod < kNumSquares) {
+              if (pair) {  // square modulus: X in slot 0, Z in slot 1
                 uint32_t vx[32], vz[32];
                 tmem_ld_32cols(tq + cb * 32, vx);
                 tmem_ld_32cols(tq + BN + cb * 32, vz);
                 tmem_ld_wait();
+                int res[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) res[j] = smod_i32(sq * acc_int(vx[j]) + acc_int(vz[j]), p, h, ip);
-              } else if (ph == 0) {
-                uint32_t v1[32], v2[32];
-                tmem_ld_32cols(tq + cb * 32, v1);
-                tmem_ld_32cols(tq + BN + cb * 32, v2);
-                tmem_ld_wait();
-                uint32_t pk[32];
+                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
+                continue;
+              }
+              uint32_t v[32];
+              tmem_ld_32cols(ts + cb * 32, v);
+              tmem_ld_wait();
+              uint4* sp = reinterpret_cast<uint4*>(scr + cb * 32);
+              if (ps == 0) {  // Karatsuba pass 1: park mod(D1, p)
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const int d2 = acc_int(v2[j]);
-                  const int u1 = smod_i32(15 * acc_int(v1[j]) - d2, p, h, ip);
-                  const int r2 = smod_i32(d2, p, h, ip);
-                  pk[j] = (static_cast<uint32_t>(u1) & 0xFFFFu) | (static_cast<uint32_t>(r2) << 16);
+                for (int w = 0; w < 8; ++w) {
+                  uint32_t pk[4];
+#pragma unroll
+                  for (int z = 0; z < 4; ++z)
+                    pk[z] = static_cast<uint32_t>(smod_i32(acc_int(v[4 * w + z]), p, h, ip)) & 0xFFFFu;
+                  sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
-                uint4* sp = reinterpret_cast<uint4*>(scr + cb * 32);
-#pragma unroll
-                for (int w = 0; w < 8; ++w) sp[w] = make_uint4(pk[4 * w], pk[4 * w + 1], pk[4 * w + 2], pk[4 * w + 3]);
-                continue;  // the residue is finished in the next round
-              } else {
-                uint32_t v3[32];
-                tmem_ld_32cols(tq + cb * 32, v3);
-                tmem_ld_wait();
-                const uint4* sp = reinterpret_cast<const uint4*>(scr + cb * 32);
+                continue;
+              }
+              if (!last) {  // Karatsuba pass 2: park u1 = mod(15 d1 - D2, p), r2 = mod(D2, p)
 #pragma unroll
                 for (int w = 0; w < 8; ++w) {
                   const uint4 pv = sp[w];
                   const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+                  uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z) {
-                    const int j = 4 * w + z;
-                    const int u1 = static_cast<int16_t>(pr[z] & 0xFFFFu);
-                    const int r2 = static_cast<int16_t>(pr[z] >> 16);
-                    const int uu = smod_i32(u1 + acc_int(v3[j]), p, h, ip);
-                    res[j] = smod_i32(16 * uu + r2, p, h, ip);
+                    const int d1 = static_cast<int16_t>(pr[z] & 0xFFFFu);
+                    const int d2 = acc_int(v[4 * w + z]);
+                    const int u1 = smod_i32(15 * d1 - d2, p, h, ip);
+                    const int r2 = smod_i32(d2, p, h, ip);
+                    pk[z] = (static_cast<uint32_t>(u1) & 0xFFFFu) | (static_cast<uint32_t>(r2) << 16);
                   }
+                  sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                }
+                continue;
+              }
+              int res[32];  // Karatsuba pass 3
+#pragma unroll
+              for (int w = 0; w < 8; ++w) {
+                const uint4 pv = sp[w];
+                const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                for (int z = 0; z < 4; ++z) {
+                  const int j = 4 * w + z;
+                  const int u1 = static_cast<int16_t>(pr[z] & 0xFFFFu);
+                  const int r2 = static_cast<int16_t>(pr[z] >> 16);
+                  const int uu = smod_i32(u1 + acc_int(v[j]), p, h, ip);
+                  res[j] = smod_i32(16 * uu + r2, p, h, ip);
                 }
               }
               if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
@@ -500,7 +554,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
             for (int cb = 0; cb < BN / 64; ++cb) {
               uint32_t v0[32];
-              tmem_ld_32cols(tq + cb * 32, v0);
+              tmem_ld_32cols(ts + cb * 32, v0);
               tmem_ld_wait();
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
               float cv[32];
@@ -520,7 +574,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll 1
             for (int cb = 0; cb < BN / 64; ++cb) {
               uint32_t v0[32];
-              tmem_ld_32cols(tq + cb * 32, v0);
+              tmem_ld_32cols(ts + cb * 32, v0);
               tmem_ld_wait();
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
               if (gi < uc.m) {
@@ -532,8 +586,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           }
           tc_fence_before();
-          mbar_arrive(tempty);
-          ++rc;
+          if (pair) {
+            mbar_arrive(tempty + 0);
+            mbar_arrive(tempty + 1);
+            sl.bump(0u);
+            sl.bump(1u);
+          } else {
+            mbar_arrive(tempty + slot);
+            sl.bump(slot);
+            sl.next ^= 1u;
+          }
         }
       }
     }
