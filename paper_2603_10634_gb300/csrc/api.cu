@@ -245,6 +245,13 @@ void mark(Ctx& c, int idx) {
     if (_e != cudaSuccess) return OZK2_ERR_CUDA; \
   } while (0)
 
+// 2-D copy that is issued as one linear copy when both sides are contiguous.
+cudaError_t copy_2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t height,
+                    cudaMemcpyKind kind, cudaStream_t st) {
+  if (dpitch == width && spitch == width) return cudaMemcpyAsync(dst, src, width * height, kind, st);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, st);
+}
+
 // ------------------------------------------------------------------ phases
 // Zero the bound maxima and column reductions of a call (and its flag word when
 // clear_flags: the first block of a call; later blocks keep what earlier blocks
@@ -491,8 +498,8 @@ ozk2_status products_and_crt(Ctx& c, const Operand& a, double* C, int64_t ldc, c
     if ((s = crt_rows(c, i0, rows, e, f, rs, cs, C + i0 * ldc, ldc, c.st)) != OZK2_OK) return s;
     OZK2_TRY(cudaEventRecord(cb->done[b], c.st));
     OZK2_TRY(cudaStreamWaitEvent(cb->cs, cb->done[b], 0));
-    OZK2_TRY(cudaMemcpy2DAsync(cb->hC + i0 * cb->ldc, size_t(cb->ldc) * 8, C + i0 * ldc, size_t(ldc) * 8,
-                               size_t(c.n) * 8, size_t(rows), cudaMemcpyDeviceToHost, cb->cs));
+    OZK2_TRY(copy_2d(cb->hC + i0 * cb->ldc, size_t(cb->ldc) * 8, C + i0 * ldc, size_t(ldc) * 8, size_t(c.n) * 8,
+                     size_t(rows), cudaMemcpyDeviceToHost, cb->cs));
   }
   return OZK2_OK;
 }
@@ -604,10 +611,10 @@ cudaError_t copy_lines_h2d(double* dst, const double* src, int64_t ld, bool kcon
                            int64_t i0, int64_t i1, cudaStream_t cs) {
   if (i1 <= i0) return cudaSuccess;
   if (kcontig)
-    return cudaMemcpy2DAsync(dst + i0 * k, size_t(k) * 8, src + i0 * ld, size_t(ld) * 8, size_t(k) * 8,
-                             size_t(i1 - i0), cudaMemcpyHostToDevice, cs);
-  return cudaMemcpy2DAsync(dst + i0, size_t(lines) * 8, src + i0, size_t(ld) * 8, size_t(i1 - i0) * 8, size_t(k),
-                           cudaMemcpyHostToDevice, cs);
+    return copy_2d(dst + i0 * k, size_t(k) * 8, src + i0 * ld, size_t(ld) * 8, size_t(k) * 8, size_t(i1 - i0),
+                   cudaMemcpyHostToDevice, cs);
+  return copy_2d(dst + i0, size_t(lines) * 8, src + i0, size_t(ld) * 8, size_t(i1 - i0) * 8, size_t(k),
+                 cudaMemcpyHostToDevice, cs);
 }
 
 // C = op(A) op(B) from host buffers: B and then A (in line chunks) go up on the copy
