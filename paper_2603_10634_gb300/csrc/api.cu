@@ -8,8 +8,8 @@
 //   3N digit products + mod-reduce -> C'_l                        (Eqs. 3matmult, C'-Karatsuba)
 //   CRT + inverse scaling -> C                                    (Eqs. CRT_finalreduction,
 //                                                                  inversescaling)
-// All kernels are launched on the caller's stream; nothing here runs on the CPU
-// except bookkeeping.
+// All kernels are launched on the caller's stream (a host-buffer call moves its data on
+// a library copy stream); nothing here runs on the CPU except bookkeeping.
 #include <algorithm>
 #include <climits>
 #include <cstdio>
