@@ -103,3 +103,25 @@ def test_nonfinite_and_caller_workspace(cuda):
         assert _same(Cs[i], ozk.dgemm(As[i], Bs[i], num_moduli=12))
     with pytest.raises(ozk.Ozk2Error):
         ozk.dgemm_batched(As, Bs, num_moduli=12, workspace=ws[: need - 256])
+
+
+def test_single_call_graph_capture(cuda):
+    """One ozk2_dgemm call captured into a CUDA graph (after a warm-up call of the same
+    size, which sizes the workspace) replays the method on new operand contents."""
+    A, B = workloads.problem(300, 200, 500, 1.0, seed=80, device=cuda)
+    C = torch.empty((300, 200), dtype=torch.float64, device=cuda)
+    ozk.dgemm(A, B, num_moduli=12, out=C)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            ozk.dgemm(A, B, num_moduli=12, out=C)
+    torch.cuda.current_stream().wait_stream(s)
+    A2, B2 = workloads.problem(300, 200, 500, 2.0, seed=82, device=cuda)
+    A.copy_(A2)
+    B.copy_(B2)
+    C.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert _same(C, ozk.dgemm(A2, B2, num_moduli=12))
