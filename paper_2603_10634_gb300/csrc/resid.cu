@@ -242,7 +242,20 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const Mod
 
 // Columns of B.  A warp covers 8 columns x 32 consecutive h: lane 4 jj + qq takes
 // column j0 + jj, rows h0 + 8 qq .. h0 + 8 qq + 7.  Each group of four lanes writes one
-// full 32-byte sector of row j of every plane.
+// full 32-byte sector of row j of every plane.  Warp items are walked in tiles of
+// kColTileGroups column groups x kColTileBlocks k-blocks (column groups fastest), so
+// the warps running at one time read a band of rows of B and write a band of rows of
+// each plane, instead of touching every row of all planes (which thrashes address
+// translation once the planes reach gigabytes).
+constexpr int kColTileGroups = 64;  // 512 columns
+constexpr int kColTileBlocks = 32;  // 1024 k
+
+__host__ __device__ inline int64_t cols_items(int lines, int kp) {
+  const int64_t ntj = ((lines + 7) / 8 + kColTileGroups - 1) / kColTileGroups;
+  const int64_t nth = (kp / 32 + kColTileBlocks - 1) / kColTileBlocks;
+  return ntj * nth * kColTileGroups * kColTileBlocks;
+}
+
 __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const ModTable& mt, const int16_t* pow2_s,
                                                    int64_t vblock, int64_t vgrid) {
   const int lane = threadIdx.x & 31;
@@ -250,11 +263,16 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
   const int warps_per_block = blockDim.x >> 5;
   const int ncg = (a.lines + 7) / 8;  // column groups of 8
   const int nkb = a.kp / 32;
-  const int64_t items = static_cast<int64_t>(ncg) * nkb;
+  const int ntj = (ncg + kColTileGroups - 1) / kColTileGroups;
+  const int64_t items = cols_items(a.lines, a.kp);
   bool range_err = false;
   for (int64_t it = vblock * warps_per_block + (threadIdx.x >> 5); it < items; it += vgrid * warps_per_block) {
-    const int hb = static_cast<int>(it / ncg);
-    const int j = static_cast<int>(it % ncg) * 8 + jj;
+    const int64_t tile = it / (kColTileGroups * kColTileBlocks);
+    const int w = static_cast<int>(it % (kColTileGroups * kColTileBlocks));
+    const int cg = static_cast<int>(tile % ntj) * kColTileGroups + w % kColTileGroups;
+    const int hb = static_cast<int>(tile / ntj) * kColTileBlocks + w / kColTileGroups;
+    if (cg >= ncg || hb >= nkb) continue;  // past the edge of a partial tile (warp-uniform)
+    const int j = cg * 8 + jj;
     const bool active = j < a.lines;
     const int e = active ? a.exps[j] : 0;
     const int h0 = hb * 32 + qq * 8;
@@ -348,8 +366,7 @@ cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int
 cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, int64_t ldp, const int32_t* f,
                                  const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st) {
   ResidArgs a{B, ldb, n, k, kp, ldp, f, planes, static_cast<int64_t>(n) * ldp, flags};
-  const int64_t warps = static_cast<int64_t>((n + 7) / 8) * (kp / 32);
-  residues_cols_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
+  residues_cols_kernel<<<grid_for(cols_items(n, kp)), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
 
