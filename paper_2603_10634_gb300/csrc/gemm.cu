@@ -116,10 +116,29 @@ struct UnitCtx {
   float* S;
 };
 
-template <bool GROUPED>
+// Clustered launch (CL = 2): unit u is a PAIR of vertically adjacent tiles (rows of
+// tiles 2q and 2q + 1, the same tile column and modulus) handled by the two CTAs of a
+// cluster, which share the B tile.  Pair rows are rasterised in bands of kGroupM / 2.
+__device__ __forceinline__ void decode_pair(int tiles_m, int tiles_n, int u, uint32_t rank, int& mod, int& tm,
+                                            int& tn) {
+  const int tiles_mp = (tiles_m + 1) / 2;
+  const int per_mod = tiles_mp * tiles_n;
+  mod = u / per_mod;
+  const int t = u - mod * per_mod;
+  constexpr int kGroupPairs = kGroupM / 2;
+  const int per_group = kGroupPairs * tiles_n;
+  const int g = t / per_group;
+  const int first = g * kGroupPairs;
+  const int gsz = min(tiles_mp - first, kGroupPairs);
+  const int r = t - g * per_group;
+  tm = 2 * (first + r % gsz) + static_cast<int>(rank);
+  tn = r / gsz;
+}
+
+template <bool GROUPED, int CL>
 __device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensorMap* tmA, const CUtensorMap* tmB,
                                              const GemmProblem* __restrict__ probs, int nprobs, int u,
-                                             UnitCtx& c) {
+                                             uint32_t rank, UnitCtx& c) {
   if constexpr (!GROUPED) {
     c.ta = tmA;
     c.tb = tmB;
@@ -127,7 +146,10 @@ __device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensor
     c.n = P.n;
     c.k = P.k;
     c.prob = 0;
-    decode_unit(P.tiles_m, P.tiles_n, P.tiles, u, c.mod, c.tm, c.tn);
+    if constexpr (CL == 2)
+      decode_pair(P.tiles_m, P.tiles_n, u, rank, c.mod, c.tm, c.tn);
+    else
+      decode_unit(P.tiles_m, P.tiles_n, P.tiles, u, c.mod, c.tm, c.tn);
     c.cres = P.cres;
     c.ldr = P.ldr;
     c.res_stride = P.res_stride;
@@ -283,10 +305,14 @@ __device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int 
 }
 
 // GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).
-template <int MODE, bool GROUPED>
+// CL = 2: a cluster of two CTAs works on tile pairs; each CTA loads its own A tile and
+// one half of the shared B tile, multicast to both, and every stage is released only
+// when both CTAs' products have read it.
+template <int MODE, bool GROUPED, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ GemmParams prm, const GemmProblem* __restrict__ probs, int nprobs) {
+  static_assert(CL == 1 || (CL == 2 && !GROUPED), "clusters serve single problems");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;
@@ -300,11 +326,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const uint32_t rank = (CL == 2) ? cluster_rank() : 0u;
+  const int u_first = (CL == 2) ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
+  const int u_step = (CL == 2) ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(empty + s, 1);
+      mbar_init(empty + s, CL);  // released by the products of every CTA that reads it
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(tfull + j, 1);
@@ -324,6 +353,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -335,9 +365,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued = 0, issued_phase = 0;
       bool ok = true;
       int last_prob = -1;
-      for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
+      for (int u = u_first; ok && u < prm.num_units; u += u_step) {
         UnitCtx uc;
-        resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
+        resolve_unit<GROUPED, CL>(prm, &tmA, &tmB, probs, nprobs, u, rank, uc);
         if (GROUPED && uc.prob != last_prob) {
           tensormap_acquire(uc.ta);
           tensormap_acquire(uc.tb);
@@ -359,9 +389,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int pa, pb, acc;
                 product_of<MODE>(mod, ps, x, pa, pb, acc);
                 uint8_t* dst = tiles + stage * kStageBytes;
-                mbar_arrive_expect_tx(full + stage, kStageBytes);
+                mbar_arrive_expect_tx(full + stage, kStageBytes);  // A + both halves of B
                 tma_load_3d(dst, uc.ta, full + stage, k0 + s * BK, uc.tm * BM, pa);
-                tma_load_3d(dst + kATileBytes, uc.tb, full + stage, k0 + s * BK, uc.tn * BN, pb);
+                if constexpr (CL == 2) {
+                  const int half = static_cast<int>(rank) * (BN / 2);
+                  tma_load_3d_multicast(dst + kATileBytes + half * BK, uc.tb, full + stage, k0 + s * BK,
+                                        uc.tn * BN + half, pb, 0x3);
+                } else {
+                  tma_load_3d(dst + kATileBytes, uc.tb, full + stage, k0 + s * BK, uc.tn * BN, pb);
+                }
                 issued |= 1u << stage;
                 issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                 if (++stage == kStages) {
@@ -389,9 +425,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t phase = 0;
       Slots sl;
       bool ok = true;
-      for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
+      for (int u = u_first; ok && u < prm.num_units; u += u_step) {
         UnitCtx uc;
-        resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
+        resolve_unit<GROUPED, CL>(prm, &tmA, &tmB, probs, nprobs, u, rank, uc);
         const int mod = uc.mod;
         const UnitPlan up = plan_of<MODE>(uc.k, mod);
         for (int c = 0; ok && c < up.nchunks; ++c) {
@@ -424,7 +460,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int kk = 0; kk < BK / 32; ++kk)
                   mma_fp8(dtm, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (first && kk == 0) ? 0u : 1u);
-                mma_commit(empty + stage);
+                if constexpr (CL == 2)
+                  mma_commit_multicast(empty + stage, 0x3);  // both CTAs wrote into this stage
+                else
+                  mma_commit(empty + stage);
                 if (++stage == kStages) {
                   stage = 0;
                   phase ^= 1u;
@@ -463,9 +502,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint32_t* scr = prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BN) + row * BN + chalf * (BN / 2);
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
-    for (int u = blockIdx.x; ok && u < prm.num_units; u += gridDim.x) {
+    for (int u = u_first; ok && u < prm.num_units; u += u_step) {
       UnitCtx uc;
-      resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
+      resolve_unit<GROUPED, CL>(prm, &tmA, &tmB, probs, nprobs, u, rank, uc);
       const int mod = uc.mod, tn = uc.tn;
       const UnitPlan up = plan_of<MODE>(uc.k, mod);
       const int gi = uc.tm * BM + row;
@@ -607,25 +646,43 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
+  if constexpr (CL == 2) cluster_sync();  // no CTA leaves while its peer may still write into it
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kTmemCols);
   }
 }
 
-template <int MODE, bool GROUPED>
+template <int MODE, bool GROUPED, int CL>
 cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
                         const GemmProblem* probs, int nprobs, cudaStream_t st) {
   static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED>,
+    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED, CL>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
     if (err != cudaSuccess) return err;
     configured[dev] = true;
   }
-  fp8_gemm_kernel<MODE, GROUPED><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, prm, probs, nprobs);
+  if constexpr (CL == 1) {
+    fp8_gemm_kernel<MODE, GROUPED, 1><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, prm, probs, nprobs);
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(grid));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CL;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t err = cudaLaunchKernelEx(&cfg, fp8_gemm_kernel<MODE, GROUPED, CL>, ta, tb, prm, probs, nprobs);
+    if (err != cudaSuccess) return err;
+  }
   return cudaGetLastError();
 }
 
@@ -669,18 +726,28 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.ldd = g.ldd;
   prm.flags = g.flags;
 
+  // Tile pairs in 2-CTA clusters (half the B traffic from L2 per product) for the
+  // method's products with at least two tile rows; single CTAs otherwise.
+  const bool pairs = g.mode != kModeRaw && prm.tiles_m >= 2;
   CUtensorMap ta, tb;
   if (!encode_fp8_map(&ta, a, g.k, g.m, planes_a, lda8, g.plane_stride_a, BM, BK)) return cudaErrorInvalidValue;
-  if (!encode_fp8_map(&tb, b, g.k, g.n, planes_b, ldb8, g.plane_stride_b, BN, BK)) return cudaErrorInvalidValue;
+  if (!encode_fp8_map(&tb, b, g.k, g.n, planes_b, ldb8, g.plane_stride_b, pairs ? BN / 2 : BN, BK))
+    return cudaErrorInvalidValue;
   const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
+  if (pairs) {
+    prm.num_units = ((prm.tiles_m + 1) / 2) * prm.tiles_n * nmod;  // tile pairs
+    const int clusters = prm.num_units < ctas / 2 ? prm.num_units : ctas / 2;
+    if (g.mode == kModeResidue) return launch_mode<kModeResidue, false, 2>(prm, ta, tb, 2 * clusters, nullptr, 0, st);
+    return launch_mode<kModeBound, false, 2>(prm, ta, tb, 2 * clusters, nullptr, 0, st);
+  }
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {
     case kModeResidue:
-      return launch_mode<kModeResidue, false>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_mode<kModeResidue, false, 1>(prm, ta, tb, grid, nullptr, 0, st);
     case kModeBound:
-      return launch_mode<kModeBound, false>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_mode<kModeBound, false, 1>(prm, ta, tb, grid, nullptr, 0, st);
     default:
-      return launch_mode<kModeRaw, false>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_mode<kModeRaw, false, 1>(prm, ta, tb, grid, nullptr, 0, st);
   }
 }
 
@@ -720,8 +787,8 @@ cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs,
   const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   if (g.mode == kModeResidue)
-    return launch_mode<kModeResidue, true>(prm, unused, unused, grid, probs, count, st);
-  return launch_mode<kModeBound, true>(prm, unused, unused, grid, probs, count, st);
+    return launch_mode<kModeResidue, true, 1>(prm, unused, unused, grid, probs, count, st);
+  return launch_mode<kModeBound, true, 1>(prm, unused, unused, grid, probs, count, st);
 }
 
 }  // namespace ozk2
