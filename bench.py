@@ -387,8 +387,10 @@ def run_ours(a, rank, world):
                "h2d_bytes_per_step": hA.numel() * 8 + hB.numel() * 8, "d2h_bytes_per_step": hC.numel() * 8,
                "ms_per_step": ems,
                "path": "ozk2_dgemm_host: pinned host A, B, C; the library's copies overlap its kernels",
-               "phase_ends_ms": {"scaled (uploads done)": ends.get("scale"), "exponents": ends.get("exponents"),
-                                 "residues": ends.get("residues"), "last CRT": ends.get("residue_gemm"),
+               "phase_ends_ms": {"uploads done, last chunk of A scaled": ends.get("scale"),
+                                 "last chunk bounded": ends.get("bound_gemm"),
+                                 "last chunk converted": ends.get("exponents"),
+                                 "B converted": ends.get("residues"), "last CRT": ends.get("residue_gemm"),
                                  "last block back": ends.get("crt")}}
         e2e["matches_device_call"] = bool(torch.equal(hC, Cdev))
         # the link itself on this machine: one plain pinned copy each way

@@ -296,29 +296,43 @@ ozk2_status scale_operand(Ctx& c, const Operand& op, int64_t first, int lines, c
   return OZK2_OK;
 }
 
+// Bound product (accurate mode) of rows [i0, i0 + rows) of A with all of B: the row
+// maxima R_i of those rows, and their share of the column maxima S_j (atomic maxima, so
+// the row slices may come in any order).
+cudaError_t bound_rows(Ctx& c, int64_t i0, int rows) {
+  const Layout& L = c.L;
+  GemmArgs g{};
+  g.mode = kModeBound;
+  g.m = rows;
+  g.n = c.n;
+  g.k = c.k;
+  g.num_sms = c.num_sms;
+  g.factor = bound_factor_f32(c.k);
+  g.R = c.at<float>(L.R) + i0;
+  g.S = c.at<float>(L.S);
+  g.flags = c.at<uint32_t>(L.flags);
+  t_launches += 1;
+  return launch_fp8_gemm(g, c.at<uint8_t>(L.Abar) + i0 * L.kp, L.kp, 1, c.at<uint8_t>(L.BbarT), L.kp, 1, c.st);
+}
+
+// Exponents e_i of rows [i0, i0 + rows) (Eq. 9); with cols, also every f_j.  Each needs
+// its own final maximum (R_i: the bound products of row i with every column; S_j: those
+// of column j with every row).
+cudaError_t exponents_of(Ctx& c, int64_t i0, int rows, bool cols) {
+  const Layout& L = c.L;
+  t_launches += 1;
+  return launch_exponents(rows, cols ? c.n : 0, c.at<int32_t>(L.eprime) + i0, c.at<int32_t>(L.fprime),
+                          c.at<uint8_t>(L.rowstat) + i0, c.at<uint8_t>(L.colstat), c.at<float>(L.R) + i0,
+                          c.at<float>(L.S), c.tab->pprime, delta_f32(), c.at<int32_t>(L.e) + i0,
+                          c.at<int32_t>(L.f), c.st);
+}
+
 // Bound product (accurate mode) and the exponents e, f.
 ozk2_status bound_and_exponents(Ctx& c) {
-  const Layout& L = c.L;
   mark(c, 1);
-  if (!c.fast) {
-    GemmArgs g{};
-    g.mode = kModeBound;
-    g.m = c.m;
-    g.n = c.n;
-    g.k = c.k;
-    g.num_sms = c.num_sms;
-    g.factor = bound_factor_f32(c.k);
-    g.R = c.at<float>(L.R);
-    g.S = c.at<float>(L.S);
-    g.flags = c.at<uint32_t>(L.flags);
-    OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.Abar), L.kp, 1, c.at<uint8_t>(L.BbarT), L.kp, 1, c.st));
-    t_launches += 1;
-  }
+  if (!c.fast) OZK2_TRY(bound_rows(c, 0, c.m));
   mark(c, 2);
-  OZK2_TRY(launch_exponents(c.m, c.n, c.at<int32_t>(L.eprime), c.at<int32_t>(L.fprime), c.at<uint8_t>(L.rowstat),
-                            c.at<uint8_t>(L.colstat), c.at<float>(L.R), c.at<float>(L.S), c.tab->pprime,
-                            delta_f32(), c.at<int32_t>(L.e), c.at<int32_t>(L.f), c.st));
-  t_launches += 1;
+  OZK2_TRY(exponents_of(c, 0, c.m, true));
   mark(c, 3);
   return OZK2_OK;
 }
@@ -331,13 +345,15 @@ ozk2_status phase_scales(Ctx& c, const Operand& a, const Operand& b, bool clear_
   return bound_and_exponents(c);
 }
 
+// plane_stride: bytes between the planes (0: lines * pitch; the whole operand's when
+// `op`, `ex` and `planes` point at a slice of its lines).
 cudaError_t residues_operand(Ctx& c, const Operand& op, int lines, const int32_t* ex, uint8_t* planes,
-                             int64_t pitch) {
+                             int64_t pitch, int64_t plane_stride = 0) {
   if (op.kcontig)
     return launch_residues_rows(op.ptr, op.ld, lines, c.k, int(c.L.kp), pitch, ex, c.tab->mt, planes,
-                                c.at<uint32_t>(c.L.flags), c.st);
+                                c.at<uint32_t>(c.L.flags), c.st, plane_stride);
   return launch_residues_cols(op.ptr, op.ld, c.k, lines, int(c.L.kp), pitch, ex, c.tab->mt, planes,
-                              c.at<uint32_t>(c.L.flags), c.st);
+                              c.at<uint32_t>(c.L.flags), c.st, plane_stride);
 }
 
 // pitch: row pitch of the destination planes (0: the workspace pitch L.ldp).
@@ -470,20 +486,22 @@ int64_t row_blocks(const Ctx& c) {
   return std::max<int64_t>(1, std::min<int64_t>(kMaxRowBlocks, units / (16 * int64_t(c.num_sms))));
 }
 
-// After the scaling, the exponents and B's residues (all on c.st): A's residues, the
-// residue products and the CRT, in order on c.st.  C (device, row-major, ldc) receives
-// the result.  With cb the products and the CRT run in output row blocks, and block b is
-// copied to cb->hC on cb->cs while block b + 1 is computed.  (Running the conversion
-// kernels on a second stream beside the persistent GEMM was measured and gains nothing:
-// they get too little of an SM next to it.)
-ozk2_status products_and_crt(Ctx& c, const Operand& a, double* C, int64_t ldc, const CopyBack* cb) {
+// After the scaling, the exponents and B's residues (all on c.st): A's residues (unless
+// `a` is null: already converted), the residue products and the CRT, in order on c.st.
+// C (device, row-major, ldc) receives the result.  With cb the products and the CRT run
+// in output row blocks, and block b is copied to cb->hC on cb->cs while block b + 1 is
+// computed.  (Running the conversion kernels on a second stream beside the persistent
+// GEMM was measured and gains nothing: they get too little of an SM next to it.)
+ozk2_status products_and_crt(Ctx& c, const Operand* a, double* C, int64_t ldc, const CopyBack* cb) {
   const Layout& L = c.L;
   const int32_t* e = c.at<int32_t>(L.e);
   const int32_t* f = c.at<int32_t>(L.f);
   const uint8_t* rs = c.at<uint8_t>(L.rowstat);
   const uint8_t* cs = c.at<uint8_t>(L.colstat);
-  OZK2_TRY(residues_operand(c, a, c.m, e, c.at<uint8_t>(L.planesA), L.ldp));
-  t_launches += 1;
+  if (a) {
+    OZK2_TRY(residues_operand(c, *a, c.m, e, c.at<uint8_t>(L.planesA), L.ldp));
+    t_launches += 1;
+  }
   mark(c, 4);
   ozk2_status s;
   if (!cb) {
@@ -516,7 +534,7 @@ ozk2_status run_one(const Operand& a, const Operand& b, int64_t m, int64_t n, in
   if ((s = phase_scales(c, a, b, first)) != OZK2_OK) return s;
   OZK2_TRY(residues_operand(c, b, c.n, c.at<int32_t>(L.f), c.at<uint8_t>(L.planesB), L.ldp));
   t_launches += 1;
-  return products_and_crt(c, a, C, ldc, nullptr);
+  return products_and_crt(c, &a, C, ldc, nullptr);
 }
 
 int64_t block_or_all(int64_t b, int64_t total) { return (b <= 0 || b >= total) ? total : b; }
@@ -617,11 +635,14 @@ cudaError_t copy_lines_h2d(double* dst, const double* src, int64_t ld, bool kcon
                  cudaMemcpyHostToDevice, cs);
 }
 
-// C = op(A) op(B) from host buffers: B and then A (in line chunks) go up on the copy
-// stream while the scaling of what has arrived runs on `st`; after the exponents and
-// residues, the residue products and the CRT run in output row blocks, and block b
-// streams back while block b + 1 is computed.  The device arithmetic is exactly that
-// of the device-buffer call, so the results are bit-identical.
+// C = op(A) op(B) from host buffers.  B goes up first, then A in line chunks, on the copy
+// stream.  B's scaling runs once B is in; each chunk of A is then scaled, bounded against
+// all of B (accurate mode; its rows' maxima R_i are then final), given its exponents e_i
+// and converted to digit planes while the next chunk is still on its way.  Only the
+// column exponents f_j wait for the whole of A (S_j is a maximum over every row), and
+// with them B's residues.  The residue products and the CRT then run in output row
+// blocks, block b streaming back while block b + 1 is computed.  Every kernel does the
+// same arithmetic as in the device-buffer call, so the results are bit-identical.
 ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* hA,
                      int64_t lda, const double* hB, int64_t ldb, double* hC, int64_t ldc, int N, bool fast,
                      void* ws, size_t ws_bytes, cudaStream_t st) {
@@ -631,8 +652,9 @@ ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64
   Ctx c;
   const Staging G = make_staging(m, n, k);
   if ((s = setup(c, m, n, k, N, fast, ws, ws_bytes, st, G.total)) != OZK2_OK) return s;
-  // Timed phases on `st`: 0 start, 1 scaling done (after the uploads it waits for), 2-3
-  // bound product and exponents, 4 residues, 5 last block's CRT, 6 last block back.
+  // Timed phases on `st`: 0 start, 1 last chunk of A scaled (the uploads done), 2 its
+  // bound product, 3 its residues, 4 B's residues (accurate mode), 5 last block's CRT,
+  // 6 last block back.
   mark(c, 0);
   const Layout& L = c.L;
   double* dA = c.at<double>(L.total + G.A);
@@ -660,17 +682,41 @@ ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64
   if ((s = zero_scratch(c, true)) != OZK2_OK) return s;
   OZK2_TRY(cudaStreamWaitEvent(st, ev_b, 0));
   if ((s = scale_operand(c, b, 0, int(n), side_b(L))) != OZK2_OK) return s;
+  // fast mode: f_j depends on column j of B alone (Sec. III-E with the Cauchy-Schwarz
+  // bound), so B's residues need not wait for A
+  auto residues_b = [&]() -> ozk2_status {
+    OZK2_TRY(exponents_of(c, 0, 0, true));
+    OZK2_TRY(residues_operand(c, b, int(n), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesB), L.ldp));
+    t_launches += 1;
+    return OZK2_OK;
+  };
+  if (fast && (s = residues_b()) != OZK2_OK) return s;
+  const int64_t planes_a_stride = int64_t(m) * L.ldp;
   for (int q = 0; q < kHostChunks; ++q) {
     const int64_t i0 = std::min(m, q * chunk), i1 = std::min(m, (q + 1) * chunk);
+    const bool last = q == kHostChunks - 1;
     OZK2_TRY(cudaStreamWaitEvent(st, ev_a[q], 0));
-    if (i1 > i0 && (s = scale_operand(c, shift_lines(a, i0), i0, int(i1 - i0), side_a(L))) != OZK2_OK) return s;
+    if (i1 > i0) {
+      const int rows = int(i1 - i0);
+      const Operand ai = shift_lines(a, i0);
+      if ((s = scale_operand(c, ai, i0, rows, side_a(L))) != OZK2_OK) return s;
+      if (last) mark(c, 1);
+      if (!fast) OZK2_TRY(bound_rows(c, i0, rows));
+      if (last) mark(c, 2);
+      OZK2_TRY(exponents_of(c, i0, rows, false));
+      OZK2_TRY(residues_operand(c, ai, rows, c.at<int32_t>(L.e) + i0, c.at<uint8_t>(L.planesA) + i0 * L.ldp,
+                                L.ldp, planes_a_stride));
+      t_launches += 1;
+    } else if (last) {
+      mark(c, 1);
+      mark(c, 2);
+    }
   }
-  if ((s = bound_and_exponents(c)) != OZK2_OK) return s;
-  OZK2_TRY(residues_operand(c, b, int(n), c.at<int32_t>(L.f), c.at<uint8_t>(L.planesB), L.ldp));
-  t_launches += 1;
+  mark(c, 3);
+  if (!fast && (s = residues_b()) != OZK2_OK) return s;
   // residue products and CRT in output row blocks; each finished block streams back
   const CopyBack cb{hC, ldc, cs, ev_blk};
-  if ((s = products_and_crt(c, a, dC, n, &cb)) != OZK2_OK) return s;
+  if ((s = products_and_crt(c, nullptr, dC, n, &cb)) != OZK2_OK) return s;
   mark(c, 5);
   // the call is complete on `st` once the last block is back on the host
   OZK2_TRY(cudaEventRecord(ev_done, cs));

@@ -83,13 +83,14 @@ cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t*
                              int32_t* e, int32_t* f, cudaStream_t st);
 
 // resid.cu.  Planes: M_N planes of lines x kp bytes, row pitch ldp bytes (>= kp, a
-// multiple of 16), plane stride lines * ldp.
+// multiple of 16), plane stride plane_stride bytes (0: lines * ldp; larger when the
+// lines converted are a slice of a taller operand).
 cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp, int64_t ldp,
                                  const int32_t* e, const ModTable& mt, uint8_t* planes,
-                                 uint32_t* flags, cudaStream_t st);
+                                 uint32_t* flags, cudaStream_t st, int64_t plane_stride = 0);
 cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, int64_t ldp,
                                  const int32_t* f, const ModTable& mt, uint8_t* planes,
-                                 uint32_t* flags, cudaStream_t st);
+                                 uint32_t* flags, cudaStream_t st, int64_t plane_stride = 0);
 
 // gemm.cu
 enum GemmMode { kModeResidue = 0, kModeBound = 1, kModeRaw = 2 };

@@ -356,16 +356,18 @@ int grid_for(int64_t warps) {
 }  // namespace
 
 cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int kp, int64_t ldp, const int32_t* e,
-                                 const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st) {
-  ResidArgs a{A, lda, m, k, kp, ldp, e, planes, static_cast<int64_t>(m) * ldp, flags};
+                                 const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st,
+                                 int64_t plane_stride) {
+  ResidArgs a{A, lda, m, k, kp, ldp, e, planes, plane_stride ? plane_stride : static_cast<int64_t>(m) * ldp, flags};
   const int64_t warps = static_cast<int64_t>(m) * ((kp + kRowSpan - 1) / kRowSpan);
   residues_rows_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, int64_t ldp, const int32_t* f,
-                                 const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st) {
-  ResidArgs a{B, ldb, n, k, kp, ldp, f, planes, static_cast<int64_t>(n) * ldp, flags};
+                                 const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st,
+                                 int64_t plane_stride) {
+  ResidArgs a{B, ldb, n, k, kp, ldp, f, planes, plane_stride ? plane_stride : static_cast<int64_t>(n) * ldp, flags};
   residues_cols_kernel<<<grid_for(cols_items(n, kp)), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }

@@ -27,12 +27,29 @@ def _host(X, pinned):
     (4096, 4096, 512, 12, "accurate", True),   # four output row blocks
     (4000, 3000, 700, 13, "fast", True),       # three ragged row blocks
     (2048, 4096, 300, 12, "accurate", False),  # two blocks, pageable memory
+    (3, 40, 70, 12, "accurate", True),         # fewer rows than upload chunks
+    (515, 300, 260, 14, "fast", True),         # ragged chunks of A, fast mode
 ])
 def test_bit_identical_to_device_call(cuda, m, n, k, N, mode, pinned):
     A, B = workloads.problem(m, n, k, 1.0, seed=30)
     C = ozk.dgemm_host(_host(A, pinned), _host(B, pinned), num_moduli=N, mode=mode)
     ref = ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=N, mode=mode).cpu()
     assert torch.equal(C.view(torch.int64), ref.view(torch.int64))
+    assert ozk.device_status() == "OZK2_OK"
+
+
+def test_column_maxima_from_the_last_chunk(cuda):
+    # A's chunks are bounded and converted while later chunks upload; the column
+    # exponents must still see every chunk: here the largest rows sit in the last one,
+    # and a zero row sits in the first.
+    m, n, k = 1000, 700, 300
+    A, B = workloads.problem(m, n, k, 1.0, seed=31)
+    A = A * torch.exp2(torch.linspace(-30, 30, m, dtype=torch.float64)).unsqueeze(1)
+    A[5] = 0
+    for mode in ("accurate", "fast"):
+        C = ozk.dgemm_host(A.pin_memory(), B.pin_memory(), num_moduli=12, mode=mode)
+        ref = ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=12, mode=mode).cpu()
+        assert torch.equal(C.view(torch.int64), ref.view(torch.int64))
     assert ozk.device_status() == "OZK2_OK"
 
 
