@@ -35,6 +35,7 @@ constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 constexpr int kPieces = 5;  // 11-bit pieces of the 53-bit shifted significand
 constexpr int kElems = 8;  // elements per thread
+constexpr int kPairs = kElems / 2;
 
 // Signed byte pieces of a' (as floats) and t'.
 __device__ __forceinline__ void decode_element(double a, int e, float (&c)[kPieces], int& tp, bool& range_err) {
@@ -69,59 +70,72 @@ __device__ __forceinline__ void decode_element(double a, int e, float (&c)[kPiec
   for (int j = 0; j < kPieces; ++j) c[j] = fmaf(sg, __uint_as_float(0x4B000000u | pieces[j]), off);
 }
 
+// The arithmetic below runs on element pairs: two elements of the same modulus share
+// every constant, so each step is one packed two-wide FP32 instruction of sm_100-class
+// GPUs (__ffma2_rn / __fadd2_rn), which rounds each component exactly like the scalar
+// fmaf / add.  The digits are therefore bit-identical to an element-at-a-time pass.
+using f2 = float2;
+__device__ __forceinline__ f2 dup(float v) { return make_float2(v, v); }
+
 struct ModF {
-  float p, inv_p;
-  float w[kPieces];
+  f2 neg_p, inv_p;
+  f2 w[kPieces];
   bool pow2_modulus;  // p = 1024
 };
 
 // Rounding to an integer without a conversion instruction: for |y| < 2^22, y + 1.5 2^23
 // rounds (to nearest, ties to even) to an integer-valued float, and subtracting
-// 1.5 2^23 is exact.  fmaf(x, inv_p, kMagic) rounds the exact product x (1/p), so the
+// 1.5 2^23 is exact.  fma(x, inv_p, kMagic) rounds the exact product x (1/p), so the
 // quotient estimate carries only the error of inv_p: |x| (1/p) 2^-24 < 1/(2p) for |x| < 2^23.
 // Inputs are never -0 (the pieces c_j come out of an exact FMA as +0 when zero), so
 // no remainder or digit is -0 (E4M3 0x80).
 constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
 
-__device__ __forceinline__ float reduce(float x, const ModF& m) {
+__device__ __forceinline__ f2 round_magic(f2 y) { return __fadd2_rn(y, dup(-kMagic)); }
+
+__device__ __forceinline__ f2 reduce(f2 x, const ModF& m) {
   if (m.pow2_modulus) {
     // floor((x + 512) / 1024) = round((x + 0.5) / 1024) for integer x (never a tie);
     // (x + 0.5) / 1024 is formed exactly by the inner FMA.
-    const float q = (fmaf(x, 0.0009765625f, 0.00048828125f) + kMagic) - kMagic;
-    return fmaf(-1024.0f, q, x);
+    const f2 q = round_magic(__fadd2_rn(__ffma2_rn(x, dup(0.0009765625f), dup(0.00048828125f)), dup(kMagic)));
+    return __ffma2_rn(dup(-1024.0f), q, x);
   }
-  const float q = fmaf(x, m.inv_p, kMagic) - kMagic;
-  return fmaf(-m.p, q, x);
+  const f2 q = round_magic(__ffma2_rn(x, m.inv_p, dup(kMagic)));
+  return __ffma2_rn(m.neg_p, q, x);
 }
 
-__device__ __forceinline__ float residue_of(const float (&c)[kPieces], int tp, const ModF& m, const int16_t* pow2,
-                                            bool use_pow2) {
-  float x = c[0];
+__device__ __forceinline__ f2 residue_of(const f2 (&c)[kPieces], int tp0, int tp1, const ModF& m,
+                                         const int16_t* pow2, bool use_pow2) {
+  f2 x = c[0];
 #pragma unroll
-  for (int j = 1; j < kPieces; ++j) x = fmaf(c[j], m.w[j], x);
-  float r = reduce(x, m);
-  if (use_pow2) r = reduce(fmaf(r, static_cast<float>(pow2[tp]), 0.0f), m);  // +0, never -0
+  for (int j = 1; j < kPieces; ++j) x = __ffma2_rn(c[j], m.w[j], x);
+  f2 r = reduce(x, m);
+  if (use_pow2)  // + 0 gives +0, never -0
+    r = reduce(__ffma2_rn(r, make_float2(static_cast<float>(pow2[tp0]), static_cast<float>(pow2[tp1])), dup(0.0f)),
+               m);
   return r;
 }
 
 // Digits of a residue r (an exact float, never -0); the digits are never -0 either
 // (an exact zero from x - x or x + (-x) is +0 in round-to-nearest).
-__device__ __forceinline__ void square_digits(float r, float s, float inv_s, float& d1, float& d2) {
-  d1 = fmaf(r, inv_s, kMagic) - kMagic;  // round(r / s), ties to even (only s = 32 has ties)
-  d2 = fmaf(-s, d1, r);
+__device__ __forceinline__ void square_digits(f2 r, f2 neg_s, f2 inv_s, f2& d1, f2& d2) {
+  d1 = round_magic(__ffma2_rn(r, inv_s, dup(kMagic)));  // round(r / s), ties to even (only s = 32 has ties)
+  d2 = __ffma2_rn(neg_s, d1, r);
 }
-__device__ __forceinline__ void karatsuba_digits(float r, float& d1, float& d2, float& d3) {
+__device__ __forceinline__ void karatsuba_digits(f2 r, f2& d1, f2& d2, f2& d3) {
   // ceil(|r| / 16) = round((|r| + 7.5) / 16) for integer |r| (never a tie)
-  const float m1 = (fmaf(fabsf(r), 0.0625f, 0.46875f) + kMagic) - kMagic;
-  d1 = copysignf(m1, r);
-  d2 = fmaf(-16.0f, d1, r);
-  d3 = d1 + d2;
+  const f2 a = make_float2(fabsf(r.x), fabsf(r.y));
+  const f2 m1 = round_magic(__fadd2_rn(__ffma2_rn(a, dup(0.0625f), dup(0.46875f)), dup(kMagic)));
+  d1 = make_float2(copysignf(m1.x, r.x), copysignf(m1.y, r.y));
+  d2 = __ffma2_rn(dup(-16.0f), d1, r);
+  d3 = __fadd2_rn(d1, d2);
 }
 
-__device__ __forceinline__ uint32_t e4m3x4(float a, float b, float c, float d) {
-  const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
-  const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
-  return lo | (hi << 16);
+// Four E4M3 bytes, elements in address order: pair lo, then pair hi.
+__device__ __forceinline__ uint32_t e4m3x4(f2 lo, f2 hi) {
+  const uint32_t a = __nv_cvt_float2_to_fp8x2(lo, __NV_SATFINITE, __NV_E4M3);
+  const uint32_t b = __nv_cvt_float2_to_fp8x2(hi, __NV_SATFINITE, __NV_E4M3);
+  return a | (b << 16);
 }
 
 struct ResidArgs {
@@ -144,10 +158,10 @@ __device__ __forceinline__ void load_table(const ModTable& mt, int16_t* pow2_s) 
 
 __device__ __forceinline__ ModF consts_of(const ModTable& mt, int l) {
   ModF m;
-  m.p = static_cast<float>(mt.p[l]);
-  m.inv_p = mt.inv_p[l];
+  m.neg_p = dup(-static_cast<float>(mt.p[l]));
+  m.inv_p = dup(mt.inv_p[l]);
 #pragma unroll
-  for (int j = 0; j < kPieces; ++j) m.w[j] = mt.w11[l][j];
+  for (int j = 0; j < kPieces; ++j) m.w[j] = dup(mt.w11[l][j]);
   m.pow2_modulus = (mt.p[l] == 1024);
   return m;
 }
@@ -156,36 +170,52 @@ __host__ __device__ constexpr int plane_of(int l) {
   return l < kNumSquares ? 2 * l : 2 * kNumSquares + 3 * (l - kNumSquares);
 }
 
-// Digits of the thread's 8 elements for modulus l, packed as E4M3 bytes: words[x][q]
-// holds plane x's bytes of elements 4q .. 4q+3.
-__device__ __forceinline__ void digits_of(const float (&c)[kElems][kPieces], const int (&tp)[kElems],
+// Digits of the thread's 8 elements (4 pairs) for modulus l, packed as E4M3 bytes:
+// words[x][q] holds plane x's bytes of elements 4q .. 4q+3.
+__device__ __forceinline__ void digits_of(const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems],
                                           const ModTable& mt, int l, const int16_t* pow2_s, bool use_pow2,
                                           uint32_t (&words)[3][2]) {
   const ModF m = consts_of(mt, l);
   const int16_t* pw = pow2_s + l * kPow2Table;
   if (l < kNumSquares) {
-    const float s = static_cast<float>(mt.s[l]);
-    const float inv_s = mt.inv_s[l];
+    const f2 neg_s = dup(-static_cast<float>(mt.s[l]));
+    const f2 inv_s = dup(mt.inv_s[l]);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      float d1[4], d2[4];
+      f2 d1[2], d2[2];
 #pragma unroll
-      for (int t = 0; t < 4; ++t) square_digits(residue_of(c[4 * q + t], tp[4 * q + t], m, pw, use_pow2), s, inv_s,
-                                                d1[t], d2[t]);
-      words[0][q] = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
-      words[1][q] = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
+      for (int u = 0; u < 2; ++u) {
+        const int pr = 2 * q + u;
+        square_digits(residue_of(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw, use_pow2), neg_s, inv_s, d1[u], d2[u]);
+      }
+      words[0][q] = e4m3x4(d1[0], d1[1]);
+      words[1][q] = e4m3x4(d2[0], d2[1]);
     }
   } else {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      float d1[4], d2[4], d3[4];
+      f2 d1[2], d2[2], d3[2];
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
-        karatsuba_digits(residue_of(c[4 * q + t], tp[4 * q + t], m, pw, use_pow2), d1[t], d2[t], d3[t]);
-      words[0][q] = e4m3x4(d1[0], d1[1], d1[2], d1[3]);
-      words[1][q] = e4m3x4(d2[0], d2[1], d2[2], d2[3]);
-      words[2][q] = e4m3x4(d3[0], d3[1], d3[2], d3[3]);
+      for (int u = 0; u < 2; ++u) {
+        const int pr = 2 * q + u;
+        karatsuba_digits(residue_of(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw, use_pow2), d1[u], d2[u], d3[u]);
+      }
+      words[0][q] = e4m3x4(d1[0], d1[1]);
+      words[1][q] = e4m3x4(d2[0], d2[1]);
+      words[2][q] = e4m3x4(d3[0], d3[1]);
     }
+  }
+}
+
+// Pieces of element t of the thread's 8, into its pair slot.
+__device__ __forceinline__ void decode_into(f2 (&c)[kPairs][kPieces], int t, double a, int e, int& tp,
+                                            bool& range_err) {
+  float v[kPieces];
+  decode_element(a, e, v, tp, range_err);
+#pragma unroll
+  for (int j = 0; j < kPieces; ++j) {
+    if (t & 1) c[t >> 1][j].y = v[j];
+    else c[t >> 1][j].x = v[j];
   }
 }
 
@@ -207,7 +237,7 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const Mod
     const int base = static_cast<int>(it % nkw) * kRowSpan;
     const double* x = a.X + static_cast<int64_t>(row) * a.ldx;
     const int e = a.exps[row];
-    float c[kElems][kPieces];
+    f2 c[kPairs][kPieces];
     int tp[kElems];
     int any_tp = 0;
 #pragma unroll
@@ -215,7 +245,7 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const Mod
 #pragma unroll
       for (int t = 0; t < 4; ++t) {
         const int h = base + g * 128 + lane * 4 + t;
-        decode_element((h < a.k) ? __ldg(x + h) : 0.0, e, c[4 * g + t], tp[4 * g + t], range_err);
+        decode_into(c, 4 * g + t, (h < a.k) ? __ldg(x + h) : 0.0, e, tp[4 * g + t], range_err);
         any_tp |= tp[4 * g + t];
       }
     }
@@ -276,14 +306,14 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
     const bool active = j < a.lines;
     const int e = active ? a.exps[j] : 0;
     const int h0 = hb * 32 + qq * 8;
-    float c[kElems][kPieces];
+    f2 c[kPairs][kPieces];
     int tp[kElems];
     int any_tp = 0;
 #pragma unroll
     for (int t = 0; t < kElems; ++t) {
       const int h = h0 + t;
       const double val = (active && h < a.k) ? __ldg(a.X + static_cast<int64_t>(h) * a.ldx + j) : 0.0;
-      decode_element(val, e, c[t], tp[t], range_err);
+      decode_into(c, t, val, e, tp[t], range_err);
       any_tp |= tp[t];
     }
     const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
@@ -303,13 +333,13 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
-__global__ void __launch_bounds__(256) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
+__global__ void __launch_bounds__(256, 3) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
   __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
   residues_rows_body(a, mt, pow2_s, blockIdx.x, gridDim.x);
 }
 
-__global__ void __launch_bounds__(256) residues_cols_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
+__global__ void __launch_bounds__(256, 3) residues_cols_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
   __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
   residues_cols_body(a, mt, pow2_s, blockIdx.x, gridDim.x);
