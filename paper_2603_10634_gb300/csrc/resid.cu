@@ -104,15 +104,18 @@ __device__ __forceinline__ f2 reduce(f2 x, const ModF& m) {
   return __ffma2_rn(m.neg_p, q, x);
 }
 
+// P2: some element of the warp has t' > 0 (rare: a' >= 2^53), so the remainder takes the
+// factor 2^t' mod p.  A template argument rather than a branch, so that the common path
+// carries no table loads.
+template <bool P2>
 __device__ __forceinline__ f2 residue_of(const f2 (&c)[kPieces], int tp0, int tp1, const ModF& m,
-                                         const int16_t* pow2, bool use_pow2) {
+                                         const float* pow2) {
   f2 x = c[0];
 #pragma unroll
   for (int j = 1; j < kPieces; ++j) x = __ffma2_rn(c[j], m.w[j], x);
   f2 r = reduce(x, m);
-  if (use_pow2)  // + 0 gives +0, never -0
-    r = reduce(__ffma2_rn(r, make_float2(static_cast<float>(pow2[tp0]), static_cast<float>(pow2[tp1])), dup(0.0f)),
-               m);
+  if constexpr (P2)  // + 0 gives +0, never -0
+    r = reduce(__ffma2_rn(r, make_float2(pow2[tp0], pow2[tp1]), dup(0.0f)), m);
   return r;
 }
 
@@ -150,9 +153,10 @@ struct ResidArgs {
   uint32_t* flags;
 };
 
-__device__ __forceinline__ void load_table(const ModTable& mt, int16_t* pow2_s) {
+__device__ __forceinline__ void load_table(const ModTable& mt, float* pow2_s) {
   const int total = mt.N * kPow2Table;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) pow2_s[i] = mt.pow2[i / kPow2Table][i % kPow2Table];
+  for (int i = threadIdx.x; i < total; i += blockDim.x)
+    pow2_s[i] = static_cast<float>(mt.pow2[i / kPow2Table][i % kPow2Table]);
   __syncthreads();
 }
 
@@ -172,11 +176,12 @@ __host__ __device__ constexpr int plane_of(int l) {
 
 // Digits of the thread's 8 elements (4 pairs) for modulus l, packed as E4M3 bytes:
 // words[x][q] holds plane x's bytes of elements 4q .. 4q+3.
+template <bool P2>
 __device__ __forceinline__ void digits_of(const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems],
-                                          const ModTable& mt, int l, const int16_t* pow2_s, bool use_pow2,
+                                          const ModTable& mt, int l, const float* pow2_s,
                                           uint32_t (&words)[3][2]) {
   const ModF m = consts_of(mt, l);
-  const int16_t* pw = pow2_s + l * kPow2Table;
+  const float* pw = pow2_s + l * kPow2Table;
   if (l < kNumSquares) {
     const f2 neg_s = dup(-static_cast<float>(mt.s[l]));
     const f2 inv_s = dup(mt.inv_s[l]);
@@ -186,7 +191,7 @@ __device__ __forceinline__ void digits_of(const f2 (&c)[kPairs][kPieces], const 
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int pr = 2 * q + u;
-        square_digits(residue_of(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw, use_pow2), neg_s, inv_s, d1[u], d2[u]);
+        square_digits(residue_of<P2>(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw), neg_s, inv_s, d1[u], d2[u]);
       }
       words[0][q] = e4m3x4(d1[0], d1[1]);
       words[1][q] = e4m3x4(d2[0], d2[1]);
@@ -198,7 +203,7 @@ __device__ __forceinline__ void digits_of(const f2 (&c)[kPairs][kPieces], const 
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int pr = 2 * q + u;
-        karatsuba_digits(residue_of(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw, use_pow2), d1[u], d2[u], d3[u]);
+        karatsuba_digits(residue_of<P2>(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw), d1[u], d2[u], d3[u]);
       }
       words[0][q] = e4m3x4(d1[0], d1[1]);
       words[1][q] = e4m3x4(d2[0], d2[1]);
@@ -219,13 +224,62 @@ __device__ __forceinline__ void decode_into(f2 (&c)[kPairs][kPieces], int t, dou
   }
 }
 
+// NM > 0: the number of moduli fixed at compile time (the modulus loop unrolls, every
+// constant sits at a known offset of the table); NM = 0: the table's own count.
+template <int NM>
+__device__ __forceinline__ int moduli_count(const ModTable& mt) {
+  return NM > 0 ? NM : mt.N;
+}
+
+// The planes of one warp item of the row kernel: the lane's 4 bytes at rowp (when
+// store0: inside kp) and at rowp + 128 (when store1).
+template <int NM, bool P2>
+__device__ __forceinline__ void rows_planes(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
+                                            const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems], uint8_t* rowp,
+                                            bool store0, bool store1) {
+#pragma unroll (NM > 0 ? NM : 1)
+  for (int l = 0; l < moduli_count<NM>(mt); ++l) {
+    uint32_t words[3][2];
+    digits_of<P2>(c, tp, mt, l, pow2_s, words);
+    uint8_t* pl = rowp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
+    const int nplanes = (l < kNumSquares) ? 2 : 3;
+#pragma unroll
+    for (int xp = 0; xp < 3; ++xp) {
+      if (xp < nplanes) {
+        if (store0) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride) = words[xp][0];
+        if (store1) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride + 128) = words[xp][1];
+      }
+    }
+  }
+}
+
+// The planes of one warp item of the column kernel: the lane's 8 bytes at colp.
+template <int NM, bool P2>
+__device__ __forceinline__ void cols_planes(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
+                                            const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems], uint8_t* colp,
+                                            bool active) {
+#pragma unroll (NM > 0 ? NM : 1)
+  for (int l = 0; l < moduli_count<NM>(mt); ++l) {
+    uint32_t words[3][2];
+    digits_of<P2>(c, tp, mt, l, pow2_s, words);
+    uint8_t* pl = colp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
+    const int nplanes = (l < kNumSquares) ? 2 : 3;
+    if (active) {
+#pragma unroll
+      for (int xp = 0; xp < 3; ++xp)
+        if (xp < nplanes) *reinterpret_cast<uint2*>(pl + xp * a.plane_stride) = make_uint2(words[xp][0], words[xp][1]);
+    }
+  }
+}
+
 // Rows of A.  One warp covers 256 consecutive k of one row: lane l owns elements
 // base + 128 g + 4 l + {0..3}, g = 0, 1, so loads and 4-byte plane stores coalesce.
 constexpr int kRowSpan = 256;
 
 // vblock / vgrid: the block's index among, and the number of, the blocks serving this
 // operand (the warps stride over its items).
-__device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const ModTable& mt, const int16_t* pow2_s,
+template <int NM>
+__device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
                                                    int64_t vblock, int64_t vgrid) {
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
@@ -249,23 +303,10 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const Mod
         any_tp |= tp[4 * g + t];
       }
     }
-    const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
-    uint8_t* rowp = a.planes + static_cast<int64_t>(row) * a.ldp;
-    for (int l = 0; l < mt.N; ++l) {
-      uint32_t words[3][2];
-      digits_of(c, tp, mt, l, pow2_s, use_pow2, words);
-      uint8_t* pl = rowp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
-      const int nplanes = (l < kNumSquares) ? 2 : 3;
-#pragma unroll
-      for (int g = 0; g < 2; ++g) {
-        const int h = base + g * 128 + lane * 4;
-        if (h < a.kp) {
-#pragma unroll
-          for (int xp = 0; xp < 3; ++xp)
-            if (xp < nplanes) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride + h) = words[xp][g];
-        }
-      }
-    }
+    uint8_t* rowp = a.planes + static_cast<int64_t>(row) * a.ldp + base + lane * 4;
+    const bool store0 = base + lane * 4 < a.kp, store1 = base + 128 + lane * 4 < a.kp;
+    if (__any_sync(0xffffffffu, any_tp != 0)) rows_planes<NM, true>(a, mt, pow2_s, c, tp, rowp, store0, store1);
+    else rows_planes<NM, false>(a, mt, pow2_s, c, tp, rowp, store0, store1);
   }
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
@@ -286,7 +327,8 @@ __host__ __device__ inline int64_t cols_items(int lines, int kp) {
   return ntj * nth * kColTileGroups * kColTileBlocks;
 }
 
-__device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const ModTable& mt, const int16_t* pow2_s,
+template <int NM>
+__device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
                                                    int64_t vblock, int64_t vgrid) {
   const int lane = threadIdx.x & 31;
   const int jj = lane >> 2, qq = lane & 3;
@@ -316,33 +358,25 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
       decode_into(c, t, val, e, tp[t], range_err);
       any_tp |= tp[t];
     }
-    const bool use_pow2 = __any_sync(0xffffffffu, any_tp != 0);
     uint8_t* colp = a.planes + static_cast<int64_t>(active ? j : 0) * a.ldp + h0;
-    for (int l = 0; l < mt.N; ++l) {
-      uint32_t words[3][2];
-      digits_of(c, tp, mt, l, pow2_s, use_pow2, words);
-      uint8_t* pl = colp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
-      const int nplanes = (l < kNumSquares) ? 2 : 3;
-      if (active) {
-#pragma unroll
-        for (int xp = 0; xp < 3; ++xp)
-          if (xp < nplanes) *reinterpret_cast<uint2*>(pl + xp * a.plane_stride) = make_uint2(words[xp][0], words[xp][1]);
-      }
-    }
+    if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(a, mt, pow2_s, c, tp, colp, active);
+    else cols_planes<NM, false>(a, mt, pow2_s, c, tp, colp, active);
   }
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
+template <int NM>
 __global__ void __launch_bounds__(256, 3) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
-  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
+  __shared__ float pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
-  residues_rows_body(a, mt, pow2_s, blockIdx.x, gridDim.x);
+  residues_rows_body<NM>(a, mt, pow2_s, blockIdx.x, gridDim.x);
 }
 
+template <int NM>
 __global__ void __launch_bounds__(256, 3) residues_cols_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
-  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
+  __shared__ float pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
-  residues_cols_body(a, mt, pow2_s, blockIdx.x, gridDim.x);
+  residues_cols_body<NM>(a, mt, pow2_s, blockIdx.x, gridDim.x);
 }
 
 __device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
@@ -357,9 +391,9 @@ __device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ pr
 
 // Grouped: rows of every A, then (second launch) columns of every B.
 template <bool ROWS>
-__global__ void __launch_bounds__(256) residues_batch(const BatchProblem* __restrict__ probs, int count,
+__global__ void __launch_bounds__(256, 3) residues_batch(const BatchProblem* __restrict__ probs, int count,
                                                       uint32_t* flags, const __grid_constant__ ModTable mt) {
-  __shared__ int16_t pow2_s[kMaxModuli * kPow2Table];
+  __shared__ float pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
   constexpr int w = ROWS ? kBkResidRows : kBkResidCols;
   const int p = batch_problem(probs, count, w, blockIdx.x);
@@ -367,10 +401,10 @@ __global__ void __launch_bounds__(256) residues_batch(const BatchProblem* __rest
   const int64_t vb = blockIdx.x - P.first_block[w];
   if constexpr (ROWS) {
     const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.ldp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.ldp, flags};
-    residues_rows_body(a, mt, pow2_s, vb, P.nblocks[w]);
+    residues_rows_body<0>(a, mt, pow2_s, vb, P.nblocks[w]);
   } else {
     const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.ldp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.ldp, flags};
-    residues_cols_body(a, mt, pow2_s, vb, P.nblocks[w]);
+    residues_cols_body<0>(a, mt, pow2_s, vb, P.nblocks[w]);
   }
 }
 
@@ -390,7 +424,11 @@ cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int
                                  int64_t plane_stride) {
   ResidArgs a{A, lda, m, k, kp, ldp, e, planes, plane_stride ? plane_stride : static_cast<int64_t>(m) * ldp, flags};
   const int64_t warps = static_cast<int64_t>(m) * ((kp + kRowSpan - 1) / kRowSpan);
-  residues_rows_kernel<<<grid_for(warps), 256, 0, st>>>(a, mt);
+  const int grid = grid_for(warps);
+  switch (mt.N) {
+    case 12: residues_rows_kernel<12><<<grid, 256, 0, st>>>(a, mt); break;
+    default: residues_rows_kernel<0><<<grid, 256, 0, st>>>(a, mt); break;
+  }
   return cudaGetLastError();
 }
 
@@ -398,7 +436,11 @@ cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int
                                  const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st,
                                  int64_t plane_stride) {
   ResidArgs a{B, ldb, n, k, kp, ldp, f, planes, plane_stride ? plane_stride : static_cast<int64_t>(n) * ldp, flags};
-  residues_cols_kernel<<<grid_for(cols_items(n, kp)), 256, 0, st>>>(a, mt);
+  const int grid = grid_for(cols_items(n, kp));
+  switch (mt.N) {
+    case 12: residues_cols_kernel<12><<<grid, 256, 0, st>>>(a, mt); break;
+    default: residues_cols_kernel<0><<<grid, 256, 0, st>>>(a, mt); break;
+  }
   return cudaGetLastError();
 }
 
