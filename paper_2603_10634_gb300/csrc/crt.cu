@@ -128,9 +128,19 @@ __device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64
   constexpr int L = limbs_for(N);
   const int nq = (n + 1) >> 1;
   const int64_t total = static_cast<int64_t>(m) * nq;
-  for (int64_t it = vblock * blockDim.x + threadIdx.x; it < total; it += vgrid * blockDim.x) {
-    const int i = static_cast<int>(it / nq);
-    const int j0 = static_cast<int>(it % nq) * 2;
+  const int64_t stride = vgrid * blockDim.x;
+  const int64_t first = vblock * blockDim.x + threadIdx.x;
+  if (first >= total) return;
+  // (row, column pair) of the item, advanced by the stride's own quotient and remainder
+  // instead of a 64-bit division per item (the stride is at most a few grids of threads)
+  int i = static_cast<int>(first / nq), jq = static_cast<int>(first % nq);
+  const int di = static_cast<int>(stride / nq), dj = static_cast<int>(stride % nq);
+  for (; i < m; i += di, jq += dj) {
+    if (jq >= nq) {
+      jq -= nq;
+      if (++i >= m) break;
+    }
+    const int j0 = jq * 2;
     const int16_t* src = cres + static_cast<int64_t>(i) * ldr + j0;
     uint64_t acc[2][L];
     uint32_t est[2] = {0u, 0u};

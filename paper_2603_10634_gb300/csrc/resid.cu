@@ -285,10 +285,20 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const Mod
   const int warps_per_block = blockDim.x >> 5;
   const int nkw = (a.kp + kRowSpan - 1) / kRowSpan;
   const int64_t items = static_cast<int64_t>(a.lines) * nkw;
+  const int64_t stride = vgrid * warps_per_block;
+  const int64_t first = vblock * warps_per_block + (threadIdx.x >> 5);
+  if (first >= items) return;
+  // (row, k chunk) of the item, advanced by the stride's quotient and remainder
+  // instead of a 64-bit division per item (the stride is at most a few grids of warps)
+  int row = static_cast<int>(first / nkw), chunk = static_cast<int>(first % nkw);
+  const int drow = static_cast<int>(stride / nkw), dchunk = static_cast<int>(stride % nkw);
   bool range_err = false;
-  for (int64_t it = vblock * warps_per_block + (threadIdx.x >> 5); it < items; it += vgrid * warps_per_block) {
-    const int row = static_cast<int>(it / nkw);
-    const int base = static_cast<int>(it % nkw) * kRowSpan;
+  for (; row < a.lines; row += drow, chunk += dchunk) {
+    if (chunk >= nkw) {
+      chunk -= nkw;
+      if (++row >= a.lines) break;
+    }
+    const int base = chunk * kRowSpan;
     const double* x = a.X + static_cast<int64_t>(row) * a.ldx;
     const int e = a.exps[row];
     f2 c[kPairs][kPieces];
@@ -337,12 +347,33 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
   const int nkb = a.kp / 32;
   const int ntj = (ncg + kColTileGroups - 1) / kColTileGroups;
   const int64_t items = cols_items(a.lines, a.kp);
+  constexpr int kTileItems = kColTileGroups * kColTileBlocks;
+  const int64_t stride = vgrid * warps_per_block;
+  int64_t it = vblock * warps_per_block + (threadIdx.x >> 5);
+  if (it >= items) return;
+  // item -> (item within its tile w, tile column tj, tile row th), advanced by the
+  // stride's own decomposition instead of 64-bit divisions per item
+  int w = static_cast<int>(it % kTileItems);
+  int tj = static_cast<int>((it / kTileItems) % ntj), th = static_cast<int>((it / kTileItems) / ntj);
+  const int dw = static_cast<int>(stride % kTileItems);
+  const int dtj = static_cast<int>((stride / kTileItems) % ntj), dth = static_cast<int>((stride / kTileItems) / ntj);
+  auto advance = [&]() {
+    w += dw;
+    tj += dtj;
+    th += dth;
+    if (w >= kTileItems) {
+      w -= kTileItems;
+      ++tj;
+    }
+    if (tj >= ntj) {
+      tj -= ntj;
+      ++th;
+    }
+  };
   bool range_err = false;
-  for (int64_t it = vblock * warps_per_block + (threadIdx.x >> 5); it < items; it += vgrid * warps_per_block) {
-    const int64_t tile = it / (kColTileGroups * kColTileBlocks);
-    const int w = static_cast<int>(it % (kColTileGroups * kColTileBlocks));
-    const int cg = static_cast<int>(tile % ntj) * kColTileGroups + w % kColTileGroups;
-    const int hb = static_cast<int>(tile / ntj) * kColTileBlocks + w / kColTileGroups;
+  for (; it < items; it += stride, advance()) {
+    const int cg = tj * kColTileGroups + w % kColTileGroups;
+    const int hb = th * kColTileBlocks + w / kColTileGroups;
     if (cg >= ncg || hb >= nkb) continue;  // past the edge of a partial tile (warp-uniform)
     const int j = cg * 8 + jj;
     const bool active = j < a.lines;
@@ -408,6 +439,33 @@ __global__ void __launch_bounds__(256, 3) residues_batch(const BatchProblem* __r
   }
 }
 
+// Launch with the modulus loop unrolled for N in [kUnrollLo, kUnrollHi] (the counts the
+// moduli tuner and the benchmarks use), the generic loop otherwise.
+constexpr int kUnrollLo = 8, kUnrollHi = 16;
+
+struct RowsKernel {
+  template <int NM>
+  static void launch(int grid, cudaStream_t st, const ResidArgs& a, const ModTable& mt) {
+    residues_rows_kernel<NM><<<grid, 256, 0, st>>>(a, mt);
+  }
+};
+struct ColsKernel {
+  template <int NM>
+  static void launch(int grid, cudaStream_t st, const ResidArgs& a, const ModTable& mt) {
+    residues_cols_kernel<NM><<<grid, 256, 0, st>>>(a, mt);
+  }
+};
+
+template <class K, int NM = kUnrollLo>
+void launch_unrolled(const ModTable& mt, int grid, cudaStream_t st, const ResidArgs& a) {
+  if constexpr (NM > kUnrollHi) {
+    K::template launch<0>(grid, st, a, mt);
+  } else {
+    if (mt.N == NM) K::template launch<NM>(grid, st, a, mt);
+    else launch_unrolled<K, NM + 1>(mt, grid, st, a);
+  }
+}
+
 int grid_for(int64_t warps) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -425,10 +483,7 @@ cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int
   ResidArgs a{A, lda, m, k, kp, ldp, e, planes, plane_stride ? plane_stride : static_cast<int64_t>(m) * ldp, flags};
   const int64_t warps = static_cast<int64_t>(m) * ((kp + kRowSpan - 1) / kRowSpan);
   const int grid = grid_for(warps);
-  switch (mt.N) {
-    case 12: residues_rows_kernel<12><<<grid, 256, 0, st>>>(a, mt); break;
-    default: residues_rows_kernel<0><<<grid, 256, 0, st>>>(a, mt); break;
-  }
+  launch_unrolled<RowsKernel>(mt, grid, st, a);
   return cudaGetLastError();
 }
 
@@ -437,10 +492,7 @@ cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int
                                  int64_t plane_stride) {
   ResidArgs a{B, ldb, n, k, kp, ldp, f, planes, plane_stride ? plane_stride : static_cast<int64_t>(n) * ldp, flags};
   const int grid = grid_for(cols_items(n, kp));
-  switch (mt.N) {
-    case 12: residues_cols_kernel<12><<<grid, 256, 0, st>>>(a, mt); break;
-    default: residues_cols_kernel<0><<<grid, 256, 0, st>>>(a, mt); break;
-  }
+  launch_unrolled<ColsKernel>(mt, grid, st, a);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,11 @@ def oracle_codes(digits):
 
 
 @pytest.mark.parametrize("m,n,k,phi,N", [(64, 48, 100, 0.5, 12), (37, 29, 1100, 2.0, 7),
-                                         (16, 16, 40, 1.0, 20), (8, 9, 3, 1.0, 4)])
+                                         (16, 16, 40, 1.0, 20), (8, 9, 3, 1.0, 4),
+                                         # the unrolled kernels (N = 8 .. 16); at N = 16
+                                         # many elements have t' > 0 (the 2^t' mod p path)
+                                         (19, 70, 530, 0.5, 8), (33, 17, 257, 1.0, 13),
+                                         (40, 33, 300, 1.0, 16)])
 def test_digit_planes_bit_exact(cuda, m, n, k, phi, N):
     A, B = workloads.problem(m, n, k, phi, seed=k)
     sc = ozk.scales(A.to(cuda), B.to(cuda), num_moduli=N)
