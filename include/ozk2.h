@@ -156,10 +156,11 @@ size_t ozk2_workspace_size_ex(int64_t m, int64_t n, int64_t k, int num_moduli,
  * leading dimensions and ops as ozk2_dgemm_ex, no blocking).
  *
  * The library copies B and then A (in four line chunks) to the device on its own copy
- * stream while the scaling of what has arrived runs on `stream`; after the exponents
- * and residues, the residue products and the CRT run in output row blocks and each
- * block is copied back while the next one is computed.  The device arithmetic is that
- * of ozk2_dgemm_ex, so C is bit-identical to the device-buffer call.
+ * stream while the scaling, bound product and residues of what has arrived run on
+ * `stream`; the residue products and the CRT then run in output row blocks and each
+ * block is copied back (on a second copy stream) while the next one is computed.  The
+ * device arithmetic is that of ozk2_dgemm_ex, so C is bit-identical to the
+ * device-buffer call.
  *   A, B, C    host pointers.  Page-locked (pinned) memory lets the copies overlap the
  *              kernels; pageable memory works, with less overlap.  They must stay valid
  *              and A, B unchanged until `stream` reaches the end of the call.
@@ -177,6 +178,31 @@ ozk2_status ozk2_dgemm_host(ozk2_op transa, ozk2_op transb,
                             int num_moduli, ozk2_mode mode,
                             void *workspace, size_t workspace_bytes,
                             ozk2_stream_t stream);
+
+/*
+ * ozk2_dgemm_host_ex - ozk2_dgemm_host with flags (0: exactly ozk2_dgemm_host).
+ *
+ *   OZK2_HOST_INPUTS_READY  A and B are complete in host memory when the call is made
+ *              (no earlier work on `stream` writes them).  Then, with the library-owned
+ *              workspace (workspace = NULL) and when the previous call that used that
+ *              workspace was a host-buffer call of the same sizes, the upload of A and B
+ *              starts as soon as that call's kernels have read its own staged inputs for
+ *              the last time, instead of after all earlier work on `stream`: back-to-back
+ *              calls then overlap each upload with the previous call's residue products.
+ *              Every kernel of the call still runs after earlier work on `stream`, and C
+ *              is complete when `stream` reaches the end of the call, as without the flag.
+ * Other flag bits: OZK2_ERR_INVALID_VALUE.
+ */
+#define OZK2_HOST_INPUTS_READY 1u
+
+ozk2_status ozk2_dgemm_host_ex(ozk2_op transa, ozk2_op transb,
+                               int64_t m, int64_t n, int64_t k,
+                               const double *A, int64_t lda,
+                               const double *B, int64_t ldb,
+                               double *C, int64_t ldc,
+                               int num_moduli, ozk2_mode mode, unsigned flags,
+                               void *workspace, size_t workspace_bytes,
+                               ozk2_stream_t stream);
 
 /* ozk2_workspace_size_host - workspace bytes of one ozk2_dgemm_host call; 0 on
  * invalid arguments. */

@@ -28,6 +28,8 @@ SIGNATURES = {
     "ozk2_workspace_size_ex": (c_size_t, [c_i64, c_i64, c_i64, c_int, c_int, c_i64, c_i64]),
     "ozk2_dgemm_host": (c_int, [c_int, c_int, c_i64, c_i64, c_i64, c_void_p, c_i64, c_void_p, c_i64, c_void_p, c_i64,
                                 c_int, c_int, c_void_p, c_size_t, c_void_p]),
+    "ozk2_dgemm_host_ex": (c_int, [c_int, c_int, c_i64, c_i64, c_i64, c_void_p, c_i64, c_void_p, c_i64, c_void_p,
+                                   c_i64, c_int, c_int, ctypes.c_uint, c_void_p, c_size_t, c_void_p]),
     "ozk2_workspace_size_host": (c_size_t, [c_i64, c_i64, c_i64, c_int, c_int]),
     "ozk2_debug_scales_ex": (c_int, [c_int, c_int, c_i64, c_i64, c_i64, c_void_p, c_i64, c_void_p, c_i64, c_int, c_int,
                                      c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,

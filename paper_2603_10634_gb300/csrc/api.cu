@@ -166,6 +166,7 @@ struct Ctx {
   int m, n, k, N;
   bool fast;
   bool timed = true;  // record the per-phase timing events (sequential calls only)
+  uint64_t owned_use = 0;  // > 0: the call runs in the library-owned workspace, its use number
   Layout L;
   uint8_t* ws;
   const Tables* tab;
@@ -181,15 +182,18 @@ struct Ctx {
 struct OwnedWs {
   void* ptr = nullptr;
   size_t bytes = 0;
+  uint64_t uses = 0;  // calls that have taken it
 };
 std::mutex g_ws_mutex;
 OwnedWs g_ws[64];
 
-uint8_t* owned_workspace(size_t need, ozk2_status* err) {
+uint8_t* owned_workspace(size_t need, ozk2_status* err, uint64_t* use = nullptr) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_ws_mutex);
   OwnedWs& w = g_ws[dev];
+  ++w.uses;
+  if (use) *use = w.uses;
   if (w.bytes < need) {
     if (w.ptr) cudaFree(w.ptr);
     w.ptr = nullptr;
@@ -464,7 +468,7 @@ ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, bool fast, voi
     c.ws = static_cast<uint8_t*>(ws);
   } else {
     ozk2_status err = OZK2_OK;
-    c.ws = owned_workspace(c.L.total + extra, &err);
+    c.ws = owned_workspace(c.L.total + extra, &err, &c.owned_use);
     if (!c.ws) return err;
   }
   return OZK2_OK;
@@ -593,8 +597,15 @@ constexpr int kHostChunks = 4;  // A arrives in this many line chunks
 constexpr int kHostEvents = 2 + kHostChunks + kMaxRowBlocks + 1;
 
 struct CopyEngine {
-  cudaStream_t cs = nullptr;
+  cudaStream_t up = nullptr, down = nullptr;  // host-to-device and device-to-host copies
   cudaEvent_t ev[kHostEvents] = {};
+  // The last host-buffer call in the owned workspace: recorded on its stream once its
+  // kernels have read the staged A and B for the last time, with the workspace use
+  // number and the staging range of that call.
+  cudaEvent_t staged_free = nullptr;
+  uint64_t staged_use = 0;
+  const uint8_t* staged_at = nullptr;
+  size_t staged_bytes = 0;
 };
 std::mutex g_copy_mutex;
 CopyEngine g_copy[64];
@@ -608,10 +619,11 @@ CopyEngine* copy_engine(ozk2_status* err) {
   }
   std::lock_guard<std::mutex> lk(g_copy_mutex);
   CopyEngine& e = g_copy[dev];
-  if (!e.cs) {
-    if (cudaStreamCreateWithFlags(&e.cs, cudaStreamNonBlocking) != cudaSuccess) {
+  if (!e.up) {
+    if (cudaStreamCreateWithFlags(&e.down, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&e.up, cudaStreamNonBlocking) != cudaSuccess) {
       *err = OZK2_ERR_CUDA;
-      e.cs = nullptr;
+      e.up = nullptr;
       return nullptr;
     }
     for (auto& ev : e.ev)
@@ -619,6 +631,10 @@ CopyEngine* copy_engine(ozk2_status* err) {
         *err = OZK2_ERR_CUDA;
         return nullptr;
       }
+    if (cudaEventCreateWithFlags(&e.staged_free, cudaEventDisableTiming) != cudaSuccess) {
+      *err = OZK2_ERR_CUDA;
+      return nullptr;
+    }
   }
   return &e;
 }
@@ -645,7 +661,7 @@ cudaError_t copy_lines_h2d(double* dst, const double* src, int64_t ld, bool kcon
 // same arithmetic as in the device-buffer call, so the results are bit-identical.
 ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* hA,
                      int64_t lda, const double* hB, int64_t ldb, double* hC, int64_t ldc, int N, bool fast,
-                     void* ws, size_t ws_bytes, cudaStream_t st) {
+                     unsigned flags, void* ws, size_t ws_bytes, cudaStream_t st) {
   ozk2_status s;
   CopyEngine* ce = copy_engine(&s);
   if (!ce) return s;
@@ -663,20 +679,30 @@ ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64
   const bool a_kc = transa == OZK2_OP_N, b_kc = transb == OZK2_OP_T;
   const Operand a = operand_a(transa, dA, a_kc ? k : m);
   const Operand b = operand_b(transb, dB, b_kc ? k : n);
-  cudaStream_t cs = ce->cs;
+  cudaStream_t up = ce->up;
   cudaEvent_t* ev = ce->ev;
   cudaEvent_t ev_start = ev[0], ev_b = ev[1], *ev_a = ev + 2, *ev_blk = ev + 2 + kHostChunks,
               ev_done = ev[kHostEvents - 1];
 
-  // nothing is copied into the workspace before earlier work on `st` is done with it
-  OZK2_TRY(cudaEventRecord(ev_start, st));
-  OZK2_TRY(cudaStreamWaitEvent(cs, ev_start, 0));
-  OZK2_TRY(copy_lines_h2d(dB, hB, ldb, b_kc, n, k, 0, n, cs));
-  OZK2_TRY(cudaEventRecord(ev_b, cs));
+  // Nothing is copied into the workspace before earlier work on `st` is done with it.
+  // With OZK2_HOST_INPUTS_READY, when the previous use of the owned workspace was a host
+  // call with the same staging, "done with it" is that call's last read of its staged
+  // A and B, so the upload overlaps its residue products.
+  const uint8_t* stage = c.ws + L.total;
+  const bool early = (flags & OZK2_HOST_INPUTS_READY) && c.owned_use > 0 && ce->staged_use + 1 == c.owned_use &&
+                     ce->staged_at == stage && ce->staged_bytes == G.total;
+  if (early) {
+    OZK2_TRY(cudaStreamWaitEvent(up, ce->staged_free, 0));
+  } else {
+    OZK2_TRY(cudaEventRecord(ev_start, st));
+    OZK2_TRY(cudaStreamWaitEvent(up, ev_start, 0));
+  }
+  OZK2_TRY(copy_lines_h2d(dB, hB, ldb, b_kc, n, k, 0, n, up));
+  OZK2_TRY(cudaEventRecord(ev_b, up));
   const int64_t chunk = (m + kHostChunks - 1) / kHostChunks;
   for (int q = 0; q < kHostChunks; ++q) {
-    OZK2_TRY(copy_lines_h2d(dA, hA, lda, a_kc, m, k, std::min(m, q * chunk), std::min(m, (q + 1) * chunk), cs));
-    OZK2_TRY(cudaEventRecord(ev_a[q], cs));
+    OZK2_TRY(copy_lines_h2d(dA, hA, lda, a_kc, m, k, std::min(m, q * chunk), std::min(m, (q + 1) * chunk), up));
+    OZK2_TRY(cudaEventRecord(ev_a[q], up));
   }
 
   if ((s = zero_scratch(c, true)) != OZK2_OK) return s;
@@ -714,12 +740,17 @@ ozk2_status run_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64
   }
   mark(c, 3);
   if (!fast && (s = residues_b()) != OZK2_OK) return s;
+  // the staged A and B are not read again by this call
+  OZK2_TRY(cudaEventRecord(ce->staged_free, st));
+  ce->staged_use = c.owned_use;
+  ce->staged_at = stage;
+  ce->staged_bytes = G.total;
   // residue products and CRT in output row blocks; each finished block streams back
-  const CopyBack cb{hC, ldc, cs, ev_blk};
+  const CopyBack cb{hC, ldc, ce->down, ev_blk};
   if ((s = products_and_crt(c, nullptr, dC, n, &cb)) != OZK2_OK) return s;
   mark(c, 5);
   // the call is complete on `st` once the last block is back on the host
-  OZK2_TRY(cudaEventRecord(ev_done, cs));
+  OZK2_TRY(cudaEventRecord(ev_done, ce->down));
   OZK2_TRY(cudaStreamWaitEvent(st, ev_done, 0));
   mark(c, 6);
   return OZK2_OK;
@@ -1112,9 +1143,17 @@ ozk2_status ozk2_dgemm_ex(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, 
 ozk2_status ozk2_dgemm_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
                             int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int num_moduli,
                             ozk2_mode mode, void* workspace, size_t workspace_bytes, ozk2_stream_t stream) {
+  return ozk2_dgemm_host_ex(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode, 0u, workspace,
+                            workspace_bytes, stream);
+}
+
+ozk2_status ozk2_dgemm_host_ex(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
+                               int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int num_moduli,
+                               ozk2_mode mode, unsigned flags, void* workspace, size_t workspace_bytes,
+                               ozk2_stream_t stream) {
   t_launches = 0;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  if (!valid_mode(mode)) return OZK2_ERR_INVALID_VALUE;
+  if (!valid_mode(mode) || (flags & ~unsigned(OZK2_HOST_INPUTS_READY))) return OZK2_ERR_INVALID_VALUE;
   ozk2_status s = validate(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli);
   if (s != OZK2_OK) return s;
   if (m == 0 || n == 0) return OZK2_OK;
@@ -1123,8 +1162,8 @@ ozk2_status ozk2_dgemm_host(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n
     for (int64_t i = 0; i < m; ++i) std::memset(C + i * ldc, 0, size_t(n) * 8);
     return OZK2_OK;
   }
-  return run_host(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode == OZK2_MODE_FAST, workspace,
-                  workspace_bytes, st);
+  return run_host(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, num_moduli, mode == OZK2_MODE_FAST, flags,
+                  workspace, workspace_bytes, st);
 }
 
 size_t ozk2_workspace_size_host(int64_t m, int64_t n, int64_t k, int num_moduli, ozk2_mode mode) {

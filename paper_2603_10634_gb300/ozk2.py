@@ -137,13 +137,16 @@ def workspace_size_host(m, n, k, num_moduli=12, mode="accurate"):
     return int(_lib.load().ozk2_workspace_size_host(m, n, k, num_moduli, _mode(mode)))
 
 
-def dgemm_host(A, B, num_moduli=12, out=None, mode="accurate", workspace=None, device=None, sync=True):
+def dgemm_host(A, B, num_moduli=12, out=None, mode="accurate", workspace=None, device=None, sync=True,
+               inputs_ready=False):
     """C = A @ B with A, B and C in host memory (float64 CPU tensors; A and B row-major
     or transposed views, C row-major; pinned memory lets the copies overlap the
     kernels).  The library moves the data and pipelines the copies with the kernels on
     ``device`` (default: the current CUDA device) and its current stream.  With
     ``sync`` the call waits for the stream, otherwise ``out`` is complete only once the
-    stream is."""
+    stream is.  ``inputs_ready`` (OZK2_HOST_INPUTS_READY): A and B are final when the
+    call is made, so back-to-back calls in the library-owned workspace may upload their
+    inputs while the previous call is still computing."""
     ta, lda = _operand(A, "A", on_host=True)
     tb, ldb = _operand(B, "B", on_host=True)
     m, k = A.shape
@@ -162,9 +165,9 @@ def dgemm_host(A, B, num_moduli=12, out=None, mode="accurate", workspace=None, d
     lib = _lib.load()
     with torch.cuda.device(dev):
         st = torch.cuda.current_stream(dev)
-        s = lib.ozk2_dgemm_host(ta, tb, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(out), ldc, num_moduli, _mode(mode),
-                                _ptr(workspace), 0 if workspace is None else workspace.numel(),
-                                ctypes.c_void_p(st.cuda_stream))
+        s = lib.ozk2_dgemm_host_ex(ta, tb, m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(out), ldc, num_moduli,
+                                   _mode(mode), 1 if inputs_ready else 0, _ptr(workspace),
+                                   0 if workspace is None else workspace.numel(), ctypes.c_void_p(st.cuda_stream))
         _lib.check(s, "ozk2_dgemm_host")
         if sync:
             st.synchronize()

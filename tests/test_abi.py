@@ -37,7 +37,7 @@ def test_header_declares_the_boundary():
                      "ozk2_device_status", "ozk2_moduli", "ozk2_debug_fp8_gemm", "ozk2_debug_scales",
                      "ozk2_debug_residue_planes", "ozk2_debug_residue_products", "ozk2_debug_crt",
                      "ozk2_dgemm_ex", "ozk2_workspace_size_ex", "ozk2_debug_scales_ex", "ozk2_dgemm_noalloc",
-                     "ozk2_dgemm_host", "ozk2_workspace_size_host", "ozk2_dgemm_batched",
+                     "ozk2_dgemm_host", "ozk2_dgemm_host_ex", "ozk2_workspace_size_host", "ozk2_dgemm_batched",
                      "ozk2_batch_plan_create", "ozk2_batch_plan_execute", "ozk2_batch_plan_destroy",
                      "ozk2_workspace_size_batched"]:
         assert required in names
@@ -150,6 +150,10 @@ def test_host_entry_validation_and_size(lib):
     assert host(0, 0, 4, 4, 8, bogus, 4, bogus, 4, bogus, 4, 12, 0, null, 0, null) == 1  # lda < k
     assert host(0, 0, 4, 4, 4, null, 4, bogus, 4, bogus, 4, 12, 0, null, 0, null) == 1
     assert host(0, 0, 0, 4, 4, null, 4, null, 4, null, 4, 12, 0, null, 0, null) == 0  # empty
+    hx = lib.ozk2_dgemm_host_ex
+    assert hx(0, 0, 0, 4, 4, null, 4, null, 4, null, 4, 12, 0, 1, null, 0, null) == 0  # inputs-ready flag
+    assert hx(0, 0, 0, 4, 4, null, 4, null, 4, null, 4, 12, 0, 2, null, 0, null) == 1  # unknown flag
+    assert hx(0, 0, 4, 4, 8, bogus, 4, bogus, 4, bogus, 4, 12, 0, 1, null, 0, null) == 1  # lda < k
     m, n, k, N = 1000, 700, 300, 12
     for mode in (0, 1):
         staged = 8 * (m * k + k * n + m * n)

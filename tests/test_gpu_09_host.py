@@ -53,6 +53,30 @@ def test_column_maxima_from_the_last_chunk(cuda):
     assert ozk.device_status() == "OZK2_OK"
 
 
+def test_pipelined_calls_with_inputs_ready(cuda):
+    # Back-to-back calls with OZK2_HOST_INPUTS_READY upload while the previous call
+    # computes; a device-buffer call, a change of shape or of mode in between must fall
+    # back to waiting for the stream.  Every result must equal its device-buffer call.
+    s1, s2 = (1500, 1300, 700), (900, 1100, 500)
+    shapes = [s1, s1, s1, s1, s2, s2, s2, s2]
+    modes = ["accurate"] * 6 + ["fast"] * 2
+    probs = [workloads.problem(m, n, k, 1.0, seed=40 + i) for i, (m, n, k) in enumerate(shapes)]
+    outs = [torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64).pin_memory() for A, B in probs]
+    hosts = [(A.pin_memory(), B.pin_memory()) for A, B in probs]
+    mid = None
+    for i, ((hA, hB), o) in enumerate(zip(hosts, outs)):
+        ozk.dgemm_host(hA, hB, num_moduli=12, out=o, sync=False, inputs_ready=True, mode=modes[i])
+        if i == 1:  # a device-buffer call in the same owned workspace
+            A, B = probs[0]
+            mid = ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=12)
+    torch.cuda.current_stream().synchronize()
+    for i, ((A, B), o) in enumerate(zip(probs, outs)):
+        ref = ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=12, mode=modes[i]).cpu()
+        assert torch.equal(o.view(torch.int64), ref.view(torch.int64)), i
+    assert torch.equal(mid.cpu().view(torch.int64), outs[0].view(torch.int64))
+    assert ozk.device_status() == "OZK2_OK"
+
+
 @pytest.mark.parametrize("ta,tb", [(True, False), (False, True), (True, True)])
 def test_transposed_host_views(cuda, ta, tb):
     m, n, k, N = 600, 520, 333, 12
