@@ -212,7 +212,7 @@ uint8_t* owned_workspace(size_t need, ozk2_status* err, uint64_t* use = nullptr)
 }
 
 // ------------------------------------------------------------------ timing
-constexpr int kMaxRowBlocks = 4;  // output row blocks of a host-buffer call
+constexpr int kMaxRowBlocks = 5;  // output row blocks of a host-buffer call (4 + the split tail)
 
 struct Timing {
   bool enabled = false;
@@ -484,10 +484,23 @@ struct CopyBack {
 };
 
 // Row blocks of a host-buffer call: each at least 16 waves of GEMM units (a persistent
-// launch loses up to one wave at its end), at most kMaxRowBlocks, 128-row aligned.
-int64_t row_blocks(const Ctx& c) {
+// launch loses up to one wave at its end), at most four, 128-row aligned.  When there
+// are several, the last is split a quarter from its end, so that the download left
+// after the last CRT is a quarter of a block.  Returns the count; first[b] is the first
+// row of block b, first[count] = m.
+int row_blocks(const Ctx& c, int64_t (&first)[kMaxRowBlocks + 1]) {
   const int64_t units = ((int64_t(c.m) + 127) / 128) * ((int64_t(c.n) + 255) / 256) * c.N;
-  return std::max<int64_t>(1, std::min<int64_t>(kMaxRowBlocks, units / (16 * int64_t(c.num_sms))));
+  const int64_t nb = std::max<int64_t>(1, std::min<int64_t>(4, units / (16 * int64_t(c.num_sms))));
+  const int64_t rb = ((c.m + nb - 1) / nb + 127) / 128 * 128;
+  int count = 0;
+  for (int64_t i0 = 0; i0 < c.m; i0 += rb) first[count++] = i0;
+  if (count > 1) {
+    const int64_t last = first[count - 1], rows = c.m - last;
+    const int64_t tail = ((rows + 3) / 4 + 127) / 128 * 128;
+    if (rows > tail) first[count++] = c.m - tail;
+  }
+  first[count] = c.m;
+  return count;
 }
 
 // After the scaling, the exponents and B's residues (all on c.st): A's residues (unless
@@ -512,10 +525,11 @@ ozk2_status products_and_crt(Ctx& c, const Operand* a, double* C, int64_t ldc, c
     if ((s = phase_products(c)) != OZK2_OK) return s;
     return phase_crt(c, e, f, rs, cs, C, ldc);
   }
-  const int64_t nb = row_blocks(c);
-  const int64_t rb = ((c.m + nb - 1) / nb + 127) / 128 * 128;
-  for (int64_t i0 = 0, b = 0; i0 < c.m; i0 += rb, ++b) {
-    const int rows = int(std::min(rb, int64_t(c.m) - i0));
+  int64_t first[kMaxRowBlocks + 1];
+  const int nb = row_blocks(c, first);
+  for (int b = 0; b < nb; ++b) {
+    const int64_t i0 = first[b];
+    const int rows = int(first[b + 1] - i0);
     if ((s = products_rows(c, i0, rows, c.st)) != OZK2_OK) return s;
     if ((s = crt_rows(c, i0, rows, e, f, rs, cs, C + i0 * ldc, ldc, c.st)) != OZK2_OK) return s;
     OZK2_TRY(cudaEventRecord(cb->done[b], c.st));
