@@ -77,6 +77,21 @@ def test_pipelined_calls_with_inputs_ready(cuda):
     assert ozk.device_status() == "OZK2_OK"
 
 
+def test_inputs_ready_with_caller_workspace(cuda):
+    # a caller workspace never takes the early start: the flag only asserts the inputs
+    m, n, k = 700, 500, 900
+    ws = torch.empty(ozk.workspace_size_host(m, n, k, 12), dtype=torch.uint8, device=cuda)
+    probs = [workloads.problem(m, n, k, 1.0, seed=60 + i) for i in range(3)]
+    outs = []
+    for A, B in probs:
+        outs.append(ozk.dgemm_host(A.pin_memory(), B.pin_memory(), num_moduli=12, workspace=ws, sync=False,
+                                   inputs_ready=True))
+    torch.cuda.current_stream().synchronize()
+    for (A, B), o in zip(probs, outs):
+        ref = ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=12).cpu()
+        assert torch.equal(o.view(torch.int64), ref.view(torch.int64))
+
+
 @pytest.mark.parametrize("ta,tb", [(True, False), (False, True), (True, True)])
 def test_transposed_host_views(cuda, ta, tb):
     m, n, k, N = 600, 520, 333, 12
