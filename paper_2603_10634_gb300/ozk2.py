@@ -144,9 +144,12 @@ def dgemm_host(A, B, num_moduli=12, out=None, mode="accurate", workspace=None, d
     kernels).  The library moves the data and pipelines the copies with the kernels on
     ``device`` (default: the current CUDA device) and its current stream.  With
     ``sync`` the call waits for the stream, otherwise ``out`` is complete only once the
-    stream is.  ``inputs_ready`` (OZK2_HOST_INPUTS_READY): A and B are final when the
-    call is made, so back-to-back calls in the library-owned workspace may upload their
-    inputs while the previous call is still computing."""
+    stream is, and A, B (and ``out``) must be kept alive and A, B unchanged until then:
+    the library reads them asynchronously and PyTorch does not know it (a freed pinned
+    block may be handed out again while its upload is pending).  ``inputs_ready``
+    (OZK2_HOST_INPUTS_READY): A and B are final when the call is made, so back-to-back
+    calls in the library-owned workspace may upload their inputs while the previous
+    call is still computing."""
     ta, lda = _operand(A, "A", on_host=True)
     tb, ldb = _operand(B, "B", on_host=True)
     m, k = A.shape

@@ -82,10 +82,12 @@ def test_inputs_ready_with_caller_workspace(cuda):
     m, n, k = 700, 500, 900
     ws = torch.empty(ozk.workspace_size_host(m, n, k, 12), dtype=torch.uint8, device=cuda)
     probs = [workloads.problem(m, n, k, 1.0, seed=60 + i) for i in range(3)]
+    # the host inputs must outlive the asynchronous calls (a freed pinned block could be
+    # handed to the next pin_memory() while its upload is still pending)
+    hosts = [(A.pin_memory(), B.pin_memory()) for A, B in probs]
     outs = []
-    for A, B in probs:
-        outs.append(ozk.dgemm_host(A.pin_memory(), B.pin_memory(), num_moduli=12, workspace=ws, sync=False,
-                                   inputs_ready=True))
+    for hA, hB in hosts:
+        outs.append(ozk.dgemm_host(hA, hB, num_moduli=12, workspace=ws, sync=False, inputs_ready=True))
     torch.cuda.current_stream().synchronize()
     for (A, B), o in zip(probs, outs):
         ref = ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=12).cpu()
