@@ -193,18 +193,6 @@ __device__ __forceinline__ uint64_t sw128_kmajor_desc(uint32_t saddr) {
   return d;
 }
 
-// Same for a tile written with 64-byte swizzling: rows of 64 bytes, 8-row core groups
-// 512 bytes apart, layout SWIZZLE_64B (= 4).
-__device__ __forceinline__ uint64_t sw64_kmajor_desc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>(1u) << 16;            // LBO (unused for swizzled K-major)
-  d |= static_cast<uint64_t>(512u >> 4) << 32;     // SBO
-  d |= static_cast<uint64_t>(1u) << 46;            // version
-  d |= static_cast<uint64_t>(4u) << 61;            // SWIZZLE_64B
-  return d;
-}
-
 // Instruction descriptor, kind::f8f6f4: D = F32, A = B = E4M3, both K-major.
 __host__ __device__ constexpr uint32_t fp8_idesc(int M, int N) {
   return (1u << 4)                                   // D format F32
