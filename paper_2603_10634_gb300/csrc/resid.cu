@@ -24,6 +24,8 @@
 // Rows of A produce K-major planes directly.  Columns of B are written transposed
 // (plane rows are columns of B), so both operands of the tensor-core products are
 // K-major.  Each thread owns 8 elements.
+#include <algorithm>
+
 #include <cuda_fp8.h>
 
 #include "device.cuh"
@@ -396,18 +398,85 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
+// Columns of B through shared memory.  A block converts tiles of kTileCols columns x
+// kTileK k: the tile is read row by row (512 contiguous bytes per row of B) into shared
+// memory, column-major, then each thread converts 8 consecutive k of one column, so a
+// half-warp covers 128 consecutive k of a column and writes one full 128-byte line of
+// each plane (the register kernel above writes 32-byte pieces of 8 columns).  Within a
+// column, chunk c of 8 elements sits at 64 c bytes with the element order rotated by
+// (c >> 1) & 7, so that the 16 lanes reading element t of their chunks hit 16 different
+// bank pairs.
+constexpr int kTileCols = 64, kTileK = 128;
+constexpr int kTilePitch = kTileK + 1;  // doubles per column in shared memory
+constexpr size_t kTileBytes = sizeof(double) * kTileCols * kTilePitch;
+
+__device__ __forceinline__ int tile_slot(int h) {  // position of k offset h within its column
+  const int c = h >> 3;
+  return (c << 3) + ((h & 7) ^ ((c >> 1) & 7));
+}
+
+template <int NM>
+__device__ __forceinline__ void residues_cols_tiled_body(const ResidArgs& a, const ModTable& mt,
+                                                         const float* pow2_s, double* tile) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tiles_n = (a.lines + kTileCols - 1) / kTileCols, tiles_k = (a.kp + kTileK - 1) / kTileK;
+  const int64_t tiles = static_cast<int64_t>(tiles_n) * tiles_k;
+  bool range_err = false;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int j0 = static_cast<int>(t % tiles_n) * kTileCols;
+    const int k0 = static_cast<int>(t / tiles_n) * kTileK;
+    // load: warp w reads rows w, w + 8, ...; lane l takes columns l and l + 32
+#pragma unroll 4
+    for (int r = warp; r < kTileK; r += 8) {
+      const int h = k0 + r;
+      const double* row = a.X + static_cast<int64_t>(h) * a.ldx;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = lane + 32 * u, j = j0 + c;
+        tile[c * kTilePitch + tile_slot(r)] = (h < a.k && j < a.lines) ? __ldg(row + j) : 0.0;
+      }
+    }
+    __syncthreads();
+    // convert: 4 rounds of 256 (column, 8-k chunk) tasks; a half-warp per column
+#pragma unroll 1
+    for (int round = 0; round < kTileCols * kTileK / (8 * 256); ++round) {
+      const int q = round * 256 + tid;
+      const int c = q >> 4, chunk = q & 15;
+      const int j = j0 + c, h0 = k0 + chunk * 8;
+      const bool active = j < a.lines && h0 < a.kp;
+      const int e = j < a.lines ? a.exps[j] : 0;
+      const double* src = tile + c * kTilePitch + chunk * 8;
+      f2 cc[kPairs][kPieces];
+      int tp[kElems];
+      int any_tp = 0;
+#pragma unroll
+      for (int u = 0; u < kElems; ++u) {
+        decode_into(cc, u, src[u ^ ((chunk >> 1) & 7)], e, tp[u], range_err);
+        any_tp |= tp[u];
+      }
+      uint8_t* colp = a.planes + static_cast<int64_t>(j < a.lines ? j : 0) * a.ldp + (h0 < a.kp ? h0 : 0);
+      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(a, mt, pow2_s, cc, tp, colp, active);
+      else cols_planes<NM, false>(a, mt, pow2_s, cc, tp, colp, active);
+    }
+    __syncthreads();  // the tile is reloaded
+  }
+  if (range_err) atomicOr(a.flags, kFlagRange);
+}
+
+template <int NM>
+__global__ void __launch_bounds__(256, 3) residues_cols_tiled_kernel(ResidArgs a,
+                                                                    const __grid_constant__ ModTable mt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* pow2_s = reinterpret_cast<float*>(smem_raw + kTileBytes);
+  load_table(mt, pow2_s);
+  residues_cols_tiled_body<NM>(a, mt, pow2_s, reinterpret_cast<double*>(smem_raw));
+}
+
 template <int NM>
 __global__ void __launch_bounds__(256, 3) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
   __shared__ float pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
   residues_rows_body<NM>(a, mt, pow2_s, blockIdx.x, gridDim.x);
-}
-
-template <int NM>
-__global__ void __launch_bounds__(256, 3) residues_cols_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
-  __shared__ float pow2_s[kMaxModuli * kPow2Table];
-  load_table(mt, pow2_s);
-  residues_cols_body<NM>(a, mt, pow2_s, blockIdx.x, gridDim.x);
 }
 
 __device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
@@ -452,7 +521,14 @@ struct RowsKernel {
 struct ColsKernel {
   template <int NM>
   static void launch(int grid, cudaStream_t st, const ResidArgs& a, const ModTable& mt) {
-    residues_cols_kernel<NM><<<grid, 256, 0, st>>>(a, mt);
+    constexpr size_t smem = kTileBytes + sizeof(float) * kMaxModuli * kPow2Table;
+    static bool attr = false;  // once per instantiation (the attribute belongs to the function)
+    if (!attr) {
+      cudaFuncSetAttribute(residues_cols_tiled_kernel<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(smem));
+      attr = true;
+    }
+    residues_cols_tiled_kernel<NM><<<grid, 256, smem, st>>>(a, mt);
   }
 };
 
@@ -491,7 +567,11 @@ cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int
                                  const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st,
                                  int64_t plane_stride) {
   ResidArgs a{B, ldb, n, k, kp, ldp, f, planes, plane_stride ? plane_stride : static_cast<int64_t>(n) * ldp, flags};
-  const int grid = grid_for(cols_items(n, kp));
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = static_cast<int64_t>((n + kTileCols - 1) / kTileCols) * ((kp + kTileK - 1) / kTileK);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, 3 * static_cast<int64_t>(sms)));
   launch_unrolled<ColsKernel>(mt, grid, st, a);
   return cudaGetLastError();
 }
