@@ -178,6 +178,10 @@ struct BatchProblem {
   int64_t nblocks[kBatchKernels];
 };
 
+// Tile of the column residue kernel: kResidTileCols columns x kResidTileK k per block
+// (one block per tile in a grouped launch).
+constexpr int kResidTileCols = 64, kResidTileK = 128;
+
 // Blocks of each grouped launch for one problem (the same decomposition the
 // single-problem launchers use, without their grid caps).
 void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nblocks)[kBatchKernels]);

@@ -323,81 +323,6 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const Mod
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
-// Columns of B.  A warp covers 8 columns x 32 consecutive h: lane 4 jj + qq takes
-// column j0 + jj, rows h0 + 8 qq .. h0 + 8 qq + 7.  Each group of four lanes writes one
-// full 32-byte sector of row j of every plane.  Warp items are walked in tiles of
-// kColTileGroups column groups x kColTileBlocks k-blocks (column groups fastest), so
-// the warps running at one time read a band of rows of B and write a band of rows of
-// each plane, instead of touching every row of all planes (which thrashes address
-// translation once the planes reach gigabytes).
-constexpr int kColTileGroups = 64;  // 512 columns
-constexpr int kColTileBlocks = 32;  // 1024 k
-
-__host__ __device__ inline int64_t cols_items(int lines, int kp) {
-  const int64_t ntj = ((lines + 7) / 8 + kColTileGroups - 1) / kColTileGroups;
-  const int64_t nth = (kp / 32 + kColTileBlocks - 1) / kColTileBlocks;
-  return ntj * nth * kColTileGroups * kColTileBlocks;
-}
-
-template <int NM>
-__device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
-                                                   int64_t vblock, int64_t vgrid) {
-  const int lane = threadIdx.x & 31;
-  const int jj = lane >> 2, qq = lane & 3;
-  const int warps_per_block = blockDim.x >> 5;
-  const int ncg = (a.lines + 7) / 8;  // column groups of 8
-  const int nkb = a.kp / 32;
-  const int ntj = (ncg + kColTileGroups - 1) / kColTileGroups;
-  const int64_t items = cols_items(a.lines, a.kp);
-  constexpr int kTileItems = kColTileGroups * kColTileBlocks;
-  const int64_t stride = vgrid * warps_per_block;
-  int64_t it = vblock * warps_per_block + (threadIdx.x >> 5);
-  if (it >= items) return;
-  // item -> (item within its tile w, tile column tj, tile row th), advanced by the
-  // stride's own decomposition instead of 64-bit divisions per item
-  int w = static_cast<int>(it % kTileItems);
-  int tj = static_cast<int>((it / kTileItems) % ntj), th = static_cast<int>((it / kTileItems) / ntj);
-  const int dw = static_cast<int>(stride % kTileItems);
-  const int dtj = static_cast<int>((stride / kTileItems) % ntj), dth = static_cast<int>((stride / kTileItems) / ntj);
-  auto advance = [&]() {
-    w += dw;
-    tj += dtj;
-    th += dth;
-    if (w >= kTileItems) {
-      w -= kTileItems;
-      ++tj;
-    }
-    if (tj >= ntj) {
-      tj -= ntj;
-      ++th;
-    }
-  };
-  bool range_err = false;
-  for (; it < items; it += stride, advance()) {
-    const int cg = tj * kColTileGroups + w % kColTileGroups;
-    const int hb = th * kColTileBlocks + w / kColTileGroups;
-    if (cg >= ncg || hb >= nkb) continue;  // past the edge of a partial tile (warp-uniform)
-    const int j = cg * 8 + jj;
-    const bool active = j < a.lines;
-    const int e = active ? a.exps[j] : 0;
-    const int h0 = hb * 32 + qq * 8;
-    f2 c[kPairs][kPieces];
-    int tp[kElems];
-    int any_tp = 0;
-#pragma unroll
-    for (int t = 0; t < kElems; ++t) {
-      const int h = h0 + t;
-      const double val = (active && h < a.k) ? __ldg(a.X + static_cast<int64_t>(h) * a.ldx + j) : 0.0;
-      decode_into(c, t, val, e, tp[t], range_err);
-      any_tp |= tp[t];
-    }
-    uint8_t* colp = a.planes + static_cast<int64_t>(active ? j : 0) * a.ldp + h0;
-    if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(a, mt, pow2_s, c, tp, colp, active);
-    else cols_planes<NM, false>(a, mt, pow2_s, c, tp, colp, active);
-  }
-  if (range_err) atomicOr(a.flags, kFlagRange);
-}
-
 // Columns of B through shared memory.  A block converts tiles of kTileCols columns x
 // kTileK k: the tile is read row by row (512 contiguous bytes per row of B) into shared
 // memory, column-major, then each thread converts 8 consecutive k of one column, so a
@@ -406,7 +331,7 @@ __device__ __forceinline__ void residues_cols_body(const ResidArgs& a, const Mod
 // column, chunk c of 8 elements sits at 64 c bytes with the element order rotated by
 // (c >> 1) & 7, so that the 16 lanes reading element t of their chunks hit 16 different
 // bank pairs.
-constexpr int kTileCols = 64, kTileK = 128;
+constexpr int kTileCols = kResidTileCols, kTileK = kResidTileK;
 constexpr int kTilePitch = kTileK + 1;  // doubles per column in shared memory
 constexpr size_t kTileBytes = sizeof(double) * kTileCols * kTilePitch;
 
@@ -415,14 +340,17 @@ __device__ __forceinline__ int tile_slot(int h) {  // position of k offset h wit
   return (c << 3) + ((h & 7) ^ ((c >> 1) & 7));
 }
 
+// Tiles t0, t0 + tstride, ... of the operand (tiles numbered with the column tile
+// fastest).
 template <int NM>
 __device__ __forceinline__ void residues_cols_tiled_body(const ResidArgs& a, const ModTable& mt,
-                                                         const float* pow2_s, double* tile) {
+                                                         const float* pow2_s, double* tile, int64_t t0,
+                                                         int64_t tstride) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tiles_n = (a.lines + kTileCols - 1) / kTileCols, tiles_k = (a.kp + kTileK - 1) / kTileK;
   const int64_t tiles = static_cast<int64_t>(tiles_n) * tiles_k;
   bool range_err = false;
-  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+  for (int64_t t = t0; t < tiles; t += tstride) {
     const int j0 = static_cast<int>(t % tiles_n) * kTileCols;
     const int k0 = static_cast<int>(t / tiles_n) * kTileK;
     // load: warp w reads rows w, w + 8, ...; lane l takes columns l and l + 32
@@ -469,7 +397,7 @@ __global__ void __launch_bounds__(256, 3) residues_cols_tiled_kernel(ResidArgs a
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* pow2_s = reinterpret_cast<float*>(smem_raw + kTileBytes);
   load_table(mt, pow2_s);
-  residues_cols_tiled_body<NM>(a, mt, pow2_s, reinterpret_cast<double*>(smem_raw));
+  residues_cols_tiled_body<NM>(a, mt, pow2_s, reinterpret_cast<double*>(smem_raw), blockIdx.x, gridDim.x);
 }
 
 template <int NM>
@@ -489,24 +417,30 @@ __device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ pr
   return lo;
 }
 
-// Grouped: rows of every A, then (second launch) columns of every B.
-template <bool ROWS>
-__global__ void __launch_bounds__(256, 3) residues_batch(const BatchProblem* __restrict__ probs, int count,
-                                                      uint32_t* flags, const __grid_constant__ ModTable mt) {
+// Grouped: rows of every A; columns of every B (one block per tile).
+__global__ void __launch_bounds__(256, 3) residues_rows_batch(const BatchProblem* __restrict__ probs, int count,
+                                                           uint32_t* flags, const __grid_constant__ ModTable mt) {
   __shared__ float pow2_s[kMaxModuli * kPow2Table];
   load_table(mt, pow2_s);
-  constexpr int w = ROWS ? kBkResidRows : kBkResidCols;
-  const int p = batch_problem(probs, count, w, blockIdx.x);
+  const int p = batch_problem(probs, count, kBkResidRows, blockIdx.x);
   const BatchProblem& P = probs[p];
-  const int64_t vb = blockIdx.x - P.first_block[w];
-  if constexpr (ROWS) {
-    const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.ldp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.ldp, flags};
-    residues_rows_body<0>(a, mt, pow2_s, vb, P.nblocks[w]);
-  } else {
-    const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.ldp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.ldp, flags};
-    residues_cols_body<0>(a, mt, pow2_s, vb, P.nblocks[w]);
-  }
+  const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.ldp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.ldp, flags};
+  residues_rows_body<0>(a, mt, pow2_s, blockIdx.x - P.first_block[kBkResidRows], P.nblocks[kBkResidRows]);
 }
+
+__global__ void __launch_bounds__(256, 3) residues_cols_batch(const BatchProblem* __restrict__ probs, int count,
+                                                           uint32_t* flags, const __grid_constant__ ModTable mt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* pow2_s = reinterpret_cast<float*>(smem_raw + kTileBytes);
+  load_table(mt, pow2_s);
+  const int p = batch_problem(probs, count, kBkResidCols, blockIdx.x);
+  const BatchProblem& P = probs[p];
+  const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.ldp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.ldp, flags};
+  residues_cols_tiled_body<0>(a, mt, pow2_s, reinterpret_cast<double*>(smem_raw),
+                              blockIdx.x - P.first_block[kBkResidCols], P.nblocks[kBkResidCols]);
+}
+
+constexpr size_t kColsSmem = kTileBytes + sizeof(float) * kMaxModuli * kPow2Table;
 
 // Launch with the modulus loop unrolled for N in [kUnrollLo, kUnrollHi] (the counts the
 // moduli tuner and the benchmarks use), the generic loop otherwise.
@@ -521,14 +455,13 @@ struct RowsKernel {
 struct ColsKernel {
   template <int NM>
   static void launch(int grid, cudaStream_t st, const ResidArgs& a, const ModTable& mt) {
-    constexpr size_t smem = kTileBytes + sizeof(float) * kMaxModuli * kPow2Table;
     static bool attr = false;  // once per instantiation (the attribute belongs to the function)
     if (!attr) {
       cudaFuncSetAttribute(residues_cols_tiled_kernel<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(smem));
+                           static_cast<int>(kColsSmem));
       attr = true;
     }
-    residues_cols_tiled_kernel<NM><<<grid, 256, smem, st>>>(a, mt);
+    residues_cols_tiled_kernel<NM><<<grid, 256, kColsSmem, st>>>(a, mt);
   }
 };
 
@@ -580,8 +513,14 @@ cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t 
                                   const ModTable& mt, uint32_t* flags, cudaStream_t st) {
   if (rows_blocks < 1 || cols_blocks < 1 || rows_blocks > 0x7FFFFFFFll || cols_blocks > 0x7FFFFFFFll)
     return cudaErrorInvalidValue;
-  residues_batch<true><<<static_cast<unsigned>(rows_blocks), 256, 0, st>>>(probs, count, flags, mt);
-  residues_batch<false><<<static_cast<unsigned>(cols_blocks), 256, 0, st>>>(probs, count, flags, mt);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(residues_cols_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(kColsSmem));
+    attr = true;
+  }
+  residues_rows_batch<<<static_cast<unsigned>(rows_blocks), 256, 0, st>>>(probs, count, flags, mt);
+  residues_cols_batch<<<static_cast<unsigned>(cols_blocks), 256, kColsSmem, st>>>(probs, count, flags, mt);
   return cudaGetLastError();
 }
 

@@ -360,9 +360,9 @@ void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nb)[kB
   nb[kBkSumsq] = fast ? gx : 0;
   nb[kBkExponents] = (static_cast<int64_t>(m) + n + 255) / 256;
   nb[kBkResidRows] = (static_cast<int64_t>(m) * ((kp + 255) / 256) + 7) / 8;
-  // warp items of the column residue kernel: tiles of 64 column groups x 32 k-blocks
-  const int64_t ntj = ((n + 7) / 8 + 63) / 64, nth = (kp / 32 + 31) / 32;
-  nb[kBkResidCols] = (ntj * nth * 64 * 32 + 7) / 8;
+  // one block per tile of the column residue kernel
+  nb[kBkResidCols] = static_cast<int64_t>((n + kResidTileCols - 1) / kResidTileCols) *
+                     ((kp + kResidTileK - 1) / kResidTileK);
   nb[kBkCrt] = (static_cast<int64_t>(m) * ((n + 1) / 2) + 255) / 256;
 }
 
