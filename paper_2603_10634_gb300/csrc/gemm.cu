@@ -24,9 +24,10 @@
 //                    loaded while still in L2), C'_l = mod(s X + Z, p);
 //   Karatsuba      : three passes over ONE slot each, alternating slots, so the
 //                    epilogue drains one slot while the tensor cores fill the other:
-//                    D1, park d1 = mod(D1, p); D2, park u1 = mod(15 d1 - D2, p) and
-//                    r2 = mod(D2, p); D3, C'_l = mod(16 mod(u1 + D3, p) + r2, p).
-// Parked values are int16 pairs in a CTA-private scratch tile (L2-resident).  The
+//                    D1, park d1 = mod(D1, p); D2, park v = mod(240 d1 - 15 D2, p);
+//                    D3, C'_l = mod(v + 16 D3, p)  (256 D1 + D2 + 16 (D3 - D1 - D2)
+//                    = 240 D1 - 15 D2 + 16 D3; every operand of mod is below 2^28).
+// Parked values are int16 in a CTA-private scratch tile (L2-resident).  The
 // bound and raw products are one single-slot pass per unit.  The wide tile halves the
 // operand bytes each SM pulls per flop compared with 128 x 128.
 //
@@ -499,7 +500,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int chalf = (warp - 2) >> 2;      // column half of the tile
     const int row = q * 32 + lane;
     const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
-    uint32_t* scr = prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BN) + row * BN + chalf * (BN / 2);
+    // the CTA's parking tile: BM x BN int16 (the first half of its scratch words)
+    int16_t* scr = reinterpret_cast<int16_t*>(prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BN)) +
+                   row * BN + chalf * (BN / 2);
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
     for (int u = u_first; ok && u < prm.num_units; u += u_step) {
@@ -542,48 +545,46 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t v[32];
               tmem_ld_32cols(ts + cb * 32, v);
               tmem_ld_wait();
-              uint4* sp = reinterpret_cast<uint4*>(scr + cb * 32);
-              if (ps == 0) {  // Karatsuba pass 1: park mod(D1, p)
+              uint4* sp = reinterpret_cast<uint4*>(scr + cb * 32);  // 32 int16 = 4 x 16 bytes
+              auto lo16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x & 0xFFFFu)); };
+              auto hi16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x >> 16)); };
+              auto pack = [](int a, int b) { return (static_cast<uint32_t>(a) & 0xFFFFu) | (static_cast<uint32_t>(b) << 16); };
+              if (ps == 0) {  // Karatsuba pass 1: park d1 = mod(D1, p)
 #pragma unroll
-                for (int w = 0; w < 8; ++w) {
+                for (int w = 0; w < 4; ++w) {
                   uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z)
-                    pk[z] = static_cast<uint32_t>(smod_i32(acc_int(v[4 * w + z]), p, h, ip)) & 0xFFFFu;
+                    pk[z] = pack(smod_i32(acc_int(v[8 * w + 2 * z]), p, h, ip),
+                                 smod_i32(acc_int(v[8 * w + 2 * z + 1]), p, h, ip));
                   sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
                 continue;
               }
-              if (!last) {  // Karatsuba pass 2: park u1 = mod(15 d1 - D2, p), r2 = mod(D2, p)
+              if (!last) {  // Karatsuba pass 2: park v = mod(240 d1 - 15 D2, p)
 #pragma unroll
-                for (int w = 0; w < 8; ++w) {
+                for (int w = 0; w < 4; ++w) {
                   const uint4 pv = sp[w];
                   const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
                   uint32_t pk[4];
 #pragma unroll
-                  for (int z = 0; z < 4; ++z) {
-                    const int d1 = static_cast<int16_t>(pr[z] & 0xFFFFu);
-                    const int d2 = acc_int(v[4 * w + z]);
-                    const int u1 = smod_i32(15 * d1 - d2, p, h, ip);
-                    const int r2 = smod_i32(d2, p, h, ip);
-                    pk[z] = (static_cast<uint32_t>(u1) & 0xFFFFu) | (static_cast<uint32_t>(r2) << 16);
-                  }
+                  for (int z = 0; z < 4; ++z)
+                    pk[z] = pack(smod_i32(240 * lo16(pr[z]) - 15 * acc_int(v[8 * w + 2 * z]), p, h, ip),
+                                 smod_i32(240 * hi16(pr[z]) - 15 * acc_int(v[8 * w + 2 * z + 1]), p, h, ip));
                   sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
                 continue;
               }
-              int res[32];  // Karatsuba pass 3
+              int res[32];  // Karatsuba pass 3: C' = mod(v + 16 D3, p)
 #pragma unroll
-              for (int w = 0; w < 8; ++w) {
+              for (int w = 0; w < 4; ++w) {
                 const uint4 pv = sp[w];
                 const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
 #pragma unroll
                 for (int z = 0; z < 4; ++z) {
-                  const int j = 4 * w + z;
-                  const int u1 = static_cast<int16_t>(pr[z] & 0xFFFFu);
-                  const int r2 = static_cast<int16_t>(pr[z] >> 16);
-                  const int uu = smod_i32(u1 + acc_int(v[j]), p, h, ip);
-                  res[j] = smod_i32(16 * uu + r2, p, h, ip);
+                  const int j = 8 * w + 2 * z;
+                  res[j] = smod_i32(lo16(pr[z]) + 16 * acc_int(v[j]), p, h, ip);
+                  res[j + 1] = smod_i32(hi16(pr[z]) + 16 * acc_int(v[j + 1]), p, h, ip);
                 }
               }
               if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
