@@ -255,7 +255,8 @@ __device__ __forceinline__ void rows_planes(const ResidArgs& a, const ModTable& 
   }
 }
 
-// The planes of one warp item of the column kernel: the lane's 8 bytes at colp.
+// The planes of one task of the column kernel (8 consecutive k of one column): the
+// thread's 8 bytes at colp.
 template <int NM, bool P2>
 __device__ __forceinline__ void cols_planes(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
                                             const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems], uint8_t* colp,
