@@ -443,6 +443,17 @@ __global__ void __launch_bounds__(256, 3) residues_cols_batch(const BatchProblem
 
 constexpr size_t kColsSmem = kTileBytes + sizeof(float) * kMaxModuli * kPow2Table;
 
+// Opt a column kernel into kColsSmem bytes of dynamic shared memory, once per device
+// (a launch on a device where this failed reports the error itself).
+template <class K>
+void allow_cols_smem(K* kernel, bool (&done)[64]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  if (!done[dev] && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kColsSmem)) == cudaSuccess)
+    done[dev] = true;
+}
+
 // Launch with the modulus loop unrolled for N in [kUnrollLo, kUnrollHi] (the counts the
 // moduli tuner and the benchmarks use), the generic loop otherwise.
 constexpr int kUnrollLo = 8, kUnrollHi = 16;
@@ -456,12 +467,8 @@ struct RowsKernel {
 struct ColsKernel {
   template <int NM>
   static void launch(int grid, cudaStream_t st, const ResidArgs& a, const ModTable& mt) {
-    static bool attr = false;  // once per instantiation (the attribute belongs to the function)
-    if (!attr) {
-      cudaFuncSetAttribute(residues_cols_tiled_kernel<NM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(kColsSmem));
-      attr = true;
-    }
+    static bool done[64] = {};  // per device and instantiation
+    allow_cols_smem(residues_cols_tiled_kernel<NM>, done);
     residues_cols_tiled_kernel<NM><<<grid, 256, kColsSmem, st>>>(a, mt);
   }
 };
@@ -514,12 +521,8 @@ cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t 
                                   const ModTable& mt, uint32_t* flags, cudaStream_t st) {
   if (rows_blocks < 1 || cols_blocks < 1 || rows_blocks > 0x7FFFFFFFll || cols_blocks > 0x7FFFFFFFll)
     return cudaErrorInvalidValue;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(residues_cols_batch, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(kColsSmem));
-    attr = true;
-  }
+  static bool done[64] = {};
+  allow_cols_smem(residues_cols_batch, done);
   residues_rows_batch<<<static_cast<unsigned>(rows_blocks), 256, 0, st>>>(probs, count, flags, mt);
   residues_cols_batch<<<static_cast<unsigned>(cols_blocks), 256, kColsSmem, st>>>(probs, count, flags, mt);
   return cudaGetLastError();
