@@ -37,6 +37,10 @@ struct ModTable {
   float inv_s[kMaxModuli];        // RN(1 / s)
   float w11[kMaxModuli][5];       // 2^(11 j) mod p, symmetric representative, j = 0..4
   int16_t pow2[kMaxModuli][kPow2Table];  // 2^t mod p, symmetric representative
+  // The residue kernels' constants as duplicated FP32 pairs (they work on element
+  // pairs): -p, RN(1/p), -s, RN(1/s) and w11.
+  float2 neg_p2[kMaxModuli], inv_p2[kMaxModuli], neg_s2[kMaxModuli], inv_s2[kMaxModuli];
+  float2 w2[kMaxModuli][5];
 };
 
 struct CrtTable {

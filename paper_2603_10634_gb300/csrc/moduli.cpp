@@ -174,6 +174,12 @@ bool build_mod_table(int N, ModTable* mt) {
       if (t % 11 == 0 && t / 11 < 5) mt->w11[l][t / 11] = static_cast<float>(sym(v));
       v = (2 * v) % p;
     }
+    auto pair = [](float x) { return make_float2(x, x); };
+    mt->neg_p2[l] = pair(-static_cast<float>(p));
+    mt->inv_p2[l] = pair(mt->inv_p[l]);
+    mt->neg_s2[l] = pair(-static_cast<float>(mt->s[l]));
+    mt->inv_s2[l] = pair(mt->inv_s[l]);
+    for (int j = 0; j < 5; ++j) mt->w2[l][j] = pair(mt->w11[l][j]);
   }
   return true;
 }

@@ -164,10 +164,10 @@ __device__ __forceinline__ void load_table(const ModTable& mt, float* pow2_s) {
 
 __device__ __forceinline__ ModF consts_of(const ModTable& mt, int l) {
   ModF m;
-  m.neg_p = dup(-static_cast<float>(mt.p[l]));
-  m.inv_p = dup(mt.inv_p[l]);
+  m.neg_p = mt.neg_p2[l];
+  m.inv_p = mt.inv_p2[l];
 #pragma unroll
-  for (int j = 0; j < kPieces; ++j) m.w[j] = dup(mt.w11[l][j]);
+  for (int j = 0; j < kPieces; ++j) m.w[j] = mt.w2[l][j];
   m.pow2_modulus = (mt.p[l] == 1024);
   return m;
 }
@@ -185,8 +185,8 @@ __device__ __forceinline__ void digits_of(const f2 (&c)[kPairs][kPieces], const 
   const ModF m = consts_of(mt, l);
   const float* pw = pow2_s + l * kPow2Table;
   if (l < kNumSquares) {
-    const f2 neg_s = dup(-static_cast<float>(mt.s[l]));
-    const f2 inv_s = dup(mt.inv_s[l]);
+    const f2 neg_s = mt.neg_s2[l];
+    const f2 inv_s = mt.inv_s2[l];
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       f2 d1[2], d2[2];
