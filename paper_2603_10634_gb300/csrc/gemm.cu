@@ -269,6 +269,19 @@ __device__ __forceinline__ float warp_column_max(float (&v)[32], int lane) {
 
 __device__ __forceinline__ int acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
 
+// x - p round(x / p) for an exact-integer float |x| <= 2^24, in FP32 without a
+// conversion: the quotient comes from one rounded product (x RN(1/p) is within 0.003 of
+// x / p for p >= 443), so the remainder, formed exactly by one FMA, lies in (-0.51p, 0.51p).
+__device__ __forceinline__ float mod_near_f32(float x, float p, float inv_p) {
+  const float q = __fadd_rn(__fmaf_rn(x, inv_p, 12582912.0f), -12582912.0f);  // 1.5 2^23
+  return __fmaf_rn(-p, q, x);
+}
+// An integer in (-p, p) into the symmetric range [-h, p-1-h].
+__device__ __forceinline__ int sym_fix(int r, int p, int h) {
+  r = (r > p - 1 - h) ? r - p : r;
+  return (r < -h) ? r + p : r;
+}
+
 // Store 32 int16 residues of one row (adding the previous block's residues when
 // `accumulate`), vectorised when the 32 columns are all inside the matrix.
 __device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int (&res)[32], bool accumulate,
@@ -536,9 +549,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld_32cols(tq + cb * 32, vx);
                 tmem_ld_32cols(tq + BN + cb * 32, vz);
                 tmem_ld_wait();
+                // mod(s X + Z, p) in FP32: X mod p first keeps s (X mod p) + Z below 2^24
+                // (|X| <= 2^24, |Z| <= 2^23), so every step is exact; one conversion
                 int res[32];
+                const float pf = static_cast<float>(p), sqf = static_cast<float>(sq);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) res[j] = smod_i32(sq * acc_int(vx[j]) + acc_int(vz[j]), p, h, ip);
+                for (int j = 0; j < 32; ++j) {
+                  const float y = __fmaf_rn(sqf, mod_near_f32(__uint_as_float(vx[j]), pf, ip), __uint_as_float(vz[j]));
+                  res[j] = sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
+                }
                 if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
                 continue;
               }
