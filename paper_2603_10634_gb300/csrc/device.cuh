@@ -202,17 +202,6 @@ __host__ __device__ constexpr uint32_t fp8_idesc(int M, int N) {
 }
 
 // ---------------------------------------------------------------- integers
-// Symmetric remainder of |x| < 2^30.2 for 443 <= p <= 1089 (the hybrid moduli with
-// N <= 20): float(x) is within 2^6 of x and the product carries a relative error
-// below 2^-23, so the estimate is within 0.48 of x/p; after rounding |x - q p| < 0.98 p
-// and one correction step on each side lands in [-h, p-1-h].
-__device__ __forceinline__ int smod_i32(int x, int p, int h, float inv_p) {
-  const int q = __float2int_rn(__int2float_rn(x) * inv_p);
-  int r = x - q * p;
-  r = (r > p - 1 - h) ? r - p : r;
-  r = (r < -h) ? r + p : r;
-  return r;
-}
 // Normalise a value in [-2h, 2(p-1-h)] (a sum of two symmetric residues).
 __device__ __forceinline__ int smod_small(int x, int p, int h) {
   x = (x > p - 1 - h) ? x - p : x;

@@ -267,8 +267,6 @@ __device__ __forceinline__ float warp_column_max(float (&v)[32], int lane) {
   return v[0];
 }
 
-__device__ __forceinline__ int acc_int(uint32_t bits) { return __float2int_rn(__uint_as_float(bits)); }
-
 // x - p round(x / p) for an exact-integer float |x| <= 2^24, in FP32 without a
 // conversion: the quotient comes from one rounded product (x RN(1/p) is within 0.003 of
 // x / p for p >= 443), so the remainder, formed exactly by one FMA, lies in (-0.51p, 0.51p).
@@ -280,6 +278,17 @@ __device__ __forceinline__ float mod_near_f32(float x, float p, float inv_p) {
 __device__ __forceinline__ int sym_fix(int r, int p, int h) {
   r = (r > p - 1 - h) ? r - p : r;
   return (r < -h) ? r + p : r;
+}
+// Karatsuba, second pass: mod(240 d1 - 15 D2, p) from the parked d1 and D2 (|D2| <= 2^24):
+// D2 mod p first keeps 240 d1 - 15 (D2 mod p) below 2^18, exact in FP32.
+__device__ __forceinline__ int kara_v(int d1, uint32_t d2_bits, float pf, float ip, int p, int h) {
+  const float y = __fmaf_rn(-15.0f, mod_near_f32(__uint_as_float(d2_bits), pf, ip), 240.0f * static_cast<float>(d1));
+  return sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
+}
+// Karatsuba, third pass: C' = mod(v + 16 D3, p), D3 mod p first (|v + 16 (D3 mod p)| < 2^15).
+__device__ __forceinline__ int kara_c(int v, uint32_t d3_bits, float pf, float ip, int p, int h) {
+  const float y = __fmaf_rn(16.0f, mod_near_f32(__uint_as_float(d3_bits), pf, ip), static_cast<float>(v));
+  return sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
 }
 
 // Store 32 int16 residues of one row (adding the previous block's residues when
@@ -539,6 +548,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           if constexpr (MODE == kModeResidue) {
             const int p = prm.mod.p[mod], h = prm.mod.half[mod], sq = prm.mod.s[mod];
             const float ip = prm.mod.inv_p[mod];
+            const float pf = static_cast<float>(p);
             const bool last = ps == up.npasses - 1;
             int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
 #pragma unroll 1
@@ -552,7 +562,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // mod(s X + Z, p) in FP32: X mod p first keeps s (X mod p) + Z below 2^24
                 // (|X| <= 2^24, |Z| <= 2^23), so every step is exact; one conversion
                 int res[32];
-                const float pf = static_cast<float>(p), sqf = static_cast<float>(sq);
+                const float sqf = static_cast<float>(sq);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
                   const float y = __fmaf_rn(sqf, mod_near_f32(__uint_as_float(vx[j]), pf, ip), __uint_as_float(vz[j]));
@@ -574,8 +584,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                   uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z)
-                    pk[z] = pack(smod_i32(acc_int(v[8 * w + 2 * z]), p, h, ip),
-                                 smod_i32(acc_int(v[8 * w + 2 * z + 1]), p, h, ip));
+                    pk[z] = pack(sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)), p, h),
+                                 sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)), p, h));
                   sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
                 continue;
@@ -588,8 +598,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                   uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z)
-                    pk[z] = pack(smod_i32(240 * lo16(pr[z]) - 15 * acc_int(v[8 * w + 2 * z]), p, h, ip),
-                                 smod_i32(240 * hi16(pr[z]) - 15 * acc_int(v[8 * w + 2 * z + 1]), p, h, ip));
+                    pk[z] = pack(kara_v(lo16(pr[z]), v[8 * w + 2 * z], pf, ip, p, h),
+                                 kara_v(hi16(pr[z]), v[8 * w + 2 * z + 1], pf, ip, p, h));
                   sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 }
                 continue;
@@ -602,8 +612,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int z = 0; z < 4; ++z) {
                   const int j = 8 * w + 2 * z;
-                  res[j] = smod_i32(lo16(pr[z]) + 16 * acc_int(v[j]), p, h, ip);
-                  res[j + 1] = smod_i32(hi16(pr[z]) + 16 * acc_int(v[j + 1]), p, h, ip);
+                  res[j] = kara_c(lo16(pr[z]), v[j], pf, ip, p, h);
+                  res[j + 1] = kara_c(hi16(pr[z]), v[j + 1], pf, ip, p, h);
                 }
               }
               if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
