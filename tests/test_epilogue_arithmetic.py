@@ -1,0 +1,80 @@
+"""Arithmetic facts the residue-product epilogue relies on, checked on the CPU in exact
+arithmetic (the GPU parity tests check the kernels themselves).
+
+* Karatsuba moduli (Sec. III-B): with r = 16 d1 + d2 and d3 = d1 + d2 for both operands
+  and Dx = dx_a dx_b, 240 D1 - 15 D2 + 16 D3 = r_a r_b exactly (Eq. C'-Karatsuba
+  rearranged), so the second pass may park v = mod(240 d1 - 15 D2, p) and the third
+  finish with mod(v + 16 D3, p).
+* The FP32 reduction: for an exact-integer float |x| <= 2^24 and every modulus p of the
+  hybrid list (N <= 20), q = RN(x RN(1/p) + 1.5 2^23) - 1.5 2^23 gives r = x - p q with
+  r = x (mod p) and |r| < 0.51 p, and the sums formed from such remainders stay below
+  2^24 (exact in FP32).
+"""
+import os
+import random
+import sys
+from fractions import Fraction
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from oracle import ozaki2 as oz  # noqa: E402
+
+MAGIC = Fraction(3 * 2**22)  # 1.5 * 2^23
+
+
+def _residues(p):
+    h = p // 2
+    return np.arange(-h, p - h, dtype=np.int64)
+
+
+def test_karatsuba_parking_identity():
+    for p in oz.hybrid_moduli(20):
+        kind, s = oz.modulus_kind(p)
+        if kind == "square":
+            continue
+        r = _residues(p)
+        d = np.array([oz.split_karatsuba(int(x), s) for x in r], dtype=np.int64)  # (p, 3)
+        d1, d2, d3 = d[:, 0], d[:, 1], d[:, 2]
+        D1, D2, D3 = np.outer(d1, d1), np.outer(d2, d2), np.outer(d3, d3)
+        assert np.array_equal(240 * D1 - 15 * D2 + 16 * D3, np.outer(r, r)), p
+
+
+def _mod_near(x, p, inv_p):
+    """The kernel's steps in exact arithmetic: one FMA rounded to FP32, one exact
+    subtraction, one exact FMA."""
+    t = oz.f32_round_nearest(Fraction(x) * Fraction(float(inv_p)) + MAGIC)
+    q = Fraction(float(t)) - MAGIC
+    assert q.denominator == 1
+    return x - p * int(q)
+
+
+def test_fp32_reduction_exact_and_bounded():
+    rng = random.Random(7)
+    top = 2**24
+    for p in oz.hybrid_moduli(20):
+        inv_p = oz.f32_round_nearest(Fraction(1, p))
+        xs = [0, 1, -1, top, -top, top - 1, -(top - 1), p // 2, -(p // 2), p // 2 + 1]
+        base = (top // p) * p
+        xs += [base + p // 2 + t for t in (-1, 0, 1)] + [-(base + p // 2 + t) for t in (-1, 0, 1)]
+        xs += [rng.randint(-top, top) for _ in range(150)]
+        for x in xs:
+            r = _mod_near(x, p, inv_p)
+            assert (x - r) % p == 0, (p, x)
+            assert abs(r) < 0.51 * p, (p, x, r)
+
+
+def test_fp32_reduction_sums_stay_exact():
+    bound = 0.51
+    for p in oz.hybrid_moduli(20):
+        kind, s = oz.modulus_kind(p)
+        if kind == "square":
+            # s (X mod p) + Z with |Z| <= 2^15 * 16 * 16 = 2^23
+            assert s * bound * p + 2**23 < 2**24, p
+        else:
+            # 240 d1 - 15 (D2 mod p) with |d1| <= p/2, and v + 16 (D3 mod p) with |v| <= p/2
+            assert 240 * (p // 2) + 15 * bound * p < 2**24, p
+            assert (p // 2) + 16 * bound * p < 2**24, p
