@@ -78,3 +78,30 @@ def test_fp32_reduction_sums_stay_exact():
             # 240 d1 - 15 (D2 mod p) with |d1| <= p/2, and v + 16 (D3 mod p) with |v| <= p/2
             assert 240 * (p // 2) + 15 * bound * p < 2**24, p
             assert (p // 2) + 16 * bound * p < 2**24, p
+
+
+def test_residue_kernel_quotient_is_the_nearest_integer():
+    # The digit-plane kernels form x = sum_j c_j w_j (|x| <= 5 (2^11 - 1) 544 < 2^23) and
+    # take q from one rounded product x RN(1/p) + 1.5 2^23; for odd p this is the
+    # nearest integer to x / p (never a tie), so r = x - p q is the symmetric remainder
+    # without a correction.  p = 1024 uses q = RN(x 2^-10 + 2^-11 + 1.5 2^23) - 1.5 2^23
+    # = floor((x + 512) / 1024).
+    rng = random.Random(11)
+    top = 5 * (2**11 - 1) * 544
+    assert top < 2**23
+    for p in oz.hybrid_moduli(20):
+        h = p // 2
+        xs = [0, 1, -1, top, -top] + [rng.randint(-top, top) for _ in range(150)]
+        xs += [k * p + d for k in (1, 7, 1000, -3, -1000) for d in (h, h + 1, -h, -h - 1)]
+        for x in xs:
+            if p == 1024:
+                t = oz.f32_round_nearest(Fraction(x, 1024) + Fraction(1, 2048) + MAGIC)
+                q = Fraction(float(t)) - MAGIC
+                assert q == (x + 512) // 1024, x
+            else:
+                inv_p = oz.f32_round_nearest(Fraction(1, p))
+                t = oz.f32_round_nearest(Fraction(x) * Fraction(float(inv_p)) + MAGIC)
+                q = Fraction(float(t)) - MAGIC
+                assert q == round(Fraction(x, p)), (p, x)
+            r = x - p * int(q)
+            assert r == oz.smod(x, p), (p, x)
