@@ -1,5 +1,5 @@
-"""Arithmetic facts the residue-product epilogue relies on, checked on the CPU in exact
-arithmetic (the GPU parity tests check the kernels themselves).
+"""Arithmetic facts the digit-plane kernels and the residue-product epilogue rely on,
+checked on the CPU in exact arithmetic (the GPU parity tests check the kernels).
 
 * Karatsuba moduli (Sec. III-B): with r = 16 d1 + d2 and d3 = d1 + d2 for both operands
   and Dx = dx_a dx_b, 240 D1 - 15 D2 + 16 D3 = r_a r_b exactly (Eq. C'-Karatsuba
@@ -9,6 +9,8 @@ arithmetic (the GPU parity tests check the kernels themselves).
   hybrid list (N <= 20), q = RN(x RN(1/p) + 1.5 2^23) - 1.5 2^23 gives r = x - p q with
   r = x (mod p) and |r| < 0.51 p, and the sums formed from such remainders stay below
   2^24 (exact in FP32).
+* The digit-plane kernels' quotient: one rounded product gives the nearest integer to
+  x / p for odd p (|x| < 2^23), and the floor form for p = 1024.
 """
 import os
 import random
