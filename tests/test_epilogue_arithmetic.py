@@ -11,6 +11,8 @@ checked on the CPU in exact arithmetic (the GPU parity tests check the kernels).
   2^24 (exact in FP32).
 * The digit-plane kernels' quotient: one rounded product gives the nearest integer to
   x / p for odd p (|x| < 2^23), and the floor form for p = 1024.
+* The CRT kernel's quotient estimate from 16-bit weight fractions (Eq. CRT_finalreduction):
+  within 0.17 of V / P, in a 32-bit accumulator that cannot overflow (N <= 20).
 """
 import os
 import random
@@ -107,3 +109,22 @@ def test_residue_kernel_quotient_is_the_nearest_integer():
                 assert q == round(Fraction(x, p)), (p, x)
             r = x - p * int(q)
             assert r == oz.smod(x, p), (p, x)
+
+
+def test_crt_quotient_estimate_bound():
+    # The CRT kernel estimates Q = round(V / P), V = sum_l u_l w_l with u_l in [0, p_l),
+    # from est = sum_l u_l round(2^16 w_l / P) in a 32-bit integer: the estimate is within
+    # 0.17 of V / P (so a fractional part at least 0.3 from one half decides the
+    # rounding, and the rarer cases take the exact comparison) and est never overflows.
+    for N in range(1, 21):
+        moduli = oz.hybrid_moduli(N)
+        w, P = oz.crt_weights(moduli)
+        err = Fraction(0)
+        est_max = 0
+        for p, wl in zip(moduli, w):
+            exact = Fraction(2**16 * wl, P)
+            f16 = round(exact)
+            err += (p - 1) * abs(f16 - exact) / 2**16
+            est_max += (p - 1) * f16
+        assert err < Fraction(17, 100), (N, float(err))
+        assert est_max + 0x8000 < 2**32, N
