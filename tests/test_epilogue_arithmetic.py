@@ -128,3 +128,13 @@ def test_crt_quotient_estimate_bound():
             est_max += (p - 1) * f16
         assert err < Fraction(17, 100), (N, float(err))
         assert est_max + 0x8000 < 2**32, N
+
+
+def test_library_reciprocals_are_correctly_rounded():
+    # The library stores 1/p and 1/s as float(1.0 / p) (a double quotient rounded to
+    # float); the quotient bounds above assume the correctly rounded RN(1/p), and the two
+    # agree for every modulus and digit base of the list.
+    for p in oz.hybrid_moduli(20):
+        _, s = oz.modulus_kind(p)
+        for v in (p, s):
+            assert np.float32(1.0 / v) == oz.f32_round_nearest(Fraction(1, v)), v
