@@ -275,17 +275,54 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def cpu_baseline(a, size=1024):
-    dt = oracle_sample(size, a.phi, a.moduli)
-    return {"value": 2.0 * size**3 / dt / 1e12, "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
-            "sample": f"full oracle pipeline on one m=n=k={size} instance of the same generator "
-                      f"(phi={a.phi}, N={a.moduli}); {dt:.1f} s; python single-threaded except numpy BLAS"}
+# The oracle runs with every BLAS / OpenMP pool pinned to one thread, so that the
+# core count stated beside its time is the one it used.
+ONE_THREAD_ENV = {"OPENBLAS_NUM_THREADS": "1", "OMP_NUM_THREADS": "1", "MKL_NUM_THREADS": "1",
+                  "BLIS_NUM_THREADS": "1", "VECLIB_MAXIMUM_THREADS": "1"}
+
+
+def oracle_times(sizes, phi, moduli):
+    """Seconds of one oracle run per size, in a child process with one thread."""
+    code = ("import json, sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps([bench.oracle_sample(s, %r, %d) for s in %r]))" % (ROOT, phi, moduli, list(sizes)))
+    env = dict(os.environ, **ONE_THREAD_ENV)
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def extrapolate_seconds(t_small, t_large, s_small, s_large, target):
+    """Fit t(s) = a s^2 + b s^3 (conversions and CRT grow as s^2, the digit products as
+    s^3) through two timed sizes and evaluate it at `target`."""
+    r = s_large / s_small
+    b = (t_large - r**2 * t_small) / (s_large**3 - r**2 * s_small**3)
+    a = (t_small - b * s_small**3) / s_small**2
+    if a < 0 or b < 0:  # noisy small samples: fall back to pure cubic scaling of the larger one
+        return t_large * (target / s_large) ** 3
+    return a * target**2 + b * target**3
+
+
+def cpu_baseline(a, sizes=(256, 512)):
+    t = oracle_times(sizes, a.phi, a.moduli)
+    s = sizes[-1]
+    t_ext = extrapolate_seconds(t[0], t[1], sizes[0], sizes[1], a.size)
+    return {"value": 2.0 * s**3 / t[-1] / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"full oracle pipeline on one m=n=k={s} instance of the workload's generator "
+                      f"(phi={a.phi}, N={a.moduli}), {t[-1]:.2f} s, one thread (BLAS pinned to 1)",
+            "extrapolated_to_workload": {"m=n=k": a.size, "seconds": t_ext,
+                                         "tflops": 2.0 * a.size**3 / t_ext / 1e12,
+                                         "how": f"t = a s^2 + b s^3 fitted to the oracle's times at "
+                                                f"s = {sizes[0]} ({t[0]:.2f} s) and {sizes[1]} ({t[1]:.2f} s); "
+                                                f"extrapolated, not measured"}}
 
 
 def run_reference(a, rank, world):
-    """--impl reference: the CPU oracle as it stands, one bounded sample per step."""
+    """--impl reference: the CPU oracle as it stands, one bounded sample of the workload
+    per step, on one host thread."""
     if rank != 0:
         return
+    os.environ.update(ONE_THREAD_ENV)  # before numpy is first imported in this process
     size = int(os.environ.get("OZK2_REFERENCE_SAMPLE", "512"))
     for _ in range(a.warmup):
         oracle_sample(size, a.phi, a.moduli)
@@ -294,14 +331,18 @@ def run_reference(a, rank, world):
         oracle_sample(size, a.phi, a.moduli)
     dt = (time.perf_counter() - t0) / a.steps
     val = 2.0 * size**3 / dt / 1e12
+    cfg = workload_config(a)
+    cfg["workload"] += f" (reference arm: each step times the oracle on one m=n=k={size} sample of this workload)"
+    cfg["reference_sample"] = {"m": size, "n": size, "k": size}
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s", "n_gpus": a.gpus,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+int", "data": "synthetic",
-        "config": workload_config(a),
-        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": host_cores(), "kind": "oracle",
+        "config": cfg,
+        "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
                          "sample": f"each step: full oracle pipeline on one m=n=k={size} instance of the "
-                                   f"workload's generator; python single-threaded except numpy BLAS"},
+                                   f"workload's generator (2 {size}^3 flop per step), one thread "
+                                   f"(BLAS pinned to 1)"},
         "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

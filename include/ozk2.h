@@ -80,9 +80,13 @@ ozk2_status ozk2_dgemm(int64_t m, int64_t n, int64_t k,
 size_t ozk2_workspace_size(int64_t m, int64_t n, int64_t k, int num_moduli);
 
 /*
- * ozk2_dgemm_ws - ozk2_dgemm with a caller-owned workspace (device memory, at least
- * ozk2_workspace_size bytes, 256-byte aligned).  The workspace is in use until the
- * stream passes this call.  OZK2_ERR_INVALID_VALUE if it is too small or misaligned.
+ * ozk2_dgemm_ws - ozk2_dgemm with a caller-owned workspace (device memory of the current
+ * device, at least ozk2_workspace_size bytes, 256-byte aligned).  The workspace is in use
+ * until the stream passes this call.  OZK2_ERR_INVALID_VALUE, touching no memory, if it
+ * is too small, misaligned, or not device memory of the current device (host, managed or
+ * another GPU's memory, as cudaPointerGetAttributes reports it): the FP8 product kernels
+ * read the workspace through TMA tensor maps, which this library builds only over the
+ * calling GPU's own memory.  The same check applies to every caller workspace below.
  */
 ozk2_status ozk2_dgemm_ws(int64_t m, int64_t n, int64_t k,
                           const double *A, int64_t lda,
@@ -99,14 +103,21 @@ ozk2_status ozk2_dgemm_ws(int64_t m, int64_t n, int64_t k,
  * OZK2_NOALLOC_MAX_BYTES bytes, which every GPU that loads it keeps until the process
  * exits.  The paper has no counterpart; this is an interface convenience.
  *
- * Same arguments and result as ozk2_dgemm.  Returns OZK2_ERR_UNSUPPORTED, touching no
+ * Same arguments and result as ozk2_dgemm: argument errors, m or n = 0 (nothing written)
+ * and k = 0 (C = 0) behave exactly as there.  Returns OZK2_ERR_UNSUPPORTED, touching no
  * memory, when ozk2_workspace_size(m, n, k, num_moduli) exceeds OZK2_NOALLOC_MAX_BYTES
  * (for N = 12 that is square sizes up to 1664).  The first call on a device looks
- * the array up (cudaGetSymbolAddress, which may load this part of the library on that
- * device); make that first call before any stream capture.  All calls on a device share
- * the array and each call overwrites it, so calls whose work overlaps on the GPU (other
- * streams, other threads) race; serialise them.  Device-side conditions are not
- * reported through ozk2_device_status (non-finite inputs still give NaN rows/columns).
+ * the array up (cudaGetSymbolAddress, which loads this part of the library on that
+ * device and so reserves the array there); make that first call before any stream
+ * capture.  On a device without room for the array that first call fails with
+ * OZK2_ERR_CUDA.  With eager module loading (CUDA_MODULE_LOADING=EAGER) the array is
+ * reserved on every device the process initialises, for every user of the library,
+ * whether or not this entry point is ever called.  All calls on a device share the
+ * array and each call overwrites it (clearing what must start at zero), so calls whose
+ * work overlaps on the GPU (other streams, other threads) race; serialise them.
+ * Device-side conditions of the last call are read by ozk2_noalloc_device_status, not by
+ * ozk2_device_status (which reads the library-owned workspace of ozk2_dgemm and reports
+ * nothing about these calls); non-finite inputs give NaN rows/columns either way.
  */
 #define OZK2_NOALLOC_MAX_BYTES (256u * 1024u * 1024u)
 ozk2_status ozk2_dgemm_noalloc(int64_t m, int64_t n, int64_t k,
@@ -114,6 +125,12 @@ ozk2_status ozk2_dgemm_noalloc(int64_t m, int64_t n, int64_t k,
                                const double *B, int64_t ldb,
                                double *C, int64_t ldc,
                                int num_moduli, ozk2_stream_t stream);
+
+/* ozk2_noalloc_device_status - ozk2_device_status for the static workspace of
+ * ozk2_dgemm_noalloc on the current device: synchronises `stream`, then reads and clears
+ * the flag word of the last ozk2_dgemm_noalloc call (OZK2_OK if none has run on this
+ * device).  Allocates nothing. */
+ozk2_status ozk2_noalloc_device_status(ozk2_stream_t stream);
 
 /* Operand form and scaling mode of ozk2_dgemm_ex. */
 typedef enum { OZK2_OP_N = 0, OZK2_OP_T = 1 } ozk2_op;
@@ -300,6 +317,44 @@ int ozk2_get_timing(float *ms, int max);
 /* ozk2_last_launch_count - kernels launched by the last ozk2_dgemm / ozk2_dgemm_ws
  * call on this thread (host-side count). */
 int ozk2_last_launch_count(void);
+
+/*
+ * ozk2_set_wait_limit - the bound, in nanoseconds, of every device-side wait of the FP8
+ * product kernels launched after this call (a wait on a TMA copy, a tensor-core product
+ * or the epilogue).  0 restores the default of 4 s.  A wait that reaches the bound makes
+ * the kernel stop issuing work, let the copies and products it has in flight complete,
+ * free its tensor memory and return; the call's results are then invalid and
+ * ozk2_device_status reports OZK2_ERR_TIMEOUT.  Returns the previous setting.
+ * Process-wide; not a feature of the paper (failure detection of this library).
+ */
+uint64_t ozk2_set_wait_limit(uint64_t ns);
+
+/*
+ * ozk2_debug_inject_fault - host-side fault injection for tests of the error paths.
+ * Arms one fault that fires once, at the next point where it applies, then disarms:
+ *   OZK2_FAULT_ALLOC   the next workspace allocation of the library (the library-owned
+ *                      workspace, a batch plan's private workspace or its pinned
+ *                      descriptor staging) reports failure without allocating: the call
+ *                      returns OZK2_ERR_ALLOC and touches no caller memory.
+ *   OZK2_FAULT_LAUNCH  the next launch of an FP8 product kernel is not made and the call
+ *                      returns OZK2_ERR_CUDA (C is not written: the CRT comes later).
+ *   OZK2_FAULT_STALL   the next FP8 product kernel waits first on a barrier that nothing
+ *                      signals; the wait runs out after the wait limit
+ *                      (ozk2_set_wait_limit), the kernel returns early and
+ *                      ozk2_device_status reports OZK2_ERR_TIMEOUT.
+ * OZK2_FAULT_NONE disarms.  A negative kind only queries.  Returns the kind armed before
+ * the call, or -1 (nothing changed) for an unknown kind.  The environment variable
+ * OZK2_FAULT=alloc|launch|stall arms one fault when the library first needs the setting.
+ * No fault is made on the GPU: every injected failure is a host-side decision or a
+ * bounded wait.
+ */
+typedef enum {
+  OZK2_FAULT_NONE = 0,
+  OZK2_FAULT_ALLOC = 1,
+  OZK2_FAULT_LAUNCH = 2,
+  OZK2_FAULT_STALL = 3
+} ozk2_fault;
+int ozk2_debug_inject_fault(int kind);
 
 /* ozk2_debug_timeline - of the last timed call: milliseconds from its start to the end
  * of each of the six phases (as ozk2_get_timing orders them).  Returns the number of

@@ -492,6 +492,32 @@ def integer_cols(B, f):
     return integer_rows(B.T, f).T
 
 
+INT64_SAFE = float(2**62)
+
+
+def integer_rows_int64(A, e):
+    """A' = trunc(diag(2^e) A) [Eq. def:A'] as an int64 array, for inputs whose scaled
+    entries all stay below 2^62 in magnitude (raises ValueError otherwise; integer_rows
+    has no such limit).  Non-finite entries give 0 (R10).
+
+    For a finite double a, ldexp(a, e) = 2^e a exactly whenever the result is at least 1
+    in magnitude (it is then a normal double and only the exponent changes); a result
+    below 1 in magnitude, rounded or not, truncates to 0.  np.trunc is exact, and values
+    below 2^62 convert to int64 exactly."""
+    A = np.asarray(A, dtype=np.float64)
+    x = np.where(np.isfinite(A), A, 0.0)
+    ex = np.asarray(e, dtype=np.int64).reshape(-1, 1)
+    v = np.ldexp(x, ex.astype(np.int32))
+    if v.size and not np.all(np.abs(v) < INT64_SAFE):
+        raise ValueError("a scaled entry reaches 2^62: use integer_rows")
+    return np.trunc(v).astype(np.int64)
+
+
+def integer_cols_int64(B, f):
+    """B' = trunc(B diag(2^f)) [Eq. def:B'] as int64 (see integer_rows_int64)."""
+    return integer_rows_int64(np.asarray(B, dtype=np.float64).T, f).T
+
+
 # --------------------------------------------------------------------------
 # Residues, digit planes and residue products
 # [Sec. II Eq. CRTmatmul; Sec. III-B Eqs. Karatsuba, C'-Karatsuba; Sec. III-C Eq. 3matmult]
@@ -503,10 +529,43 @@ def residue_matrix(Xint, p):
     return np.array(smod(Xint, p), dtype=np.int64) if Xint.size else np.zeros(Xint.shape, np.int64)
 
 
-def digit_planes(Xint, p):
-    """The FP8 digit planes of X' for modulus p, as int64 arrays of integers in [-16, 16]:
-    two planes (d1, d2) for a square modulus, three (d1, d2, d3) for a Karatsuba one."""
-    r = residue_matrix(Xint, p)
+def scaled_decomposition(A, e):
+    """(M, s) with 2^e_i a_ih = M_ih 2^s_ih exactly, M an integer of magnitude below 2^53
+    (np.frexp scaled by 2^53) and s = E + e_i; non-finite entries count as 0 (R10)."""
+    A = np.asarray(A, dtype=np.float64)
+    x = np.where(np.isfinite(A), A, 0.0)
+    frac, E = np.frexp(x)  # x = frac 2^E, 0.5 <= |frac| < 1 (frac = 0 for x = 0)
+    M = np.ldexp(frac, 53).astype(np.int64)
+    s = E.astype(np.int64) - 53 + np.asarray(e, dtype=np.int64).reshape(-1, 1)
+    return M, s
+
+
+def residues_of_decomposition(M, s, p):
+    """smod(trunc(M 2^s), p) for the (M, s) of scaled_decomposition: for s >= 0 the value
+    is the integer M 2^s and its residue is smod(smod(M, p) (2^s mod p), p); for s < 0,
+    trunc(M 2^s) = sign(M) (|M| >> -s) lies below 2^53 and is reduced directly."""
+    smax = int(s.max()) if s.size else 0
+    pow2 = np.array([pow(2, t, p) for t in range(max(smax, 0) + 1)], dtype=np.int64)
+    up = s >= 0
+    r_up = smod(smod(M, p) * pow2[np.where(up, s, 0)], p)
+    q = np.abs(M) >> np.minimum(np.where(up, 0, -s), 63)
+    r_down = smod(np.sign(M) * q, p)
+    return np.where(up, r_up, r_down).astype(np.int64)
+
+
+def scaled_residues_rows(A, e, p):
+    """smod(trunc(2^e_i a_ih), p) [Eqs. def:A', CRTmatmul] as int64, without forming the
+    integers a' (they exceed 64 bits for large N): a finite double is M 2^E with an
+    integer |M| < 2^53, so 2^e a = M 2^(E + e) and its truncation's residue follows from
+    M and the power of two alone (residues_of_decomposition)."""
+    return residues_of_decomposition(*scaled_decomposition(A, e), p)
+
+
+def digit_split(r, p):
+    """The FP8 digit planes of residues r (int64, symmetric mod p) as int64 arrays of
+    integers in [-16, 16]: two planes (d1, d2) for a square modulus, three (d1, d2, d3)
+    for a Karatsuba one [Sec. III-B, III-D]."""
+    r = np.asarray(r, dtype=np.int64)
     kind, s = modulus_kind(p)
     if kind == "square":
         # round half to even of r/s (R9).  r/s is a half-integer only for even s (= 32),
@@ -518,6 +577,11 @@ def digit_planes(Xint, p):
     d1 = sign * ((np.abs(r) + (s - 1)) // s)
     d2 = r - s * d1
     return [d1, d2, d1 + d2]
+
+
+def digit_planes(Xint, p):
+    """The FP8 digit planes of X' for modulus p (digit_split of mod(X', p))."""
+    return digit_split(residue_matrix(Xint, p), p)
 
 
 def _int_matmul(X, Y):

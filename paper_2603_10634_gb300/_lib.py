@@ -43,6 +43,9 @@ SIGNATURES = {
     "ozk2_dgemm_batched": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_int, c_int, c_void_p, c_size_t, c_void_p]),
     "ozk2_debug_timeline": (c_int, [c_void_p, c_int]),
+    "ozk2_noalloc_device_status": (c_int, [c_void_p]),
+    "ozk2_set_wait_limit": (ctypes.c_uint64, [ctypes.c_uint64]),
+    "ozk2_debug_inject_fault": (c_int, [c_int]),
     "ozk2_status_string": (ctypes.c_char_p, [c_int]),
     "ozk2_device_status": (c_int, [c_void_p, c_void_p]),
     "ozk2_moduli": (c_int, [c_int, ctypes.POINTER(ctypes.c_int32)]),

@@ -11,8 +11,10 @@
 // All kernels are launched on the caller's stream (a host-buffer call moves its data on
 // a library copy stream); nothing here runs on the CPU except bookkeeping.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -70,6 +72,46 @@ bool device_info(int* num_sms) {
   }
   *num_sms = d.num_sms;
   return d.supported;
+}
+
+// ------------------------------------------------------------------ fault injection, wait limit
+// One armed fault kind (kFaultNone when none), set by ozk2_debug_inject_fault or, once at
+// first use, by the environment variable OZK2_FAULT (alloc | launch | stall).
+std::mutex g_fault_mutex;
+int g_fault = kFaultNone;
+bool g_fault_env_read = false;
+
+int fault_kind_of(const char* s) {
+  if (!s) return kFaultNone;
+  if (!std::strcmp(s, "alloc")) return kFaultAlloc;
+  if (!std::strcmp(s, "launch")) return kFaultLaunch;
+  if (!std::strcmp(s, "stall")) return kFaultStall;
+  return kFaultNone;
+}
+
+// With g_fault_mutex held.
+void read_fault_env() {
+  if (g_fault_env_read) return;
+  g_fault_env_read = true;
+  const int k = fault_kind_of(std::getenv("OZK2_FAULT"));
+  if (k != kFaultNone) g_fault = k;
+}
+
+std::atomic<unsigned long long> g_wait_ns{0};  // 0: the default limit of the kernels
+
+// ------------------------------------------------------------------ workspace checks
+// A caller workspace must be device memory of the current device: the FP8 product kernels
+// read it through TMA tensor maps, and nothing else (host, managed or another GPU's memory)
+// may become the source of those loads.
+bool device_memory_here(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 // ------------------------------------------------------------------ constant tables
@@ -190,6 +232,10 @@ OwnedWs g_ws[64];
 uint8_t* owned_workspace(size_t need, ozk2_status* err, uint64_t* use = nullptr) {
   int dev = 0;
   cudaGetDevice(&dev);
+  if (take_fault(kFaultAlloc)) {  // injected: as if the workspace could not be obtained
+    *err = OZK2_ERR_ALLOC;
+    return nullptr;
+  }
   std::lock_guard<std::mutex> lk(g_ws_mutex);
   OwnedWs& w = g_ws[dev];
   ++w.uses;
@@ -300,6 +346,14 @@ ozk2_status scale_operand(Ctx& c, const Operand& op, int64_t first, int lines, c
   return OZK2_OK;
 }
 
+// Launch controls of an FP8 product launch: the device wait limit and the injected
+// faults.  Returns false when an injected launch failure replaces this launch.
+bool launch_controls(GemmArgs& g) {
+  g.wait_ns = wait_limit_ns();
+  g.stall = take_fault(kFaultStall);
+  return !take_fault(kFaultLaunch);
+}
+
 // Bound product (accurate mode) of rows [i0, i0 + rows) of A with all of B: the row
 // maxima R_i of those rows, and their share of the column maxima S_j (atomic maxima, so
 // the row slices may come in any order).
@@ -315,6 +369,7 @@ cudaError_t bound_rows(Ctx& c, int64_t i0, int rows) {
   g.R = c.at<float>(L.R) + i0;
   g.S = c.at<float>(L.S);
   g.flags = c.at<uint32_t>(L.flags);
+  if (!launch_controls(g)) return cudaErrorLaunchFailure;
   t_launches += 1;
   return launch_fp8_gemm(g, c.at<uint8_t>(L.Abar) + i0 * L.kp, L.kp, 1, c.at<uint8_t>(L.BbarT), L.kp, 1, c.st);
 }
@@ -388,6 +443,7 @@ ozk2_status products_rows(Ctx& c, int64_t i0, int rows, cudaStream_t st) {
   g.flags = c.at<uint32_t>(L.flags);
   g.plane_stride_a = int64_t(c.m) * L.ldp;
   g.plane_stride_b = int64_t(c.n) * L.ldp;
+  if (!launch_controls(g)) return OZK2_ERR_CUDA;
   OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA) + i0 * L.ldp, L.ldp, L.planes, c.at<uint8_t>(L.planesB),
                            L.ldp, L.planes, st));
   t_launches += 1;
@@ -450,8 +506,10 @@ ozk2_status validate_operands(ozk2_op transa, ozk2_op transb, int64_t m, int64_t
 }
 
 // `extra`: bytes the caller needs after the layout (256-aligned, at offset L.total).
+// ws_trusted: `ws` is memory of this library (the static array of ozk2_dgemm_noalloc),
+// known to be device memory of the current device.
 ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, bool fast, void* ws, size_t ws_bytes,
-                  cudaStream_t st, size_t extra = 0) {
+                  cudaStream_t st, size_t extra = 0, bool ws_trusted = false) {
   c.m = int(m);
   c.n = int(n);
   c.k = int(k);
@@ -465,6 +523,7 @@ ozk2_status setup(Ctx& c, int64_t m, int64_t n, int64_t k, int N, bool fast, voi
   c.L = make_layout(m, n, k, N, fast);
   if (ws) {
     if (ws_bytes < c.L.total + extra || (reinterpret_cast<uintptr_t>(ws) & 255u)) return OZK2_ERR_INVALID_VALUE;
+    if (!ws_trusted && !device_memory_here(ws)) return OZK2_ERR_INVALID_VALUE;
     c.ws = static_cast<uint8_t*>(ws);
   } else {
     ozk2_status err = OZK2_OK;
@@ -543,9 +602,9 @@ ozk2_status products_and_crt(Ctx& c, const Operand* a, double* C, int64_t ldc, c
 // One emulated product over whole operands (no blocking); arguments already validated,
 // m, n, k > 0.
 ozk2_status run_one(const Operand& a, const Operand& b, int64_t m, int64_t n, int64_t k, double* C, int64_t ldc,
-                    int N, bool fast, bool first, void* ws, size_t ws_bytes, cudaStream_t st) {
+                    int N, bool fast, bool first, void* ws, size_t ws_bytes, cudaStream_t st, bool ws_trusted) {
   Ctx c;
-  ozk2_status s = setup(c, m, n, k, N, fast, ws, ws_bytes, st);
+  ozk2_status s = setup(c, m, n, k, N, fast, ws, ws_bytes, st, 0, ws_trusted);
   if (s != OZK2_OK) return s;
   mark(c, 0);
   const Layout& L = c.L;
@@ -563,7 +622,8 @@ size_t workspace_bytes(int64_t m, int64_t n, int64_t k, int N, bool fast, int64_
 
 ozk2_status dgemm_general(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, int64_t k, const double* A,
                           int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int N, int mode,
-                          int64_t block_m, int64_t block_n, void* ws, size_t ws_bytes, cudaStream_t st) {
+                          int64_t block_m, int64_t block_n, void* ws, size_t ws_bytes, cudaStream_t st,
+                          bool ws_trusted = false) {
   t_launches = 0;
   if (!valid_mode(mode) || block_m < 0 || block_n < 0) return OZK2_ERR_INVALID_VALUE;
   ozk2_status s = validate(transa, transb, m, n, k, A, lda, B, ldb, C, ldc, N);
@@ -581,7 +641,7 @@ ozk2_status dgemm_general(ozk2_op transa, ozk2_op transb, int64_t m, int64_t n, 
     for (int64_t j0 = 0; j0 < n; j0 += bn) {
       const int64_t mm = std::min(bm, m - i0), nn = std::min(bn, n - j0);
       s = run_one(shift_lines(a, i0), shift_lines(b, j0), mm, nn, k, C + i0 * ldc + j0, ldc, N, fast,
-                  i0 == 0 && j0 == 0, ws, ws_bytes, st);
+                  i0 == 0 && j0 == 0, ws, ws_bytes, st, ws_trusted);
       if (s != OZK2_OK) return s;
     }
   }
@@ -946,7 +1006,7 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
   plan->cnt = int(probs.size());
   const BatchLayout& L = plan->L;
   if (ws) {
-    if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255u)) {
+    if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255u) || !device_memory_here(ws)) {
       destroy_plan(plan);
       return OZK2_ERR_INVALID_VALUE;
     }
@@ -960,7 +1020,7 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
     }
   } else {
     void* p = nullptr;
-    if (cudaMalloc(&p, L.total) != cudaSuccess) {
+    if (take_fault(kFaultAlloc) || cudaMalloc(&p, L.total) != cudaSuccess) {
       cudaGetLastError();
       destroy_plan(plan);
       return OZK2_ERR_ALLOC;
@@ -1048,7 +1108,7 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
     }
     // one pinned staging copy of everything the device reads: problems, then the maps
     const size_t nb = (L.gres - L.probs) + sizeof(GemmProblem) * probs.size();
-    if (cudaMallocHost(reinterpret_cast<void**>(&plan->host), nb) != cudaSuccess ||
+    if (take_fault(kFaultAlloc) || cudaMallocHost(reinterpret_cast<void**>(&plan->host), nb) != cudaSuccess ||
         cudaEventCreateWithFlags(&plan->uploaded, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       destroy_plan(plan);
@@ -1091,6 +1151,7 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
   g.flags = flags;
   if (!plan->fast) {
     g.mode = kModeBound;
+    if (!launch_controls(g)) return OZK2_ERR_CUDA;
     OZK2_TRY(launch_fp8_gemm_grouped(g, reinterpret_cast<const GemmProblem*>(ws + L.gbound), plan->cnt,
                                      plan->units_bound, st));
     t_launches += 1;
@@ -1101,6 +1162,7 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
   g.mode = kModeResidue;
   g.mt = &tab->mt;
   g.scratch = reinterpret_cast<uint32_t*>(ws + L.scratch);
+  if (!launch_controls(g)) return OZK2_ERR_CUDA;
   OZK2_TRY(launch_fp8_gemm_grouped(g, reinterpret_cast<const GemmProblem*>(ws + L.gres), plan->cnt, plan->units_res,
                                    st));
   OZK2_TRY(launch_crt_batch(probs, plan->cnt, plan->totals[kBkCrt], tab->ct, st));
@@ -1109,6 +1171,31 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
 }
 
 }  // namespace
+
+bool take_fault(int kind) {
+  std::lock_guard<std::mutex> lk(g_fault_mutex);
+  read_fault_env();
+  if (kind == kFaultNone || g_fault != kind) return false;
+  g_fault = kFaultNone;
+  return true;
+}
+
+unsigned long long wait_limit_ns() {
+  const unsigned long long v = g_wait_ns.load();
+  return v ? v : 4000000000ull;
+}
+
+int validate_dgemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                   const double* C, int64_t ldc, int N) {
+  return validate(OZK2_OP_N, OZK2_OP_N, m, n, k, A, lda, B, ldb, C, ldc, N);
+}
+
+int dgemm_library_ws(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double* C, int64_t ldc, int N, void* ws, size_t ws_bytes, cudaStream_t st) {
+  if (!ws) return OZK2_ERR_INTERNAL;
+  return dgemm_general(OZK2_OP_N, OZK2_OP_N, m, n, k, A, lda, B, ldb, C, ldc, N, OZK2_MODE_ACCURATE, 0, 0, ws,
+                       ws_bytes, st, true);
+}
 
 bool encode_fp8_map(CUtensorMap* map, const void* base, int64_t cols, int64_t rows, int64_t planes,
                     int64_t row_stride_bytes, int64_t plane_stride_bytes, int box_rows, int box_cols) {
@@ -1306,6 +1393,17 @@ int ozk2_debug_timeline(float* ms, int max) {
 
 int ozk2_last_launch_count(void) { return t_launches; }
 
+uint64_t ozk2_set_wait_limit(uint64_t ns) { return static_cast<uint64_t>(g_wait_ns.exchange(ns)); }
+
+int ozk2_debug_inject_fault(int kind) {
+  std::lock_guard<std::mutex> lk(g_fault_mutex);
+  read_fault_env();
+  const int prev = g_fault;
+  if (kind > kFaultStall) return -1;
+  if (kind >= 0) g_fault = kind;
+  return prev;
+}
+
 ozk2_status ozk2_debug_fp8_gemm(int64_t m, int64_t n, int64_t k, const uint8_t* A8, int64_t lda8, const uint8_t* B8,
                                 int64_t ldb8, float* D, int64_t ldd, ozk2_stream_t stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1335,6 +1433,7 @@ ozk2_status ozk2_debug_fp8_gemm(int64_t m, int64_t n, int64_t k, const uint8_t* 
   uint8_t* ws = owned_workspace(256, &err);  // flag word only
   if (!ws) return err;
   g.flags = reinterpret_cast<uint32_t*>(ws);
+  if (!launch_controls(g)) return OZK2_ERR_CUDA;
   OZK2_TRY(launch_fp8_gemm(g, A8, lda8, 1, B8, ldb8, 1, st));
   return OZK2_OK;
 }

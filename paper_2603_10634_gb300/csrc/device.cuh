@@ -10,8 +10,10 @@
 
 namespace ozk2 {
 
-// Give up a device wait after this many nanoseconds; the kernel then records
-// kFlagTimeout and returns instead of hanging.
+// Default limit of a device wait in nanoseconds (the host may set another per launch);
+// a wait that reaches its limit makes the kernel record kFlagTimeout and return instead
+// of hanging.  The waits of an aborting kernel for its own copies and products in
+// flight always use this default.
 constexpr unsigned long long kWaitLimitNs = 4000000000ull;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -53,16 +55,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Wait for the phase of `bar` with the given parity to complete.  Returns false if
-// the CTA-wide abort flag is raised or the time limit passes.
+// the CTA-wide abort flag is raised or more than limit_ns nanoseconds pass.
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
-                                                  volatile int* abort_flag) {
+                                                  volatile int* abort_flag, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 31u) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kWaitLimitNs) return false;
+      if (global_ns() - t0 > limit_ns) return false;
     }
   }
 }
@@ -78,40 +80,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
       " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_addr(dst)),
       "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
       : "memory");
-}
-
-// The same load delivered to the same shared-memory offset of every CTA in cta_mask (a
-// thread-block cluster), each CTA's mbarrier at `bar`'s offset receiving its bytes.
-__device__ __forceinline__ void tma_load_3d_multicast(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
-                                                      int y, int z, uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-      " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_addr(dst)),
-      "l"(map), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z), "h"(cta_mask)
-      : "memory");
-}
-
-// ---------------------------------------------------------------- clusters
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count_x() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-// All threads of all CTAs of the cluster (release / acquire of shared memory).
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile(
-      "barrier.cluster.arrive.release.aligned;\n"
-      "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------- tcgen05
@@ -152,16 +120,6 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
           smem_addr(bar))
       : "memory");
 }
-// Arrive (once the products issued so far complete) on the mbarrier at `bar`'s offset in
-// every CTA of cta_mask.
-__device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t cta_mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_addr(bar)),
-      "h"(cta_mask)
-      : "memory");
-}
-
 // Each lane reads 32 consecutive 32-bit columns of its TMEM lane.
 __device__ __forceinline__ void tmem_ld_32cols(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(

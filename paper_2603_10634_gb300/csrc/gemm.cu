@@ -40,9 +40,10 @@
 //               starts once the epilogue has released the slot(s) it writes.
 //   warps 2-9   epilogue: warp w reads TMEM lane quadrant w % 4, column half
 //               (w - 2) / 4, with tcgen05.ld; integer math; global stores.
-// Every wait is bounded (device.cuh); a wait that gives up raises a CTA-wide abort
-// flag and the global timeout flag, drains the copies and products this CTA has in
-// flight, frees TMEM and returns.
+// Every wait is bounded (device.cuh; the limit is a launch parameter); a wait that gives
+// up raises a CTA-wide abort flag and the global timeout flag, drains the copies and
+// products this CTA has in flight, frees TMEM and returns.  Operands are read only with
+// plain (non-multicast) TMA loads of this CTA's own tiles.
 #include <cstring>
 
 #include "device.cuh"
@@ -88,6 +89,8 @@ struct GemmParams {
   float* D;
   int64_t ldd;
   uint32_t* flags;
+  unsigned long long wait_ns;  // limit of every device wait (the drains of an abort use the default)
+  int stall;                   // fault injection: the MMA thread's first wait never completes
 };
 
 __device__ __forceinline__ void decode_unit(int tiles_m, int tiles_n, int tiles, int u, int& mod, int& tm,
@@ -117,29 +120,9 @@ struct UnitCtx {
   float* S;
 };
 
-// Clustered launch (CL = 2): unit u is a PAIR of vertically adjacent tiles (rows of
-// tiles 2q and 2q + 1, the same tile column and modulus) handled by the two CTAs of a
-// cluster, which share the B tile.  Pair rows are rasterised in bands of kGroupM / 2.
-__device__ __forceinline__ void decode_pair(int tiles_m, int tiles_n, int u, uint32_t rank, int& mod, int& tm,
-                                            int& tn) {
-  const int tiles_mp = (tiles_m + 1) / 2;
-  const int per_mod = tiles_mp * tiles_n;
-  mod = u / per_mod;
-  const int t = u - mod * per_mod;
-  constexpr int kGroupPairs = kGroupM / 2;
-  const int per_group = kGroupPairs * tiles_n;
-  const int g = t / per_group;
-  const int first = g * kGroupPairs;
-  const int gsz = min(tiles_mp - first, kGroupPairs);
-  const int r = t - g * per_group;
-  tm = 2 * (first + r % gsz) + static_cast<int>(rank);
-  tn = r / gsz;
-}
-
-template <bool GROUPED, int CL>
+template <bool GROUPED>
 __device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensorMap* tmA, const CUtensorMap* tmB,
-                                             const GemmProblem* __restrict__ probs, int nprobs, int u,
-                                             uint32_t rank, UnitCtx& c) {
+                                             const GemmProblem* __restrict__ probs, int nprobs, int u, UnitCtx& c) {
   if constexpr (!GROUPED) {
     c.ta = tmA;
     c.tb = tmB;
@@ -147,10 +130,7 @@ __device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensor
     c.n = P.n;
     c.k = P.k;
     c.prob = 0;
-    if constexpr (CL == 2)
-      decode_pair(P.tiles_m, P.tiles_n, u, rank, c.mod, c.tm, c.tn);
-    else
-      decode_unit(P.tiles_m, P.tiles_n, P.tiles, u, c.mod, c.tm, c.tn);
+    decode_unit(P.tiles_m, P.tiles_n, P.tiles, u, c.mod, c.tm, c.tn);
     c.cres = P.cres;
     c.ldr = P.ldr;
     c.res_stride = P.res_stride;
@@ -328,14 +308,10 @@ __device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int 
 }
 
 // GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).
-// CL = 2: a cluster of two CTAs works on tile pairs; each CTA loads its own A tile and
-// one half of the shared B tile, multicast to both, and every stage is released only
-// when both CTAs' products have read it.
-template <int MODE, bool GROUPED, int CL>
+template <int MODE, bool GROUPED>
 __global__ void __launch_bounds__(kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ GemmParams prm, const GemmProblem* __restrict__ probs, int nprobs) {
-  static_assert(CL == 1 || (CL == 2 && !GROUPED), "clusters serve single problems");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;
@@ -344,25 +320,27 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* tfull = empty + kStages;  // [2]: slot filled by the tensor cores
   uint64_t* tempty = tfull + 2;       // [2]: slot drained by the epilogue
   uint64_t* done = tempty + 2;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* never = done + 1;  // nothing arrives here (the injected stall waits on it)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(never + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const uint32_t rank = (CL == 2) ? cluster_rank() : 0u;
-  const int u_first = (CL == 2) ? static_cast<int>(cluster_id_x()) : static_cast<int>(blockIdx.x);
-  const int u_step = (CL == 2) ? static_cast<int>(cluster_count_x()) : static_cast<int>(gridDim.x);
+  const int u_first = static_cast<int>(blockIdx.x);
+  const int u_step = static_cast<int>(gridDim.x);
+  const unsigned long long wait_ns = prm.wait_ns;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(full + s, 1);
-      mbar_init(empty + s, CL);  // released by the products of every CTA that reads it
+      mbar_init(empty + s, 1);
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(tfull + j, 1);
       mbar_init(tempty + j, 32 * kEpiWarps);
     }
     mbar_init(done, 1);
+    mbar_init(never, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -376,7 +354,6 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL == 2) cluster_sync();  // the peer's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
@@ -390,7 +367,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       int last_prob = -1;
       for (int u = u_first; ok && u < prm.num_units; u += u_step) {
         UnitCtx uc;
-        resolve_unit<GROUPED, CL>(prm, &tmA, &tmB, probs, nprobs, u, rank, uc);
+        resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
         if (GROUPED && uc.prob != last_prob) {
           tensormap_acquire(uc.ta);
           tensormap_acquire(uc.tb);
@@ -405,22 +382,16 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int np = num_products<MODE>(mod);
             for (int s = 0; ok && s < ksteps; ++s) {
               for (int x = 0; x < np; ++x) {
-                if (!mbar_wait_bounded(empty + stage, phase ^ 1u, abort_flag)) {
+                if (!mbar_wait_bounded(empty + stage, phase ^ 1u, abort_flag, wait_ns)) {
                   ok = false;
                   break;
                 }
                 int pa, pb, acc;
                 product_of<MODE>(mod, ps, x, pa, pb, acc);
                 uint8_t* dst = tiles + stage * kStageBytes;
-                mbar_arrive_expect_tx(full + stage, kStageBytes);  // A + both halves of B
+                mbar_arrive_expect_tx(full + stage, kStageBytes);
                 tma_load_3d(dst, uc.ta, full + stage, k0 + s * BK, uc.tm * BM, pa);
-                if constexpr (CL == 2) {
-                  const int half = static_cast<int>(rank) * (BN / 2);
-                  tma_load_3d_multicast(dst + kATileBytes + half * BK, uc.tb, full + stage, k0 + s * BK,
-                                        uc.tn * BN + half, pb, 0x3);
-                } else {
-                  tma_load_3d(dst + kATileBytes, uc.tb, full + stage, k0 + s * BK, uc.tn * BN, pb);
-                }
+                tma_load_3d(dst + kATileBytes, uc.tb, full + stage, k0 + s * BK, uc.tn * BN, pb);
                 issued |= 1u << stage;
                 issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                 if (++stage == kStages) {
@@ -437,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         atomicOr(prm.flags, kFlagTimeout);
         int no_abort = 0;  // let this thread's copies in flight land before exiting
         for (int s = 0; s < kStages; ++s)
-          if (issued & (1u << s)) mbar_wait_bounded(full + s, (issued_phase >> s) & 1u, &no_abort);
+          if (issued & (1u << s)) mbar_wait_bounded(full + s, (issued_phase >> s) & 1u, &no_abort, kWaitLimitNs);
       }
     }
   } else if (warp == 1) {
@@ -447,10 +418,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       int stage = 0;
       uint32_t phase = 0;
       Slots sl;
-      bool ok = true;
+      // an injected stall (fault-injection tests): wait for a barrier nothing arrives at,
+      // so this wait runs out and the kernel takes its timeout path
+      bool ok = prm.stall ? mbar_wait_bounded(never, 0u, abort_flag, wait_ns) : true;
       for (int u = u_first; ok && u < prm.num_units; u += u_step) {
         UnitCtx uc;
-        resolve_unit<GROUPED, CL>(prm, &tmA, &tmB, probs, nprobs, u, rank, uc);
+        resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
         const int mod = uc.mod;
         const UnitPlan up = plan_of<MODE>(uc.k, mod);
         for (int c = 0; ok && c < up.nchunks; ++c) {
@@ -461,14 +434,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t first_slot = pair ? 0u : sl.next;
             for (uint32_t j = 0; j < 2 && ok; ++j) {
               if (!pair && j != first_slot) continue;
-              ok = mbar_wait_bounded(tempty + j, (sl.uses(j) & 1u) ^ 1u, abort_flag);
+              ok = mbar_wait_bounded(tempty + j, (sl.uses(j) & 1u) ^ 1u, abort_flag, wait_ns);
             }
             if (!ok) break;
             tc_fence_after();
             const int np = num_products<MODE>(mod);
             for (int s = 0; ok && s < ksteps; ++s) {
               for (int x = 0; x < np; ++x) {
-                if (!mbar_wait_bounded(full + stage, phase, abort_flag)) {
+                if (!mbar_wait_bounded(full + stage, phase, abort_flag, wait_ns)) {
                   ok = false;
                   break;
                 }
@@ -483,10 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int kk = 0; kk < BK / 32; ++kk)
                   mma_fp8(dtm, adesc + 2ull * kk, bdesc + 2ull * kk, idesc, (first && kk == 0) ? 0u : 1u);
-                if constexpr (CL == 2)
-                  mma_commit_multicast(empty + stage, 0x3);  // both CTAs wrote into this stage
-                else
-                  mma_commit(empty + stage);
+                mma_commit(empty + stage);
                 if (++stage == kStages) {
                   stage = 0;
                   phase ^= 1u;
@@ -510,7 +480,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
       mma_commit(done);  // every product issued here completes before TMEM is freed
       int no_abort = 0;
-      mbar_wait_bounded(done, 0, &no_abort);
+      mbar_wait_bounded(done, 0, &no_abort, kWaitLimitNs);
       if (!ok) {
         *abort_flag = 1;
         atomicOr(prm.flags, kFlagTimeout);
@@ -529,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     bool ok = true;
     for (int u = u_first; ok && u < prm.num_units; u += u_step) {
       UnitCtx uc;
-      resolve_unit<GROUPED, CL>(prm, &tmA, &tmB, probs, nprobs, u, rank, uc);
+      resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
       const int mod = uc.mod, tn = uc.tn;
       const UnitPlan up = plan_of<MODE>(uc.k, mod);
       const int gi = uc.tm * BM + row;
@@ -539,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t slot = pair ? 0u : sl.next;
           for (uint32_t j = 0; j < 2 && ok; ++j) {
             if (!pair && j != slot) continue;
-            ok = mbar_wait_bounded(tfull + j, sl.uses(j) & 1u, abort_flag);
+            ok = mbar_wait_bounded(tfull + j, sl.uses(j) & 1u, abort_flag, wait_ns);
           }
           ok = __all_sync(0xffffffffu, ok);
           if (!ok) break;
@@ -676,43 +646,25 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   tc_fence_before();
   __syncthreads();
-  if constexpr (CL == 2) cluster_sync();  // no CTA leaves while its peer may still write into it
   if (warp == 1) {
     tc_fence_after();
     tmem_dealloc(tmem_base, kTmemCols);
   }
 }
 
-template <int MODE, bool GROUPED, int CL>
+template <int MODE, bool GROUPED>
 cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
                         const GemmProblem* probs, int nprobs, cudaStream_t st) {
   static bool configured[64] = {false};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED, CL>,
+    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
     if (err != cudaSuccess) return err;
     configured[dev] = true;
   }
-  if constexpr (CL == 1) {
-    fp8_gemm_kernel<MODE, GROUPED, 1><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, prm, probs, nprobs);
-  } else {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(static_cast<unsigned>(grid));
-    cfg.blockDim = dim3(kThreads);
-    cfg.dynamicSmemBytes = kSmemBytes;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CL;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaError_t err = cudaLaunchKernelEx(&cfg, fp8_gemm_kernel<MODE, GROUPED, CL>, ta, tb, prm, probs, nprobs);
-    if (err != cudaSuccess) return err;
-  }
+  fp8_gemm_kernel<MODE, GROUPED><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, prm, probs, nprobs);
   return cudaGetLastError();
 }
 
@@ -755,29 +707,21 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.D = g.D;
   prm.ldd = g.ldd;
   prm.flags = g.flags;
+  prm.wait_ns = g.wait_ns;
+  prm.stall = g.stall ? 1 : 0;
 
-  // Tile pairs in 2-CTA clusters (half the B traffic from L2 per product) for the
-  // method's products with at least two tile rows; single CTAs otherwise.
-  const bool pairs = g.mode != kModeRaw && prm.tiles_m >= 2;
   CUtensorMap ta, tb;
   if (!encode_fp8_map(&ta, a, g.k, g.m, planes_a, lda8, g.plane_stride_a, BM, BK)) return cudaErrorInvalidValue;
-  if (!encode_fp8_map(&tb, b, g.k, g.n, planes_b, ldb8, g.plane_stride_b, pairs ? BN / 2 : BN, BK))
-    return cudaErrorInvalidValue;
+  if (!encode_fp8_map(&tb, b, g.k, g.n, planes_b, ldb8, g.plane_stride_b, BN, BK)) return cudaErrorInvalidValue;
   const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
-  if (pairs) {
-    prm.num_units = ((prm.tiles_m + 1) / 2) * prm.tiles_n * nmod;  // tile pairs
-    const int clusters = prm.num_units < ctas / 2 ? prm.num_units : ctas / 2;
-    if (g.mode == kModeResidue) return launch_mode<kModeResidue, false, 2>(prm, ta, tb, 2 * clusters, nullptr, 0, st);
-    return launch_mode<kModeBound, false, 2>(prm, ta, tb, 2 * clusters, nullptr, 0, st);
-  }
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {
     case kModeResidue:
-      return launch_mode<kModeResidue, false, 1>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_mode<kModeResidue, false>(prm, ta, tb, grid, nullptr, 0, st);
     case kModeBound:
-      return launch_mode<kModeBound, false, 1>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_mode<kModeBound, false>(prm, ta, tb, grid, nullptr, 0, st);
     default:
-      return launch_mode<kModeRaw, false, 1>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_mode<kModeRaw, false>(prm, ta, tb, grid, nullptr, 0, st);
   }
 }
 
@@ -808,6 +752,8 @@ cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs,
   prm.num_units = static_cast<int>(total_units);
   prm.scratch = g.scratch;
   prm.flags = g.flags;
+  prm.wait_ns = g.wait_ns;
+  prm.stall = g.stall ? 1 : 0;
   if (g.mode == kModeResidue) {
     fill_mod(prm, *g.mt);
     if (!g.scratch) return cudaErrorInvalidValue;
@@ -817,8 +763,8 @@ cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs,
   const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   if (g.mode == kModeResidue)
-    return launch_mode<kModeResidue, true, 1>(prm, unused, unused, grid, probs, count, st);
-  return launch_mode<kModeBound, true, 1>(prm, unused, unused, grid, probs, count, st);
+    return launch_mode<kModeResidue, true>(prm, unused, unused, grid, probs, count, st);
+  return launch_mode<kModeBound, true>(prm, unused, unused, grid, probs, count, st);
 }
 
 }  // namespace ozk2

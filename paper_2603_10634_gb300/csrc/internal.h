@@ -58,6 +58,20 @@ struct CrtTable {
 // traffic of the residue products (the L2 hashes such strides well).
 __host__ __device__ inline int64_t plane_pitch(int64_t kp) { return kp; }
 
+// Host-side fault injection and the device wait limit (api.cu).  A fault kind is armed
+// by ozk2_debug_inject_fault or the OZK2_FAULT environment variable and fires once.
+enum FaultKind { kFaultNone = 0, kFaultAlloc = 1, kFaultLaunch = 2, kFaultStall = 3 };
+bool take_fault(int kind);        // true (and disarmed) if `kind` is the armed fault
+unsigned long long wait_limit_ns();
+
+// Entry points for ozk2_dgemm_noalloc (api.cu), returning ozk2_status codes: the argument
+// checks of ozk2_dgemm, and ozk2_dgemm_ws in a workspace of this library (whose memory
+// type needs no check).
+int validate_dgemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                   const double* C, int64_t ldc, int N);
+int dgemm_library_ws(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double* C, int64_t ldc, int N, void* ws, size_t ws_bytes, cudaStream_t st);
+
 // Host-side constant generation (moduli.cpp)
 bool build_mod_table(int N, ModTable* mt);
 bool build_crt_table(int N, CrtTable* ct);
@@ -121,6 +135,8 @@ struct GemmArgs {
   // row block of a larger plane set passes the full set's plane stride.
   int64_t plane_stride_a;
   int64_t plane_stride_b;
+  unsigned long long wait_ns;  // limit of each device wait (wait_limit_ns())
+  bool stall;                  // fault injection: the kernel's first MMA wait never completes
 };
 // A operand: `planes_a` digit planes (K-major, m x k bytes, row stride lda8 bytes, plane
 // stride plane_stride_a); B operand the same with n rows.

@@ -185,3 +185,42 @@ def test_batch_validation_and_size(lib):
     assert single - 2 * scratch - 3 * 64 * 1024 <= ws <= single - 2 * scratch + 64 * 1024
     assert lib.ozk2_workspace_size_batched(3, m, n, k, 12, 0) > lib.ozk2_workspace_size_batched(3, m, n, k, 12, 1)
     assert lib.ozk2_workspace_size_batched(3, m, I64(5, -6, 7), k, 12, 0) == 0
+
+
+def test_fault_injection_arming(lib):
+    """ozk2_debug_inject_fault arms one fault kind, reports the previous one, rejects
+    unknown kinds; argument and device checks come before any injected fault."""
+    assert lib.ozk2_debug_inject_fault(-1) == 0  # nothing armed
+    assert lib.ozk2_debug_inject_fault(1) == 0  # arm alloc
+    assert lib.ozk2_debug_inject_fault(-1) == 1
+    assert lib.ozk2_debug_inject_fault(7) == -1  # unknown kind: unchanged
+    assert lib.ozk2_debug_inject_fault(-1) == 1
+    bogus = ctypes.c_void_p(0x1000)
+    null = ctypes.c_void_p(0)
+    # an argument error returns before the workspace is taken: the fault stays armed
+    assert lib.ozk2_dgemm(4, 4, 8, bogus, 4, bogus, 4, bogus, 4, 12, null) == 1
+    assert lib.ozk2_debug_inject_fault(-1) == 1
+    assert lib.ozk2_debug_inject_fault(0) == 1  # disarm
+    assert lib.ozk2_debug_inject_fault(-1) == 0
+
+
+def test_fault_injection_from_environment():
+    """OZK2_FAULT arms a fault when the library first needs the setting."""
+    import subprocess
+    import sys
+
+    code = ("from paper_2603_10634_gb300 import _lib; lib = _lib.load(); "
+            "print(lib.ozk2_debug_inject_fault(-1))")
+    for spec, want in [("stall", 3), ("launch", 2), ("alloc", 1), ("bogus", 0)]:
+        env = dict(os.environ, OZK2_FAULT=spec)
+        out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                             timeout=300)
+        assert out.returncode == 0, out.stderr
+        assert int(out.stdout.strip().splitlines()[-1]) == want, spec
+
+
+def test_wait_limit_setting(lib):
+    """ozk2_set_wait_limit returns the previous setting; 0 is the default."""
+    assert lib.ozk2_set_wait_limit(1000) == 0
+    assert lib.ozk2_set_wait_limit(0) == 1000
+    assert lib.ozk2_set_wait_limit(0) == 0
