@@ -514,7 +514,11 @@ def run_ours(a, rank, world):
 
 def run_autograd(a, rank, world):
     """Forward + backward of the differentiable product: C = A B, then dA = W B^T and
-    dB = A^T W for the upstream gradient W; three emulated products per step."""
+    dB = A^T W for the upstream gradient W; three emulated products per step.  The
+    default backward reuses the forward's exponents and digit planes (one conversion of
+    W for both gradients); the same step with fresh emulations of both gradients is
+    timed beside it, and sampled entries of dA and dB of both are compared with the
+    exact products next to native FP64."""
     import torch
 
     import paper_2603_10634_gb300 as ozk
@@ -531,38 +535,72 @@ def run_autograd(a, rank, world):
     flops = 3 * 2.0 * m * n * k
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        A.grad = None
-        B.grad = None
-        ozk.matmul(A, B, N, a.mode).backward(W)
+    def make_step(reuse):
+        def step():
+            A.grad = None
+            B.grad = None
+            ozk.matmul(A, B, N, a.mode, reuse=reuse).backward(W)
+        return step
 
-    for _ in range(a.warmup):
-        step()
-    torch.cuda.synchronize(dev)
-    launches = 0
-    for _ in range(1):
-        step()
-        launches = 3 * ozk.last_launch_count()  # the three products launch alike
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
+    def timed(step):
+        for _ in range(a.warmup):
+            step()
+        torch.cuda.synchronize(dev)
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize(dev)
         start.record(stream)
         for _ in range(a.steps):
             step()
         end.record(stream)
         torch.cuda.synchronize(dev)
-    barrier(world)
-    ms = max_over_ranks(start.elapsed_time(end) / a.steps, world, dev)
+        barrier(world)
+        return max_over_ranks(start.elapsed_time(end) / a.steps, world, dev)
+
+    def grad_errors(samples=16, seed=9):
+        import numpy as np
+
+        rng = np.random.default_rng(seed)
+        An, Bn, Wn = A.detach().cpu().numpy(), B.detach().cpu().numpy(), W.cpu().numpy()
+        gA, gB = A.grad.cpu().numpy(), B.grad.cpu().numpy()
+        nA, nB = (W @ B.detach().T).cpu().numpy(), (A.detach().T @ W).cpu().numpy()
+        worst = {"dA": 0.0, "dA_native": 0.0, "dB": 0.0, "dB_native": 0.0}
+        for _ in range(samples):
+            i, j, h = int(rng.integers(0, m)), int(rng.integers(0, n)), int(rng.integers(0, k))
+            for key, got, nat, x, y in (("dA", gA[i, h], nA[i, h], Wn[i], Bn[h]),
+                                        ("dB", gB[h, j], nB[h, j], An[:, h], Wn[:, j])):
+                num, den = _exact_dot(x, y)
+                anum, aden = _exact_dot(abs(x), abs(y))
+                for tag, v in ((key, got), (key + "_native", nat)):
+                    cn, cd = float(v).as_integer_ratio()
+                    worst[tag] = max(worst[tag], abs(num * cd - cn * den) / (den * cd) / (anum / aden))
+        worst["within_2x_native"] = bool(worst["dA"] <= 2 * max(worst["dA_native"], 2.0**-53) and
+                                         worst["dB"] <= 2 * max(worst["dB_native"], 2.0**-53))
+        return worst
+
+    step = make_step(True)
+    step()
+    launches = ozk.last_launch_count() + 9  # the backward call, plus the forward's 9
+    with ClockSampler(local) as clk:
+        ms = timed(step)
+    err_reuse = grad_errors() if rank == 0 else None
+    status = ozk.device_status()
+    ms_fresh = timed(make_step(False))
+    err_fresh = grad_errors() if rank == 0 else None
     if rank == 0:
         line = {
             "metric": "emulated FP64 forward+backward TFLOP/s (3 x 2mnk / t)", "value": world * flops / ms / 1e9,
             "unit": "TFLOP/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f8e4m3", "emulates": "f64",
             "data": "synthetic",
-            "config": {"workload": f"autograd A {m}x{k} @ B {k}x{n}, W ~ N(0,1), phi={a.phi}, N={N}, {a.mode} mode",
+            "config": {"workload": f"autograd A {m}x{k} @ B {k}x{n}, W ~ N(0,1), phi={a.phi}, N={N}, {a.mode} mode, "
+                                   f"backward reusing the forward's exponents and digit planes",
                        "l2": "operands larger than L2, no flush"},
-            "gpu_launches": launches * a.steps, "clocks": clk.summary(), "device_status": ozk.device_status(),
+            "gpu_launches": launches * a.steps, "clocks": clk.summary(), "device_status": status,
+            "gradient_error_vs_absAB": err_reuse,
+            "fresh_backward": {"ms_per_step": ms_fresh, "tflops": world * flops / ms_fresh / 1e9,
+                               "gradient_error_vs_absAB": err_fresh,
+                               "what": "both gradients as independent emulations (own scaling of both operands)"},
         }
         print(json.dumps(line), flush=True)
 

@@ -330,6 +330,21 @@ int ozk2_last_launch_count(void);
 uint64_t ozk2_set_wait_limit(uint64_t ns);
 
 /*
+ * ozk2_set_tile_n - the output tile width of the FP8 tensor-core products launched after
+ * this call (and of batch plans created after it): 256 (128 x 256 tiles), 128 (128 x 128
+ * tiles, for narrow or ragged products), or 0, the default: the library chooses 128 where
+ * a 256-wide tile would pad the product's columns by a quarter or more, else 256 (a batch
+ * plan applies that rule to the batch's total padded work).  Results are bit-identical
+ * for either width.  Returns the previous setting, or -1 (unchanged) for other values.
+ * Process-wide; a tuning knob (the moduli-and-tile tuner measures both widths).
+ */
+int ozk2_set_tile_n(int tile_n);
+
+/* ozk2_batch_plan_tile_n - the tile width a batch plan runs its products with (-1 for
+ * NULL). */
+int ozk2_batch_plan_tile_n(ozk2_batch_plan plan);
+
+/*
  * ozk2_debug_inject_fault - host-side fault injection for tests of the error paths.
  * Arms one fault that fires once, at the next point where it applies, then disarms:
  *   OZK2_FAULT_ALLOC   the next workspace allocation of the library (the library-owned
@@ -360,6 +375,46 @@ int ozk2_debug_inject_fault(int kind);
  * of each of the six phases (as ozk2_get_timing orders them).  Returns the number of
  * values written (6), or -1 if there is no timed call or max < 6. */
 int ozk2_debug_timeline(float *ms, int max);
+
+/*
+ * ozk2_dgemm_backward - the gradients dA = dC B^T (m x k) and dB = A^T dC (k x n) of
+ * C = A B (row-major, as ozk2_dgemm) by the same emulation, reusing the forward call's
+ * scaling exponents e, f and digit planes of A' = trunc(diag(2^e) A), B' = trunc(B diag(2^f))
+ * (Eqs. def:A', def:B').  The paper treats the product only; the construction is its own:
+ *   dA: G'_ij = trunc(2^(g_i - f_j) dC_ij) with B' fixed, dA_ih = 2^-g_i (G' B'^T)_ih;
+ *   dB: H'_ij = trunc(2^(h_j - e_i) dC_ij) with A' fixed, dB_hj = 2^-h_j (A'^T H')_hj;
+ * g and h take the whole budget of P (Eq. condition: 2 sum |G'||B'| < P) from FP8 bound
+ * products of |dC| with |B| and of |A| with |dC| (as accurate mode, Sec. III-E), so
+ * 3N + 1 FP8 products run per gradient, as in a fresh emulation, but A and B are not
+ * converted again (their planes are transposed), and one kernel converts dC for both.
+ *   forward_workspace  device memory of the current device, the workspace of the
+ *                      ozk2_dgemm_ws / ozk2_dgemm_ex call (accurate mode, no blocking,
+ *                      same m, n, k, num_moduli) that computed C = A B, unchanged since
+ *                      (at least ozk2_workspace_size bytes).  Read only.
+ *   A, B, dC           device, row-major: A m x k (lda), B k x n (ldb), dC m x n (lddc).
+ *   dA, dB             device outputs (ldda >= k, lddb >= n); either may be NULL (not
+ *                      computed), not both.
+ *   workspace          device, >= ozk2_workspace_size_backward bytes, 256-byte aligned,
+ *                      or NULL for the library-owned workspace.
+ * Each output entry is the correctly rounded value of its integer result; rows of dC and
+ * of B holding NaN/Inf give NaN rows / columns of dA, columns of dC and of A NaN columns /
+ * rows of dB.  m, n or k = 0: the outputs with an empty reduction are set to 0.
+ */
+ozk2_status ozk2_dgemm_backward(int64_t m, int64_t n, int64_t k,
+                                const double *A, int64_t lda,
+                                const double *B, int64_t ldb,
+                                const double *dC, int64_t lddc,
+                                double *dA, int64_t ldda,
+                                double *dB, int64_t lddb,
+                                int num_moduli, const void *forward_workspace,
+                                size_t forward_workspace_bytes,
+                                void *workspace, size_t workspace_bytes,
+                                ozk2_stream_t stream);
+
+/* ozk2_workspace_size_backward - bytes of one ozk2_dgemm_backward call's own workspace
+ * (bound operands, the digit planes of dC's two integer matrices and of the transposed
+ * A', B', the residue products of both gradients); 0 on invalid arguments. */
+size_t ozk2_workspace_size_backward(int64_t m, int64_t n, int64_t k, int num_moduli);
 
 /* ---------------------------------------------------------------------------
  * Parity hooks.  Each runs one step (or a prefix) of the method on its own so the
@@ -434,6 +489,15 @@ ozk2_status ozk2_debug_residue_products(int64_t m, int64_t n, int64_t k,
                                         const double *B, int64_t ldb, int num_moduli,
                                         const int32_t *e, const int32_t *f,
                                         int16_t *Cres, ozk2_stream_t stream);
+
+/*
+ * ozk2_debug_backward_exponents - the exponents g (m, dC's rows) and h (n, dC's columns)
+ * that the last ozk2_dgemm_backward call with these sizes used, read from its workspace
+ * (NULL: the library-owned workspace).  Either output may be NULL.
+ */
+ozk2_status ozk2_debug_backward_exponents(int64_t m, int64_t n, int64_t k, int num_moduli,
+                                          const void *workspace, int32_t *g, int32_t *h,
+                                          ozk2_stream_t stream);
 
 /*
  * ozk2_debug_crt - C = diag(2^-e) mod(sum_l q_l P/p_l C'_l, P) diag(2^-f)

@@ -759,3 +759,177 @@ def emulated_entry(a_row, b_col, e_i, f_j, moduli):
     c = sum(x * y for x, y in zip(ai, bj))
     lhs = 2 * sum(abs(x) * abs(y) for x, y in zip(ai, bj))
     return round_scaled_to_double(c, int(e_i) + int(f_j)), lhs < P
+
+
+# --------------------------------------------------------------------------
+# Gradients of C = A B that reuse the forward's integer matrices A', B'
+# (the paper covers only the product itself; this follows its construction:
+#  Eqs. def:A', def:B', condition, CRTmatmul, CRT_finalreduction, inversescaling)
+#
+#   dA = dC B^T:  B'_hj = trunc(2^f_j b_hj) is the forward's.  With G'_ij =
+#                 trunc(2^(g_i - f_j) dC_ij),  (G' B'^T)_ih ~ 2^g_i dA_ih.
+#   dB = A^T dC:  A'_ih = trunc(2^e_i a_ih) is the forward's.  With H'_ij =
+#                 trunc(2^(h_j - e_i) dC_ij),  (A'^T H')_hj ~ 2^h_j dB_hj.
+# Since |G'_ij| |B'_hj| <= 2^g_i |dC_ij| |b_hj|, the Ozaki-II condition
+# 2 sum_j |G'_ij| |B'_hj| < P holds once 2 2^g_i max_h (|dC| |B|^T)_ih <= P - 1; the
+# whole budget goes to dC's side (B' is fixed).  The bound comes from an FP8 bound
+# product as in accurate mode (Sec. III-E, Eq. barCupper), with the lines of B (and the
+# columns of A) scaled to FP8 by their own prelim exponents t_h, which the maximum then
+# removes again: R_i = max_h RU(cbar_ih 2^-t_h) >= 2^g'_i max_h (|dC||B|^T)_ih.
+# --------------------------------------------------------------------------
+
+DELTA_REUSE_POS = np.float32(-(1 + 2.0**-21))  # exact in FP32
+DELTA_REUSE_NEG = np.float32(-(1 - 2.0**-21))  # exact in FP32
+
+
+def reuse_budget_constant(moduli):
+    """Q = RD_fp32(log2(P - 1) - 1): log2 of (P - 1)/2, the whole budget of one side."""
+    P = product_P(moduli)
+    return f32_round_down(_log2_int_high_precision(P - 1) - 1)
+
+
+def reuse_exponent(gprime, rmax, Q, line_is_zero):
+    """g = g' + floor(RD(Q + RD(d log2_f32(R)))), d = -(1 + 2^-21) for log2 R >= 0 and
+    -(1 - 2^-21) below, so that d log2_f32(R) <= -log2 R whatever the FP32 rounding of
+    the logarithm: then 2 2^(g - g') R <= P - 1.  Zero line: 0.  R = 0 (the other
+    operand vanishes on this line's support): g' + floor(Q)."""
+    if line_is_zero:
+        return 0
+    if rmax == 0:
+        return int(gprime) + math.floor(float(Q))
+    L = log2_f32(rmax)
+    d = DELTA_REUSE_POS if float(L) >= 0 else DELTA_REUSE_NEG
+    t1 = f32_round_down(Fraction(float(d)) * Fraction(float(L)))
+    t2 = f32_round_down(Fraction(float(Q)) + Fraction(float(t1)))
+    return int(gprime) + math.floor(float(t2))
+
+
+def shifted_row_maxima(cbar, shift):
+    """max_h RU_fp32(cbar_ih 2^-s_h), s_h = min(shift_h, 126) (an upper bound of
+    max_h cbar_ih 2^-shift_h for every shift_h >= -126)."""
+    s = np.minimum(np.asarray(shift, dtype=np.int64), 126)
+    m, k = cbar.shape
+    out = np.zeros(m, dtype=np.float32)
+    for i in range(m):
+        best = np.float32(0.0)
+        for h in range(k):
+            c = cbar[i, h]
+            if c == 0:
+                continue
+            v = f32_round_up(Fraction(float(c)) * Fraction(2) ** int(-s[h]))
+            best = max(best, v)
+        out[i] = best
+    return out
+
+
+def reuse_side_exponents(X, Y, moduli):
+    """Exponents of the rows of X for a product X Y^T whose other operand's integers are
+    fixed: (g, g', R) with R_i >= 2^g'_i max_h sum_j |x_ij| |y_hj| from the FP8 bound
+    product of RU_E4M3(2^g' |X|) and RU_E4M3(2^t |Y|) (t: prelim exponents of Y's rows)."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    Xf = np.where(np.isfinite(X), X, 0.0)
+    Yf = np.where(np.isfinite(Y), Y, 0.0)
+    gp = prelim_exponent_rows(Xf)
+    t = prelim_exponent_rows(Yf)
+    n = X.shape[1]
+    cbar = bound_product(bound_operand(Xf, gp), bound_operand(Yf, t).T, n)
+    R = shifted_row_maxima(cbar, t) if Y.shape[0] else np.zeros(X.shape[0], np.float32)
+    Q = reuse_budget_constant(moduli)
+    zero = ~np.any(Xf != 0, axis=1)
+    g = np.array([reuse_exponent(gp[i], R[i], Q, zero[i]) for i in range(X.shape[0])], dtype=np.int64)
+    return g, np.where(zero, 0, gp), R
+
+
+def dc_integers_for_dA(dC, g, f):
+    """G'_ij = trunc(2^(g_i - f_j) dC_ij) as Python ints."""
+    m, n = dC.shape
+    out = np.empty((m, n), dtype=object)
+    for i in range(m):
+        for j in range(n):
+            out[i, j] = trunc_scaled(dC[i, j], int(g[i]) - int(f[j]))
+    return out
+
+
+def dc_integers_for_dB(dC, h, e):
+    """H'_ij = trunc(2^(h_j - e_i) dC_ij) as Python ints."""
+    m, n = dC.shape
+    out = np.empty((m, n), dtype=object)
+    for i in range(m):
+        for j in range(n):
+            out[i, j] = trunc_scaled(dC[i, j], int(h[j]) - int(e[i]))
+    return out
+
+
+def _residue_products_of_integers(Xint, YintT, moduli):
+    """C'_l = mod(X' Y'^T, p_l) from digit planes (X' is r x c, Y'^T is s x c)."""
+    out = []
+    for p in moduli:
+        px = digit_planes(Xint, p)
+        py = [z.T for z in digit_planes(YintT, p)]
+        out.append(np.asarray(residue_product(px, py, p), dtype=np.int64))
+    return out
+
+
+def reuse_gradients(A, B, dC, N, e=None, f=None, g=None, h=None):
+    """dA = dC B^T and dB = A^T dC by the method, reusing the forward's A' and B'.
+
+    e, f: the forward's exponents (default: the oracle's own accurate-mode scaling of
+    A, B); g, h: the exponents of dC's rows and columns (default: reuse_side_exponents).
+    Returns dict(dA, dB, g, h, residues_dA, residues_dB).  Non-finite entries: a row of
+    dC or a row of B holding one gives NaN in dA's row / column, a column of dC or of A
+    NaN in dB's column / row (R10)."""
+    A = np.asarray(A, dtype=np.float64)
+    B = np.asarray(B, dtype=np.float64)
+    dC = np.asarray(dC, dtype=np.float64)
+    moduli = hybrid_moduli(N)
+    if e is None or f is None:
+        sc = scaling_exponents(A, B, N, moduli)
+        e = sc["e"] if e is None else e
+        f = sc["f"] if f is None else f
+    e = np.asarray(e, dtype=np.int64)
+    f = np.asarray(f, dtype=np.int64)
+    if g is None:
+        g = reuse_side_exponents(dC, B, moduli)[0]
+    if h is None:
+        h = reuse_side_exponents(dC.T, A.T, moduli)[0]
+    g = np.asarray(g, dtype=np.int64)
+    h = np.asarray(h, dtype=np.int64)
+    Aint = integer_rows(A, e)          # the forward's A' (m x k)
+    BintT = integer_rows(B.T, f)       # the forward's B'^T (n x k): columns of B' as rows
+    Gint = dc_integers_for_dA(dC, g, f)        # m x n
+    Hint = dc_integers_for_dB(dC, h, e)        # m x n
+    # dA = G' B'^T: contraction over j; B'^T's lines are the rows h of B' (k x n)
+    res_a = _residue_products_of_integers(Gint, BintT.T, moduli)
+    # dB = A'^T H': contraction over i; lines of A'^T are the columns of A' (k x m),
+    # lines of H' for the output columns are the columns of H' (n x m)
+    res_b = _residue_products_of_integers(Aint.T, Hint.T, moduli)
+    k = A.shape[1]
+    dA = unscale(crt_reconstruct(res_a, moduli), g, np.zeros(k, np.int64))
+    dB = unscale(crt_reconstruct(res_b, moduli), np.zeros(k, np.int64), h)
+    dA[~np.all(np.isfinite(dC), axis=1), :] = np.nan
+    dA[:, ~np.all(np.isfinite(B), axis=1)] = np.nan
+    dB[:, ~np.all(np.isfinite(dC), axis=0)] = np.nan
+    dB[~np.all(np.isfinite(A), axis=0), :] = np.nan
+    return dict(dA=dA, dB=dB, g=g, h=h, residues_dA=res_a, residues_dB=res_b)
+
+
+def reuse_gradient_entry_dA(dC_row, b_row, f, g_i, moduli):
+    """One entry of dA by the plain definition: C'_ih = sum_j G'_ij B'_hj exactly, then
+    RN(C' 2^-g_i).  Returns (value, condition_holds)."""
+    P = product_P(moduli)
+    G = [trunc_scaled(x, int(g_i) - int(fj)) for x, fj in zip(dC_row, f)]
+    Bh = [trunc_scaled(x, int(fj)) for x, fj in zip(b_row, f)]
+    c = sum(x * y for x, y in zip(G, Bh))
+    lhs = 2 * sum(abs(x) * abs(y) for x, y in zip(G, Bh))
+    return round_scaled_to_double(c, int(g_i)), lhs < P
+
+
+def reuse_gradient_entry_dB(a_col, dC_col, e, h_j, moduli):
+    """One entry of dB: C'_hj = sum_i A'_ih H'_ij exactly, then RN(C' 2^-h_j)."""
+    P = product_P(moduli)
+    Ah = [trunc_scaled(x, int(ei)) for x, ei in zip(a_col, e)]
+    H = [trunc_scaled(x, int(h_j) - int(ei)) for x, ei in zip(dC_col, e)]
+    c = sum(x * y for x, y in zip(Ah, H))
+    lhs = 2 * sum(abs(x) * abs(y) for x, y in zip(Ah, H))
+    return round_scaled_to_double(c, int(h_j)), lhs < P

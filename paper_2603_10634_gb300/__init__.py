@@ -6,7 +6,7 @@ include/ozk2.h); this package is its thin binding.
 """
 from ._lib import Ozk2Error  # noqa: F401
 from .autograd import OzakiMatmul, matmul  # noqa: F401
-from .tune import choose_moduli, choose_moduli_batch  # noqa: F401
+from .tune import choose_moduli, choose_moduli_batch, choose_plan, choose_tile  # noqa: F401
 from .ozk2 import (  # noqa: F401
     MODES,
     BatchPlan,
@@ -16,6 +16,8 @@ from .ozk2 import (  # noqa: F401
     crt,
     device_status,
     dgemm,
+    dgemm_backward,
+    backward_exponents,
     dgemm_host,
     fp8_gemm,
     get_timing,
@@ -26,6 +28,8 @@ from .ozk2 import (  # noqa: F401
     scales,
     set_timing,
     timeline,
+    tile_width,
     workspace_size,
+    workspace_size_backward,
     workspace_size_host,
 )

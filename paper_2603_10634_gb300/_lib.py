@@ -44,7 +44,14 @@ SIGNATURES = {
                                    c_void_p, c_void_p, c_int, c_int, c_void_p, c_size_t, c_void_p]),
     "ozk2_debug_timeline": (c_int, [c_void_p, c_int]),
     "ozk2_noalloc_device_status": (c_int, [c_void_p]),
+    "ozk2_dgemm_backward": (c_int, [c_i64, c_i64, c_i64, c_void_p, c_i64, c_void_p, c_i64, c_void_p, c_i64,
+                                    c_void_p, c_i64, c_void_p, c_i64, c_int, c_void_p, c_size_t, c_void_p,
+                                    c_size_t, c_void_p]),
+    "ozk2_workspace_size_backward": (c_size_t, [c_i64, c_i64, c_i64, c_int]),
+    "ozk2_debug_backward_exponents": (c_int, [c_i64, c_i64, c_i64, c_int, c_void_p, c_void_p, c_void_p, c_void_p]),
     "ozk2_set_wait_limit": (ctypes.c_uint64, [ctypes.c_uint64]),
+    "ozk2_set_tile_n": (c_int, [c_int]),
+    "ozk2_batch_plan_tile_n": (c_int, [c_void_p]),
     "ozk2_debug_inject_fault": (c_int, [c_int]),
     "ozk2_status_string": (ctypes.c_char_p, [c_int]),
     "ozk2_device_status": (c_int, [c_void_p, c_void_p]),

@@ -99,6 +99,22 @@ void read_fault_env() {
 
 std::atomic<unsigned long long> g_wait_ns{0};  // 0: the default limit of the kernels
 
+// ------------------------------------------------------------------ tile width
+// The FP8 products run in 128 x 256 or 128 x 128 output tiles.  ozk2_set_tile_n fixes
+// one; 0 (the default) lets the rule below choose: the narrow tile where the wide one
+// would pad the product's columns by a quarter or more (ceil(n/256) 256 >= 1.25 ceil(n/128)
+// 128), since the wide tile otherwise runs the tensor cores more efficiently.
+std::atomic<int> g_tile_n{0};
+
+int64_t padded(int64_t n, int64_t t) { return ((n + t - 1) / t) * t; }
+
+int tile_rule(int64_t padded256, int64_t padded128) { return 4 * padded256 >= 5 * padded128 ? 128 : 256; }
+
+int tile_for(int64_t n) {
+  const int t = g_tile_n.load();
+  return t ? t : tile_rule(padded(n, 256), padded(n, 128));
+}
+
 // ------------------------------------------------------------------ workspace checks
 // A caller workspace must be device memory of the current device: the FP8 product kernels
 // read it through TMA tensor maps, and nothing else (host, managed or another GPU's memory)
@@ -369,6 +385,7 @@ cudaError_t bound_rows(Ctx& c, int64_t i0, int rows) {
   g.R = c.at<float>(L.R) + i0;
   g.S = c.at<float>(L.S);
   g.flags = c.at<uint32_t>(L.flags);
+  g.tile_n = tile_for(c.n);
   if (!launch_controls(g)) return cudaErrorLaunchFailure;
   t_launches += 1;
   return launch_fp8_gemm(g, c.at<uint8_t>(L.Abar) + i0 * L.kp, L.kp, 1, c.at<uint8_t>(L.BbarT), L.kp, 1, c.st);
@@ -443,6 +460,7 @@ ozk2_status products_rows(Ctx& c, int64_t i0, int rows, cudaStream_t st) {
   g.flags = c.at<uint32_t>(L.flags);
   g.plane_stride_a = int64_t(c.m) * L.ldp;
   g.plane_stride_b = int64_t(c.n) * L.ldp;
+  g.tile_n = tile_for(c.n);
   if (!launch_controls(g)) return OZK2_ERR_CUDA;
   OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA) + i0 * L.ldp, L.ldp, L.planes, c.at<uint8_t>(L.planesB),
                            L.ldp, L.planes, st));
@@ -834,6 +852,213 @@ size_t host_workspace_bytes(int64_t m, int64_t n, int64_t k, int N, bool fast) {
   return make_layout(m, n, k, N, fast).total + make_staging(m, n, k).total;
 }
 
+// ------------------------------------------------------------------ gradients with reuse
+// dA = dC B^T and dB = A^T dC for C = A B computed in a caller workspace, reusing that
+// call's exponents e, f and digit planes of A' = trunc(diag(2^e) A), B' = trunc(B diag(2^f)):
+//   dA: G'_ij = trunc(2^(g_i - f_j) dC_ij); (G' B'^T)_ih = 2^g_i dA_ih (up to truncation)
+//   dB: H'_ij = trunc(2^(h_j - e_i) dC_ij); (A'^T H')_hj = 2^h_j dB_hj
+// The exponents g, h of dC's side come from FP8 bound products of |dC| with |B| (rows of
+// B as lines) and of |A| (columns as lines) with |dC|, whose maxima remove the lines'
+// own FP8 scalings (colshift / rowshift), under the budget Q = log2(P - 1) - 1 (B' and A'
+// are fixed).  The forward's planes are transposed into the layout the products read.
+struct BwLayout {
+  int64_t np, mp, ldrk, ldrn;
+  int planes;
+  size_t flags, R, S, Rk, Sk, colmaxA, colbadA, colmaxC, colbadC, zk, zero_end;
+  size_t gp, hp, g, h, t, tA, rstatC, cstatC, rstatB, cstatA;
+  size_t Gbar, Bhat, AhatT, HhatT, planesG, planesBT, planesAT, planesH, cresA, cresB, scratch, total;
+};
+
+BwLayout make_bw_layout(int64_t m, int64_t n, int64_t k, int N) {
+  BwLayout L;
+  L.np = ((n + 31) / 32) * 32;
+  L.mp = ((m + 31) / 32) * 32;
+  L.ldrk = ((k + 7) / 8) * 8;
+  L.ldrn = ((n + 7) / 8) * 8;
+  L.planes = (N <= kNumSquares) ? 2 * N : 3 * N - kNumSquares;
+  size_t o = 0;
+  auto take = [&o](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.flags = take(256);
+  L.R = take(4 * size_t(m));
+  L.S = take(4 * size_t(n));
+  L.Rk = take(4 * size_t(k));
+  L.Sk = take(4 * size_t(k));
+  L.colmaxA = take(8 * size_t(k));
+  L.colbadA = take(4 * size_t(k));
+  L.colmaxC = take(8 * size_t(n));
+  L.colbadC = take(4 * size_t(n));
+  L.zk = take(4 * size_t(k));
+  L.zero_end = o;
+  L.gp = take(4 * size_t(m));
+  L.hp = take(4 * size_t(n));
+  L.g = take(4 * size_t(m));
+  L.h = take(4 * size_t(n));
+  L.t = take(4 * size_t(k));
+  L.tA = take(4 * size_t(k));
+  L.rstatC = take(size_t(m));
+  L.cstatC = take(size_t(n));
+  L.rstatB = take(size_t(k));
+  L.cstatA = take(size_t(k));
+  L.Gbar = take(size_t(m) * L.np);
+  L.Bhat = take(size_t(k) * L.np);
+  L.AhatT = take(size_t(k) * L.mp);
+  L.HhatT = take(size_t(n) * L.mp);
+  L.planesG = take(size_t(L.planes) * m * L.np);
+  L.planesBT = take(size_t(L.planes) * k * L.np);
+  L.planesAT = take(size_t(L.planes) * k * L.mp);
+  L.planesH = take(size_t(L.planes) * n * L.mp);
+  L.cresA = take(2 * size_t(N) * m * L.ldrk);
+  L.cresB = take(2 * size_t(N) * k * L.ldrn);
+  L.scratch = take(fp8_gemm_scratch_bytes(kMaxGemmCtas));
+  L.total = o;
+  return L;
+}
+
+// One bound product for the gradient exponents (single problem, accurate mode).
+cudaError_t bw_bound(const Ctx& c, const uint8_t* a, const uint8_t* b, int64_t pitch, int rows, int cols, int len,
+                     float* R, float* S, const int32_t* colshift, const int32_t* rowshift, uint32_t* flags) {
+  GemmArgs g{};
+  g.mode = kModeBound;
+  g.m = rows;
+  g.n = cols;
+  g.k = len;
+  g.num_sms = c.num_sms;
+  g.factor = bound_factor_f32(len);
+  g.R = R;
+  g.S = S;
+  g.colshift = colshift;
+  g.rowshift = rowshift;
+  g.flags = flags;
+  g.tile_n = tile_for(cols);
+  if (!launch_controls(g)) return cudaErrorLaunchFailure;
+  t_launches += 1;
+  return launch_fp8_gemm(g, a, pitch, 1, b, pitch, 1, c.st);
+}
+
+// Residue products of one gradient: `planes` planes of a (rows lines) and b (cols lines),
+// contraction len, row pitch `pitch`, into cres (N x rows x ldr).
+cudaError_t bw_products(const Ctx& c, const uint8_t* a, const uint8_t* b, int64_t pitch, int rows, int cols, int len,
+                        int16_t* cres, int64_t ldr, uint32_t* scratch, uint32_t* flags) {
+  GemmArgs g{};
+  g.mode = kModeResidue;
+  g.m = rows;
+  g.n = cols;
+  g.k = len;
+  g.num_sms = c.num_sms;
+  g.cres = cres;
+  g.ldr = ldr;
+  g.res_stride = int64_t(rows) * ldr;
+  g.scratch = scratch;
+  g.mt = &c.tab->mt;
+  g.flags = flags;
+  g.plane_stride_a = int64_t(rows) * pitch;
+  g.plane_stride_b = int64_t(cols) * pitch;
+  g.tile_n = tile_for(cols);
+  if (!launch_controls(g)) return cudaErrorLaunchFailure;
+  t_launches += 1;
+  return launch_fp8_gemm(g, a, pitch, c.tab->mt.num_planes, b, pitch, c.tab->mt.num_planes, c.st);
+}
+
+ozk2_status run_backward(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                         int64_t ldb, const double* dC, int64_t lddc, double* dA, int64_t ldda, double* dB,
+                         int64_t lddb, int N, const void* fws, size_t fws_bytes, void* ws, size_t ws_bytes,
+                         cudaStream_t st) {
+  Ctx c;
+  c.m = int(m);
+  c.n = int(n);
+  c.k = int(k);
+  c.N = N;
+  c.st = st;
+  if (!device_info(&c.num_sms)) return OZK2_ERR_UNSUPPORTED;
+  if (!encode_fn()) return OZK2_ERR_CUDA;
+  c.tab = tables_for(N);
+  if (!c.tab) return OZK2_ERR_INTERNAL;
+  const Layout FL = make_layout(m, n, k, N, false);
+  if (!fws || fws_bytes < FL.total || (reinterpret_cast<uintptr_t>(fws) & 255u) || !device_memory_here(fws))
+    return OZK2_ERR_INVALID_VALUE;
+  const BwLayout L = make_bw_layout(m, n, k, N);
+  uint8_t* w;
+  if (ws) {
+    if (ws_bytes < L.total || (reinterpret_cast<uintptr_t>(ws) & 255u) || !device_memory_here(ws))
+      return OZK2_ERR_INVALID_VALUE;
+    w = static_cast<uint8_t*>(ws);
+  } else {
+    ozk2_status err = OZK2_OK;
+    w = owned_workspace(L.total, &err);
+    if (!w) return err;
+  }
+  auto at = [w](size_t off) { return w + off; };
+  const uint8_t* f8 = static_cast<const uint8_t*>(fws);
+  const int32_t* e = reinterpret_cast<const int32_t*>(f8 + FL.e);
+  const int32_t* f = reinterpret_cast<const int32_t*>(f8 + FL.f);
+  const uint8_t* planesA = f8 + FL.planesA;
+  const uint8_t* planesB = f8 + FL.planesB;
+  uint32_t* flags = reinterpret_cast<uint32_t*>(at(L.flags));
+  const int P = L.planes;
+  int32_t* gp = reinterpret_cast<int32_t*>(at(L.gp));
+  int32_t* hp = reinterpret_cast<int32_t*>(at(L.hp));
+  int32_t* g = reinterpret_cast<int32_t*>(at(L.g));
+  int32_t* h = reinterpret_cast<int32_t*>(at(L.h));
+  const int32_t* zk = reinterpret_cast<const int32_t*>(at(L.zk));
+  OZK2_TRY(cudaMemsetAsync(w, 0, L.zero_end, st));
+  const bool wantA = dA != nullptr, wantB = dB != nullptr;
+  // bounds and exponents of dC's rows (dA) and columns (dB)
+  if (wantA) {
+    OZK2_TRY(launch_scale_rows(dC, lddc, c.m, c.n, int(L.np), gp, at(L.rstatC), at(L.Gbar), nullptr, false, flags, st));
+    OZK2_TRY(launch_scale_rows(B, ldb, c.k, c.n, int(L.np), reinterpret_cast<int32_t*>(at(L.t)), at(L.rstatB),
+                               at(L.Bhat), nullptr, false, flags, st));
+    OZK2_TRY(bw_bound(c, at(L.Gbar), at(L.Bhat), L.np, c.m, c.k, c.n, reinterpret_cast<float*>(at(L.R)),
+                      reinterpret_cast<float*>(at(L.Sk)), reinterpret_cast<const int32_t*>(at(L.t)), nullptr, flags));
+    t_launches += 2;
+  }
+  if (wantB) {
+    unsigned long long* cmC = reinterpret_cast<unsigned long long*>(at(L.colmaxC));
+    uint32_t* cbC = reinterpret_cast<uint32_t*>(at(L.colbadC));
+    OZK2_TRY(launch_colmax(dC, lddc, c.m, c.n, cmC, cbC, st));
+    OZK2_TRY(launch_scale_cols(dC, lddc, c.m, c.n, int(L.mp), cmC, cbC, hp, at(L.cstatC), at(L.HhatT), nullptr,
+                               nullptr, false, flags, st));
+    unsigned long long* cmA = reinterpret_cast<unsigned long long*>(at(L.colmaxA));
+    uint32_t* cbA = reinterpret_cast<uint32_t*>(at(L.colbadA));
+    OZK2_TRY(launch_colmax(A, lda, c.m, c.k, cmA, cbA, st));
+    OZK2_TRY(launch_scale_cols(A, lda, c.m, c.k, int(L.mp), cmA, cbA, reinterpret_cast<int32_t*>(at(L.tA)),
+                               at(L.cstatA), at(L.AhatT), nullptr, nullptr, false, flags, st));
+    OZK2_TRY(bw_bound(c, at(L.AhatT), at(L.HhatT), L.mp, c.k, c.n, c.m, reinterpret_cast<float*>(at(L.Rk)),
+                      reinterpret_cast<float*>(at(L.S)), nullptr, reinterpret_cast<const int32_t*>(at(L.tA)), flags));
+    t_launches += 4;
+  }
+  OZK2_TRY(launch_reuse_exponents(wantA ? c.m : 0, gp, at(L.rstatC), reinterpret_cast<float*>(at(L.R)), g,
+                                  wantB ? c.n : 0, hp, at(L.cstatC), reinterpret_cast<float*>(at(L.S)), h,
+                                  reuse_budget_f32(N), flags, st));
+  // dC's two integer matrices from one read of dC; the forward's planes transposed
+  OZK2_TRY(launch_grad_residues(dC, lddc, c.m, c.n, g, f, h, e, wantA ? at(L.planesG) : nullptr, L.np,
+                                wantB ? at(L.planesH) : nullptr, L.mp, c.tab->mt, flags, st));
+  t_launches += 2;
+  uint32_t* scratch = reinterpret_cast<uint32_t*>(at(L.scratch));
+  if (wantA) {
+    OZK2_TRY(launch_transpose_planes(planesB, FL.ldp, int64_t(n) * FL.ldp, c.n, c.k, at(L.planesBT), L.np,
+                                     int64_t(k) * L.np, P, st));
+    OZK2_TRY(bw_products(c, at(L.planesG), at(L.planesBT), L.np, c.m, c.k, c.n,
+                         reinterpret_cast<int16_t*>(at(L.cresA)), L.ldrk, scratch, flags));
+    OZK2_TRY(launch_crt(reinterpret_cast<int16_t*>(at(L.cresA)), L.ldrk, int64_t(m) * L.ldrk, c.m, c.k, g, zk,
+                        at(L.rstatC), at(L.rstatB), dA, ldda, c.tab->ct, st));
+    t_launches += 2;
+  }
+  if (wantB) {
+    OZK2_TRY(launch_transpose_planes(planesA, FL.ldp, int64_t(m) * FL.ldp, c.m, c.k, at(L.planesAT), L.mp,
+                                     int64_t(k) * L.mp, P, st));
+    OZK2_TRY(bw_products(c, at(L.planesAT), at(L.planesH), L.mp, c.k, c.n, c.m,
+                         reinterpret_cast<int16_t*>(at(L.cresB)), L.ldrn, scratch, flags));
+    OZK2_TRY(launch_crt(reinterpret_cast<int16_t*>(at(L.cresB)), L.ldrn, int64_t(k) * L.ldrn, c.k, c.n, zk, h,
+                        at(L.cstatA), at(L.cstatC), dB, lddb, c.tab->ct, st));
+    t_launches += 2;
+  }
+  return OZK2_OK;
+}
+
 // ------------------------------------------------------------------ batches
 // A batch plan: the descriptors of every problem, uploaded once into a device workspace,
 // and the totals of each grouped launch.  Executing it issues one launch per phase for
@@ -864,6 +1089,7 @@ struct ozk2_batch_plan_st {
   int64_t totals[ozk2::kBatchKernels] = {};
   int64_t units_bound = 0, units_res = 0;
   int num_sms = 0;
+  int tile_n = 256;  // tile width of the plan's FP8 products
   const void* tab = nullptr;  // ozk2::Tables
   uint8_t* host = nullptr;    // pinned copy of the uploaded descriptors
   size_t host_bytes = 0;
@@ -1068,13 +1294,24 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
   }
   for (int w = 0; w < kBatchKernels; ++w) plan->totals[w] = running[w];
   std::stable_sort(order.begin(), order.end(), [&probs](int a, int b) { return probs[a].k > probs[b].k; });
+  // one tile width for the whole plan: the setting, else the rule on the batch's total
+  // padded tensor work (sum of m k ceil(n / t) t)
+  {
+    int64_t w256 = 0, w128 = 0;
+    for (const BatchProblem& q : probs) {
+      w256 += int64_t(q.m) * q.k * padded(q.n, 256) / 64;
+      w128 += int64_t(q.m) * q.k * padded(q.n, 128) / 64;
+    }
+    const int t = g_tile_n.load();
+    plan->tile_n = t ? t : tile_rule(w256, w128);
+  }
   std::vector<GemmProblem> gres(probs.size()), gbound(fast ? 0 : probs.size());
   int64_t ures = 0, ubound = 0;
   for (size_t r = 0; r < order.size(); ++r) {
     const BatchProblem& q = probs[size_t(order[r])];
     GemmProblem& g = gres[r];
     std::memset(&g, 0, sizeof(g));
-    if (!encode_gemm_problem(&g, q.planesA, q.planesB, q.ldp, tab->mt.num_planes, q.m, q.n, q.k)) {
+    if (!encode_gemm_problem(&g, q.planesA, q.planesB, q.ldp, tab->mt.num_planes, q.m, q.n, q.k, plan->tile_n)) {
       destroy_plan(plan);
       return OZK2_ERR_INTERNAL;
     }
@@ -1084,11 +1321,11 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
     g.cres = q.cres;
     g.ldr = q.ldr;
     g.res_stride = int64_t(q.m) * q.ldr;
-    ures += fp8_gemm_units(kModeResidue, q.m, q.n, N);
+    ures += fp8_gemm_units(kModeResidue, q.m, q.n, N, plan->tile_n);
     if (!fast) {
       GemmProblem& b = gbound[r];
       std::memset(&b, 0, sizeof(b));
-      if (!encode_gemm_problem(&b, q.Abar, q.BbarT, q.kp, 1, q.m, q.n, q.k)) {
+      if (!encode_gemm_problem(&b, q.Abar, q.BbarT, q.kp, 1, q.m, q.n, q.k, plan->tile_n)) {
         destroy_plan(plan);
         return OZK2_ERR_INTERNAL;
       }
@@ -1096,7 +1333,7 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
       b.factor = bound_factor_f32(q.k);
       b.R = q.R;
       b.S = q.S;
-      ubound += fp8_gemm_units(kModeBound, q.m, q.n, N);
+      ubound += fp8_gemm_units(kModeBound, q.m, q.n, N, plan->tile_n);
     }
   }
   plan->units_res = ures;
@@ -1149,6 +1386,7 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
   GemmArgs g{};
   g.num_sms = plan->num_sms;
   g.flags = flags;
+  g.tile_n = plan->tile_n;
   if (!plan->fast) {
     g.mode = kModeBound;
     if (!launch_controls(g)) return OZK2_ERR_CUDA;
@@ -1393,7 +1631,61 @@ int ozk2_debug_timeline(float* ms, int max) {
 
 int ozk2_last_launch_count(void) { return t_launches; }
 
+size_t ozk2_workspace_size_backward(int64_t m, int64_t n, int64_t k, int num_moduli) {
+  if (check_sizes(m, n, k, num_moduli) != OZK2_OK) return 0;
+  return make_bw_layout(m, n, k, num_moduli).total;
+}
+
+ozk2_status ozk2_dgemm_backward(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                                int64_t ldb, const double* dC, int64_t lddc, double* dA, int64_t ldda, double* dB,
+                                int64_t lddb, int num_moduli, const void* forward_workspace,
+                                size_t forward_workspace_bytes, void* workspace, size_t workspace_bytes,
+                                ozk2_stream_t stream) {
+  t_launches = 0;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ozk2_status s = check_sizes(m, n, k, num_moduli);
+  if (s != OZK2_OK) return s;
+  if (lda < std::max<int64_t>(1, k) || ldb < std::max<int64_t>(1, n) || lddc < std::max<int64_t>(1, n) ||
+      (dA && ldda < std::max<int64_t>(1, k)) || (dB && lddb < std::max<int64_t>(1, n)))
+    return OZK2_ERR_INVALID_VALUE;
+  // empty shapes: dA (m x k) and dB (k x n) are zero where their reduction is empty
+  if (m == 0 || n == 0 || k == 0) {
+    if (dA && m > 0 && k > 0) OZK2_TRY(cudaMemset2DAsync(dA, size_t(ldda) * 8, 0, size_t(k) * 8, size_t(m), st));
+    if (dB && k > 0 && n > 0) OZK2_TRY(cudaMemset2DAsync(dB, size_t(lddb) * 8, 0, size_t(n) * 8, size_t(k), st));
+    return OZK2_OK;
+  }
+  if (!A || !B || !dC || (!dA && !dB)) return OZK2_ERR_INVALID_VALUE;
+  return run_backward(m, n, k, A, lda, B, ldb, dC, lddc, dA, ldda, dB, lddb, num_moduli, forward_workspace,
+                      forward_workspace_bytes, workspace, workspace_bytes, st);
+}
+
+ozk2_status ozk2_debug_backward_exponents(int64_t m, int64_t n, int64_t k, int num_moduli, const void* workspace,
+                                          int32_t* g, int32_t* h, ozk2_stream_t stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  ozk2_status s = check_sizes(m, n, k, num_moduli);
+  if (s != OZK2_OK) return s;
+  const BwLayout L = make_bw_layout(m, n, k, num_moduli);
+  const uint8_t* w = static_cast<const uint8_t*>(workspace);
+  if (!w) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return OZK2_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_ws_mutex);
+    if (g_ws[dev].bytes < L.total) return OZK2_ERR_INVALID_VALUE;
+    w = static_cast<const uint8_t*>(g_ws[dev].ptr);
+  }
+  if (g) OZK2_TRY(cudaMemcpyAsync(g, w + L.g, 4 * size_t(m), cudaMemcpyDeviceToDevice, st));
+  if (h) OZK2_TRY(cudaMemcpyAsync(h, w + L.h, 4 * size_t(n), cudaMemcpyDeviceToDevice, st));
+  return OZK2_OK;
+}
+
 uint64_t ozk2_set_wait_limit(uint64_t ns) { return static_cast<uint64_t>(g_wait_ns.exchange(ns)); }
+
+int ozk2_set_tile_n(int tile_n) {
+  if (tile_n != 0 && tile_n != 128 && tile_n != 256) return -1;
+  return g_tile_n.exchange(tile_n);
+}
+
+int ozk2_batch_plan_tile_n(ozk2_batch_plan plan) { return plan ? plan->tile_n : -1; }
 
 int ozk2_debug_inject_fault(int kind) {
   std::lock_guard<std::mutex> lk(g_fault_mutex);
@@ -1433,6 +1725,7 @@ ozk2_status ozk2_debug_fp8_gemm(int64_t m, int64_t n, int64_t k, const uint8_t* 
   uint8_t* ws = owned_workspace(256, &err);  // flag word only
   if (!ws) return err;
   g.flags = reinterpret_cast<uint32_t*>(ws);
+  g.tile_n = tile_for(n);
   if (!launch_controls(g)) return OZK2_ERR_CUDA;
   OZK2_TRY(launch_fp8_gemm(g, A8, lda8, 1, B8, ldb8, 1, st));
   return OZK2_OK;

@@ -52,19 +52,27 @@ namespace ozk2 {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 256;
+constexpr int BNMAX = 256;  // the wider of the two tile widths (scratch is sized for it)
 constexpr int BK = 128;  // bytes = FP8 elements per k-step (one 128-byte swizzle row)
-constexpr int kStages = 4;
 constexpr int kATileBytes = BM * BK;  // 16 KiB
-constexpr int kBTileBytes = BN * BK;  // 32 KiB
-constexpr int kStageBytes = kATileBytes + kBTileBytes;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
-constexpr uint32_t kTmemCols = 512;
 constexpr int kChunkKaratsuba = 65536;  // 2^16 * 16 * 16 = 2^24
 constexpr int kChunkSquare = 32768;     // shared accumulator: 2 * 2^15 * 16 * 16 = 2^24
 constexpr int kGroupM = 16;             // tile rasterisation: bands of 16 tile rows (2048 rows of A)
-constexpr size_t kSmemBytes = 1024 + static_cast<size_t>(kStages) * kStageBytes + 256;
+
+// Tile shapes: 128 x 256 (the default) or 128 x 128 (narrow or ragged products, where a
+// 256-wide tile would spend much of its tensor work on padding).  Both keep two TMEM
+// accumulator slots of TN columns and fill about 192 KiB of shared memory with stages.
+template <int TN>
+struct Tile {
+  static_assert(TN == 256 || TN == 128, "tile widths 256 and 128");
+  static constexpr int kStages = TN == 256 ? 4 : 6;
+  static constexpr int kBTileBytes = TN * BK;
+  static constexpr int kStageBytes = kATileBytes + kBTileBytes;
+  static constexpr uint32_t kTmemCols = 2 * TN;
+  static constexpr size_t kSmemBytes = 1024 + static_cast<size_t>(kStages) * kStageBytes + 256;
+};
 
 struct EpiMod {
   int p[kMaxModuli];
@@ -81,7 +89,7 @@ struct GemmParams {
   int16_t* cres;
   int64_t ldr;
   int64_t res_stride;
-  uint32_t* scratch;  // residue mode: BM x BN words per CTA
+  uint32_t* scratch;  // residue mode: BM x BNMAX words per CTA
   EpiMod mod;
   float factor;
   float* R;
@@ -89,6 +97,10 @@ struct GemmParams {
   float* D;
   int64_t ldd;
   uint32_t* flags;
+  // bound mode: cbar_ij is also scaled by 2^-colshift_j and 2^-rowshift_i before the
+  // maxima (each may be null; values clamped to [-126, 126], below that kFlagRange)
+  const int32_t* colshift;
+  const int32_t* rowshift;
   unsigned long long wait_ns;  // limit of every device wait (the drains of an abort use the default)
   int stall;                   // fault injection: the MMA thread's first wait never completes
 };
@@ -307,11 +319,15 @@ __device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int 
   }
 }
 
-// GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).
-template <int MODE, bool GROUPED>
+// GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).  TN: tile width.
+template <int MODE, bool GROUPED, int TN>
 __global__ void __launch_bounds__(kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ GemmParams prm, const GemmProblem* __restrict__ probs, int nprobs) {
+  constexpr int BN = TN;
+  constexpr int kStages = Tile<TN>::kStages;
+  constexpr int kStageBytes = Tile<TN>::kStageBytes;
+  constexpr uint32_t kTmemCols = Tile<TN>::kTmemCols;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* tiles = smem;
@@ -493,7 +509,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
     // the CTA's parking tile: BM x BN int16 (the first half of its scratch words)
-    int16_t* scr = reinterpret_cast<int16_t*>(prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BN)) +
+    int16_t* scr = reinterpret_cast<int16_t*>(prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BNMAX)) +
                    row * BN + chalf * (BN / 2);
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
@@ -590,6 +606,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
           } else if constexpr (MODE == kModeBound) {
             float rmax = 0.0f;
+            // 2^-s for an integer s clamped to [-126, 126] (an upper bound of 2^-s for
+            // every s >= -126; smaller s is out of range and flagged)
+            auto pow2_neg = [&](int s) {
+              if (s < -126) atomicOr(prm.flags, kFlagRange);
+              s = max(-126, min(126, s));
+              return __int_as_float((127 - s) << 23);
+            };
+            const float rscale = (GROUPED || !prm.rowshift || gi >= uc.m) ? 1.0f : pow2_neg(prm.rowshift[gi]);
+            const bool cshift = !GROUPED && prm.colshift != nullptr;
 #pragma unroll 1
             for (int cb = 0; cb < BN / 64; ++cb) {
               uint32_t v0[32];
@@ -600,6 +625,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
                 float cj = __fmul_ru(uc.factor, __uint_as_float(v0[j]));
+                if (cshift && gc + j < uc.n) cj = __fmul_ru(cj, pow2_neg(prm.colshift[gc + j]));
+                if (!GROUPED && prm.rowshift) cj = __fmul_ru(cj, rscale);
                 cj = (gi < uc.m && gc + j < uc.n) ? cj : 0.0f;
                 rmax = fmaxf(rmax, cj);
                 cv[j] = cj;
@@ -652,21 +679,31 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int MODE, bool GROUPED>
+template <int MODE, bool GROUPED, int TN>
 cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
                         const GemmProblem* probs, int nprobs, cudaStream_t st) {
   static bool configured[64] = {false};
+  constexpr size_t smem = Tile<TN>::kSmemBytes;
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kSmemBytes));
+    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED, TN>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     configured[dev] = true;
   }
-  fp8_gemm_kernel<MODE, GROUPED><<<grid, kThreads, kSmemBytes, st>>>(ta, tb, prm, probs, nprobs);
+  fp8_gemm_kernel<MODE, GROUPED, TN><<<grid, kThreads, smem, st>>>(ta, tb, prm, probs, nprobs);
   return cudaGetLastError();
 }
+
+template <int MODE, bool GROUPED>
+cudaError_t launch_tile(int tn, const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
+                        const GemmProblem* probs, int nprobs, cudaStream_t st) {
+  if (tn == 128) return launch_mode<MODE, GROUPED, 128>(prm, ta, tb, grid, probs, nprobs, st);
+  return launch_mode<MODE, GROUPED, 256>(prm, ta, tb, grid, probs, nprobs, st);
+}
+
+int tile_width(int tile_n) { return tile_n == 128 ? 128 : 256; }
 
 void fill_mod(GemmParams& prm, const ModTable& mt) {
   for (int l = 0; l < mt.N; ++l) {
@@ -679,7 +716,7 @@ void fill_mod(GemmParams& prm, const ModTable& mt) {
 
 }  // namespace
 
-size_t fp8_gemm_scratch_bytes(int num_ctas) { return static_cast<size_t>(num_ctas) * BM * BN * 4; }
+size_t fp8_gemm_scratch_bytes(int num_ctas) { return static_cast<size_t>(num_ctas) * BM * BNMAX * 4; }
 
 cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a, const uint8_t* b,
                             int64_t ldb8, int planes_b, cudaStream_t st) {
@@ -688,6 +725,7 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.m = g.m;
   prm.n = g.n;
   prm.k = g.k;
+  const int BN = tile_width(g.tile_n);
   prm.tiles_m = (g.m + BM - 1) / BM;
   prm.tiles_n = (g.n + BN - 1) / BN;
   prm.tiles = prm.tiles_m * prm.tiles_n;
@@ -707,6 +745,8 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.D = g.D;
   prm.ldd = g.ldd;
   prm.flags = g.flags;
+  prm.colshift = g.colshift;
+  prm.rowshift = g.rowshift;
   prm.wait_ns = g.wait_ns;
   prm.stall = g.stall ? 1 : 0;
 
@@ -717,21 +757,23 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {
     case kModeResidue:
-      return launch_mode<kModeResidue, false>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeResidue, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
     case kModeBound:
-      return launch_mode<kModeBound, false>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeBound, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
     default:
-      return launch_mode<kModeRaw, false>(prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeRaw, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
   }
 }
 
-int64_t fp8_gemm_units(int mode, int m, int n, int N) {
+int64_t fp8_gemm_units(int mode, int m, int n, int N, int tile_n) {
+  const int BN = tile_width(tile_n);
   const int64_t tiles = static_cast<int64_t>((m + BM - 1) / BM) * ((n + BN - 1) / BN);
   return tiles * (mode == kModeResidue ? N : 1);
 }
 
 bool encode_gemm_problem(GemmProblem* gp, const uint8_t* a, const uint8_t* b, int64_t ld8, int planes, int m, int n,
-                         int k) {
+                         int k, int tile_n) {
+  const int BN = tile_width(tile_n);
   if (!encode_fp8_map(&gp->ta, a, k, m, planes, ld8, 0, BM, BK)) return false;
   if (!encode_fp8_map(&gp->tb, b, k, n, planes, ld8, 0, BN, BK)) return false;
   gp->m = m;
@@ -762,9 +804,10 @@ cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs,
   std::memset(&unused, 0, sizeof(unused));
   const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
+  const int BN = tile_width(g.tile_n);
   if (g.mode == kModeResidue)
-    return launch_mode<kModeResidue, true>(prm, unused, unused, grid, probs, count, st);
-  return launch_mode<kModeBound, true>(prm, unused, unused, grid, probs, count, st);
+    return launch_tile<kModeResidue, true>(BN, prm, unused, unused, grid, probs, count, st);
+  return launch_tile<kModeBound, true>(BN, prm, unused, unused, grid, probs, count, st);
 }
 
 }  // namespace ozk2

@@ -78,6 +78,7 @@ bool build_crt_table(int N, CrtTable* ct);
 int hybrid_moduli(int N, int* out);  // returns N or -1
 float p_prime_f32(int N);            // RD_fp32((log2(P - 1) - 1) / 2)
 float delta_f32();                   // RD_fp32(-1 / (2 - 2^-21))
+float reuse_budget_f32(int N);       // RD_fp32(log2(P - 1) - 1), the budget of one side
 float bound_factor_f32(int64_t k);   // RU_fp32(1 + k 2^-24)
 
 // ---------------------------------------------------------------------------
@@ -99,6 +100,11 @@ cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t*
                              const uint8_t* rowstat, const uint8_t* colstat,
                              const float* R, const float* S, float pprime, float delta,
                              int32_t* e, int32_t* f, cudaStream_t st);
+// Exponents of dC's rows (g from R) and columns (h from S) for the gradient products
+// that reuse the forward's integer matrices: the whole budget q = reuse_budget_f32(N).
+cudaError_t launch_reuse_exponents(int m, const int32_t* gp, const uint8_t* rstat, const float* R, int32_t* g, int n,
+                                   const int32_t* hp, const uint8_t* cstat, const float* S, int32_t* h, float q,
+                                   uint32_t* flags, cudaStream_t st);
 
 // resid.cu.  Planes: M_N planes of lines x kp bytes, row pitch ldp bytes (>= kp, a
 // multiple of 16), plane stride plane_stride bytes (0: lines * ldp; larger when the
@@ -109,6 +115,17 @@ cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int
 cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int kp, int64_t ldp,
                                  const int32_t* f, const ModTable& mt, uint8_t* planes,
                                  uint32_t* flags, cudaStream_t st, int64_t plane_stride = 0);
+
+// Gradient operands (resid.cu): the digit planes of G'_ij = trunc(2^(g_i - f_j) dC_ij)
+// (m lines along j, pitch ldg) and of H'_ij = trunc(2^(h_j - e_i) dC_ij) (n lines along i,
+// pitch ldh) from one read of dC; a null plane pointer skips that output.
+cudaError_t launch_grad_residues(const double* dC, int64_t lddc, int m, int n, const int32_t* g, const int32_t* f,
+                                 const int32_t* h, const int32_t* e, uint8_t* planesG, int64_t ldg, uint8_t* planesH,
+                                 int64_t ldh, const ModTable& mt, uint32_t* flags, cudaStream_t st);
+// dst[p][x][y] = src[p][y][x], y < lines, x < len (pitches and strides multiples of 16;
+// src_pitch >= len and dst_pitch >= lines, both rounded up to 16).
+cudaError_t launch_transpose_planes(const uint8_t* src, int64_t src_pitch, int64_t src_stride, int lines, int len,
+                                    uint8_t* dst, int64_t dst_pitch, int64_t dst_stride, int planes, cudaStream_t st);
 
 // gemm.cu
 enum GemmMode { kModeResidue = 0, kModeBound = 1, kModeRaw = 2 };
@@ -127,6 +144,8 @@ struct GemmArgs {
   float factor;
   float* R;
   float* S;
+  const int32_t* colshift;  // optional: maxima of cbar_ij 2^-colshift_j (single problems)
+  const int32_t* rowshift;  // optional: maxima of cbar_ij 2^-rowshift_i
   // raw product
   float* D;
   int64_t ldd;
@@ -137,6 +156,7 @@ struct GemmArgs {
   int64_t plane_stride_b;
   unsigned long long wait_ns;  // limit of each device wait (wait_limit_ns())
   bool stall;                  // fault injection: the kernel's first MMA wait never completes
+  int tile_n;                  // output tile width: 128, or 256 (any other value)
 };
 // A operand: `planes_a` digit planes (K-major, m x k bytes, row stride lda8 bytes, plane
 // stride plane_stride_a); B operand the same with n rows.
@@ -230,15 +250,16 @@ struct GemmProblem {  // CUtensorMap carries the 64-byte alignment TMA needs
   float* R;
   float* S;
 };
-// Units of one problem in a GEMM of mode `mode` with N moduli.
-int64_t fp8_gemm_units(int mode, int m, int n, int N);
+// Units of one problem in a GEMM of mode `mode` with N moduli and tiles of width tile_n.
+int64_t fp8_gemm_units(int mode, int m, int n, int N, int tile_n);
 // g supplies mode, num_sms, scratch, mt and flags; the problems (device memory, built on
 // the host with encode_gemm_problem) supply everything else.
 cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs, int count, int64_t total_units,
                                     cudaStream_t st);
-// Fills the maps and tiling of one problem (the rest is the caller's).
+// Fills the maps and tiling of one problem (the rest is the caller's); every problem of
+// a grouped launch uses the launch's tile width (GemmArgs::tile_n).
 bool encode_gemm_problem(GemmProblem* gp, const uint8_t* a, const uint8_t* b, int64_t ld8, int planes, int m,
-                         int n, int k);
+                         int n, int k, int tile_n);
 
 // tensor maps (api.cu)
 // Boxes of box_rows x box_cols bytes (box_cols 128 or 64, swizzled to match).

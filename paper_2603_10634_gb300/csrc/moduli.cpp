@@ -226,6 +226,16 @@ float p_prime_f32(int N) {
   return round_down_f32((lg - 1.0) / 2.0);
 }
 
+float reuse_budget_f32(int N) {
+  int mods[kMaxModuli];
+  if (hybrid_moduli(N, mods) != N) return NAN;
+  const Big Pm1 = sub_one(product_of(N));
+  int e2;
+  const double top = top_as_double(Pm1, &e2);
+  const double lg = std::log2(top) + e2;
+  return round_down_f32(lg - 1.0);
+}
+
 float delta_f32() { return round_down_f32(-1.0 / (2.0 - std::ldexp(1.0, -21))); }
 
 float bound_factor_f32(int64_t k) { return round_up_f32(1.0 + std::ldexp(static_cast<double>(k), -24)); }

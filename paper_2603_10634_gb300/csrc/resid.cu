@@ -443,6 +443,152 @@ __global__ void __launch_bounds__(256, 3) residues_cols_batch(const BatchProblem
 
 constexpr size_t kColsSmem = kTileBytes + sizeof(float) * kMaxModuli * kPow2Table;
 
+// ------------------------------------------------------------------ gradient operands
+// The upstream gradient dC (m x n, row-major) of C = A B enters both gradient products
+// that reuse the forward's integer matrices, with per-element exponents:
+//   G'_ij = trunc(2^(g_i - f_j) dC_ij)  rows i as lines, along j   (dA = dC B^T)
+//   H'_ij = trunc(2^(h_j - e_i) dC_ij)  columns j as lines, along i (dB = A^T dC)
+// One kernel reads each kTileK x kTileCols tile of dC once into shared memory (the
+// layout of the column kernel above: tile rows are rows i of dC, tile columns are
+// columns j) and converts it twice: the column pass writes H' exactly as the column
+// kernel writes B's planes; the row pass writes G' with 8 consecutive j per task, a
+// warp covering 4 rows x 64 columns (64-byte plane pieces).
+struct GradArgs {
+  const double* dC;
+  int64_t lddc;
+  int m, n;
+  const int32_t* g;  // m: exponents of dC's rows
+  const int32_t* f;  // n: the forward's column exponents of B
+  const int32_t* h;  // n: exponents of dC's columns
+  const int32_t* e;  // m: the forward's row exponents of A
+  uint8_t* planesG;  // lines m, pitch ldg, plane stride m * ldg
+  int64_t ldg;
+  uint8_t* planesH;  // lines n, pitch ldh, plane stride n * ldh
+  int64_t ldh;
+  uint32_t* flags;
+  bool do_g, do_h;  // which of the two outputs to write
+};
+
+__global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const __grid_constant__ ModTable mt) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* tile = reinterpret_cast<double*>(smem_raw);
+  float* pow2_s = reinterpret_cast<float*>(smem_raw + kTileBytes);
+  load_table(mt, pow2_s);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tiles_n = (a.n + kTileCols - 1) / kTileCols, tiles_m = (a.m + kTileK - 1) / kTileK;
+  const int64_t tiles = static_cast<int64_t>(tiles_n) * tiles_m;
+  // plane strides of the two outputs (a task's ResidArgs carries the destination's)
+  ResidArgs ah{nullptr, 0, a.n, a.m, a.m, a.ldh, nullptr, a.planesH, static_cast<int64_t>(a.n) * a.ldh, a.flags};
+  ResidArgs ag{nullptr, 0, a.m, a.n, a.n, a.ldg, nullptr, a.planesG, static_cast<int64_t>(a.m) * a.ldg, a.flags};
+  bool range_err = false;
+  for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
+    const int j0 = static_cast<int>(t % tiles_n) * kTileCols;
+    const int i0 = static_cast<int>(t / tiles_n) * kTileK;
+#pragma unroll 4
+    for (int r = warp; r < kTileK; r += 8) {
+      const int i = i0 + r;
+      const double* row = a.dC + static_cast<int64_t>(i) * a.lddc;
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int c = lane + 32 * u, j = j0 + c;
+        tile[c * kTilePitch + tile_slot(r)] = (i < a.m && j < a.n) ? __ldg(row + j) : 0.0;
+      }
+    }
+    __syncthreads();
+    // column pass: H' (lines j, positions i), a half-warp per column
+#pragma unroll 1
+    for (int round = 0; a.do_h && round < kTileCols * kTileK / (8 * 256); ++round) {
+      const int q = round * 256 + tid;
+      const int c = q >> 4, chunk = q & 15;
+      const int j = j0 + c, ib = i0 + chunk * 8;
+      const bool active = j < a.n && ib < a.m;
+      const int hj = j < a.n ? a.h[j] : 0;
+      const double* src = tile + c * kTilePitch + chunk * 8;
+      f2 cc[kPairs][kPieces];
+      int tp[kElems];
+      int any_tp = 0;
+#pragma unroll
+      for (int u = 0; u < kElems; ++u) {
+        const int i = ib + u;
+        const int ex = hj - (i < a.m ? a.e[i] : 0);
+        decode_into(cc, u, src[u ^ ((chunk >> 1) & 7)], ex, tp[u], range_err);
+        any_tp |= tp[u];
+      }
+      uint8_t* colp = a.planesH + static_cast<int64_t>(j < a.n ? j : 0) * a.ldh + (ib < a.m ? ib : 0);
+      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<0, true>(ah, mt, pow2_s, cc, tp, colp, active);
+      else cols_planes<0, false>(ah, mt, pow2_s, cc, tp, colp, active);
+    }
+    // row pass: G' (lines i, positions j); warp w, round s: rows 4 (8 s + w) + lane / 8
+#pragma unroll 1
+    for (int round = 0; a.do_g && round < kTileK * kTileCols / (8 * 256); ++round) {
+      const int r = 4 * (8 * round + warp) + (lane >> 3), chunk = lane & 7;
+      const int i = i0 + r, jb = j0 + chunk * 8;
+      const bool active = i < a.m && jb < a.n;
+      const int gi = i < a.m ? a.g[i] : 0;
+      f2 cc[kPairs][kPieces];
+      int tp[kElems];
+      int any_tp = 0;
+#pragma unroll
+      for (int u = 0; u < kElems; ++u) {
+        const int c = chunk * 8 + u, j = jb + u;
+        const int ex = gi - (j < a.n ? a.f[j] : 0);
+        decode_into(cc, u, tile[c * kTilePitch + tile_slot(r)], ex, tp[u], range_err);
+        any_tp |= tp[u];
+      }
+      uint8_t* rowp = a.planesG + static_cast<int64_t>(i < a.m ? i : 0) * a.ldg + (jb < a.n ? jb : 0);
+      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<0, true>(ag, mt, pow2_s, cc, tp, rowp, active);
+      else cols_planes<0, false>(ag, mt, pow2_s, cc, tp, rowp, active);
+    }
+    __syncthreads();  // the tile is reloaded
+  }
+  if (range_err) atomicOr(a.flags, kFlagRange);
+}
+
+// dst[p][x][y] = src[p][y][x] for y < lines, x < len: the digit planes of an operand
+// (lines x len bytes, K-major) as the planes of its transpose, through 64 x 64 byte
+// tiles in shared memory (row pitch 68 bytes: the 16 bytes a thread gathers along y
+// fall in 16 different banks).
+constexpr int kTrTile = 64, kTrPitch = 68;
+
+__global__ void __launch_bounds__(256) transpose_planes_kernel(const uint8_t* __restrict__ src, int64_t src_pitch,
+                                                               int64_t src_stride, int lines, int len,
+                                                               uint8_t* __restrict__ dst, int64_t dst_pitch,
+                                                               int64_t dst_stride, int planes) {
+  __shared__ __align__(16) uint8_t tile[kTrTile * kTrPitch];
+  const int tx = (len + kTrTile - 1) / kTrTile, ty = (lines + kTrTile - 1) / kTrTile;
+  const int64_t total = static_cast<int64_t>(tx) * ty * planes;
+  const int t = threadIdx.x, r = t >> 2, c16 = (t & 3) * 16;
+  for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
+    const int p = static_cast<int>(b / (static_cast<int64_t>(tx) * ty));
+    const int rem = static_cast<int>(b - static_cast<int64_t>(p) * tx * ty);
+    const int y0 = (rem / tx) * kTrTile, x0 = (rem % tx) * kTrTile;
+    // load: row y0 + r, bytes x0 + c16 .. + 15 (inside the source row's pitch)
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (y0 + r < lines && x0 + c16 < len)
+      v = *reinterpret_cast<const uint4*>(src + p * src_stride + static_cast<int64_t>(y0 + r) * src_pitch + x0 + c16);
+    uint32_t* tw = reinterpret_cast<uint32_t*>(tile + r * kTrPitch + c16);
+    tw[0] = v.x;
+    tw[1] = v.y;
+    tw[2] = v.z;
+    tw[3] = v.w;
+    __syncthreads();
+    // store: destination row x0 + r, bytes y0 + c16 .. + 15
+    if (x0 + r < len && y0 + c16 < lines) {
+      uint32_t w[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int z = 0; z < 4; ++z) word |= static_cast<uint32_t>(tile[(c16 + 4 * q + z) * kTrPitch + r]) << (8 * z);
+        w[q] = word;
+      }
+      *reinterpret_cast<uint4*>(dst + p * dst_stride + static_cast<int64_t>(x0 + r) * dst_pitch + y0 + c16) =
+          make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    __syncthreads();
+  }
+}
+
 // Opt a column kernel into kColsSmem bytes of dynamic shared memory, once per device
 // (a launch on a device where this failed reports the error itself).
 template <class K>
@@ -525,6 +671,36 @@ cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t 
   allow_cols_smem(residues_cols_batch, done);
   residues_rows_batch<<<static_cast<unsigned>(rows_blocks), 256, 0, st>>>(probs, count, flags, mt);
   residues_cols_batch<<<static_cast<unsigned>(cols_blocks), 256, kColsSmem, st>>>(probs, count, flags, mt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_residues(const double* dC, int64_t lddc, int m, int n, const int32_t* g, const int32_t* f,
+                                 const int32_t* h, const int32_t* e, uint8_t* planesG, int64_t ldg, uint8_t* planesH,
+                                 int64_t ldh, const ModTable& mt, uint32_t* flags, cudaStream_t st) {
+  GradArgs a{dC, lddc, m, n, g, f, h, e, planesG, ldg, planesH, ldh, flags, planesG != nullptr, planesH != nullptr};
+  static bool done[64] = {};
+  allow_cols_smem(grad_residues_kernel, done);
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = static_cast<int64_t>((n + kTileCols - 1) / kTileCols) * ((m + kTileK - 1) / kTileK);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, 3 * static_cast<int64_t>(sms)));
+  grad_residues_kernel<<<grid, 256, kColsSmem, st>>>(a, mt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_planes(const uint8_t* src, int64_t src_pitch, int64_t src_stride, int lines, int len,
+                                    uint8_t* dst, int64_t dst_pitch, int64_t dst_stride, int planes, cudaStream_t st) {
+  if ((src_pitch % 16) || (dst_pitch % 16) || (src_stride % 16) || (dst_stride % 16) || lines < 1 || len < 1 ||
+      planes < 1 || src_pitch < ((len + 15) / 16) * 16 || dst_pitch < ((lines + 15) / 16) * 16)
+    return cudaErrorInvalidValue;
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t total = static_cast<int64_t>((len + kTrTile - 1) / kTrTile) * ((lines + kTrTile - 1) / kTrTile) * planes;
+  const int grid = static_cast<int>(std::min<int64_t>(total, 8 * static_cast<int64_t>(sms)));
+  transpose_planes_kernel<<<grid, 256, 0, st>>>(src, src_pitch, src_stride, lines, len, dst, dst_pitch, dst_stride,
+                                                planes);
   return cudaGetLastError();
 }
 

@@ -294,6 +294,41 @@ __global__ void exponents_kernel(int m, int n, const int32_t* __restrict__ eprim
   exponents_body(m, n, eprime, fprime, rowstat, colstat, R, S, pprime, delta, e, f, blockIdx.x);
 }
 
+// Exponent of a line whose product partner's integers are fixed (the gradient products
+// that reuse the forward's A' or B'): g = g' + floor(RD(Q + RD(d log2 R))) with
+// Q = RD(log2(P - 1) - 1) and d = -(1 + 2^-21) for log2 R >= 0, -(1 - 2^-21) below, so
+// that d log2 R stays below -log2 R whatever the FP32 rounding of the logarithm; then
+// 2 2^(g - g') R <= P - 1.  A zero line gets 0; R = 0 gives g' + floor(Q); an infinite
+// R (its shifted bound overflowed FP32) is out of range.
+__device__ __forceinline__ int reuse_exponent(int gp, uint8_t stat, float rmax, float q, uint32_t* flags) {
+  if (stat & kLineZero) return 0;
+  if (!(rmax > 0.0f)) return gp + static_cast<int>(floorf(q));
+  if (!(rmax < INFINITY)) {
+    atomicOr(flags, kFlagRange);
+    return gp - 256;
+  }
+  const float lg = __double2float_rn(log2(static_cast<double>(rmax)));
+  const float d = lg >= 0.0f ? -(1.0f + 0x1p-21f) : -(1.0f - 0x1p-21f);
+  const float t1 = __fmul_rd(d, lg);
+  const float t2 = __fadd_rd(q, t1);
+  return gp + static_cast<int>(floorf(t2));
+}
+
+// g_i for the m rows (prelim gp, status rstat, bound R) and h_j for the n columns.
+__global__ void reuse_exponents_kernel(int m, const int32_t* __restrict__ gp, const uint8_t* __restrict__ rstat,
+                                       const float* __restrict__ R, int32_t* __restrict__ g, int n,
+                                       const int32_t* __restrict__ hp, const uint8_t* __restrict__ cstat,
+                                       const float* __restrict__ S, int32_t* __restrict__ h, float q,
+                                       uint32_t* flags) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m) {
+    g[t] = reuse_exponent(gp[t], rstat[t], R[t], q, flags);
+  } else if (t < m + n) {
+    const int j = t - m;
+    h[j] = reuse_exponent(hp[j], cstat[j], S[j], q, flags);
+  }
+}
+
 // ------------------------------------------------------------------ grouped launches
 // Problem of block `b` of grouped launch `w`: the last p with first_block[w] <= b.
 __device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
@@ -434,6 +469,15 @@ cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t*
   const int total = m + n;
   exponents_kernel<<<(total + 255) / 256, 256, 0, st>>>(m, n, eprime, fprime, rowstat, colstat, R, S,
                                                         pprime, delta, e, f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reuse_exponents(int m, const int32_t* gp, const uint8_t* rstat, const float* R, int32_t* g, int n,
+                                   const int32_t* hp, const uint8_t* cstat, const float* S, int32_t* h, float q,
+                                   uint32_t* flags, cudaStream_t st) {
+  const int total = m + n;
+  if (total <= 0) return cudaSuccess;
+  reuse_exponents_kernel<<<(total + 255) / 256, 256, 0, st>>>(m, gp, rstat, R, g, n, hp, cstat, S, h, q, flags);
   return cudaGetLastError();
 }
 

@@ -77,6 +77,25 @@ def _block(block):
     return int(bm), int(bn)
 
 
+class tile_width:
+    """Context manager fixing the output tile width of the FP8 products (256 or 128; 0 for
+    the library's rule) for the calls and batch plans made inside it (ozk2_set_tile_n,
+    a process-wide setting, restored on exit)."""
+
+    def __init__(self, tile_n):
+        if tile_n not in (0, 128, 256):
+            raise ValueError("tile_n must be 0, 128 or 256")
+        self.tile_n = int(tile_n)
+        self.prev = None
+
+    def __enter__(self):
+        self.prev = _lib.load().ozk2_set_tile_n(self.tile_n)
+        return self
+
+    def __exit__(self, *exc):
+        _lib.load().ozk2_set_tile_n(self.prev)
+
+
 def moduli(num_moduli=12):
     """The first N moduli of the hybrid list."""
     lib = _lib.load()
@@ -131,6 +150,51 @@ def dgemm(A, B, num_moduli=12, out=None, workspace=None, mode="accurate", block=
                                   md, bm, bn, _ptr(workspace), 0 if workspace is None else workspace.numel(), st)
     _lib.check(s, "ozk2_dgemm")
     return out
+
+
+def workspace_size_backward(m, n, k, num_moduli=12):
+    return int(_lib.load().ozk2_workspace_size_backward(m, n, k, num_moduli))
+
+
+def dgemm_backward(A, B, dC, forward_workspace, num_moduli=12, need_dA=True, need_dB=True, workspace=None):
+    """(dA, dB) = (dC @ B.T, A.T @ dC) for C = A @ B computed by ``dgemm(A, B, num_moduli,
+    workspace=forward_workspace)`` (accurate mode, no blocking), reusing that call's
+    exponents and digit planes (ozk2_dgemm_backward).  A, B, dC: row-major float64 CUDA
+    tensors; forward_workspace: the uint8 tensor the forward ran in, unchanged since.
+    An output not needed is returned as None."""
+    for x, name in ((A, "A"), (B, "B"), (dC, "dC")):
+        _check_matrix(x, name)
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2 or tuple(dC.shape) != (m, n):
+        raise ValueError("shapes do not match C = A @ B")
+    if forward_workspace.dtype != torch.uint8 or not forward_workspace.is_cuda:
+        raise TypeError("forward_workspace must be a uint8 CUDA tensor")
+    if workspace is not None and (workspace.dtype != torch.uint8 or not workspace.is_cuda):
+        raise TypeError("workspace must be a uint8 CUDA tensor")
+    dA = torch.empty((m, k), dtype=torch.float64, device=A.device) if need_dA else None
+    dB = torch.empty((k, n), dtype=torch.float64, device=A.device) if need_dB else None
+    lib = _lib.load()
+    with torch.cuda.device(A.device):
+        s = lib.ozk2_dgemm_backward(m, n, k, _ptr(A), _ld(A), _ptr(B), _ld(B), _ptr(dC), _ld(dC), _ptr(dA),
+                                    _ld(dA) if dA is not None else max(1, k), _ptr(dB),
+                                    _ld(dB) if dB is not None else max(1, n), num_moduli, _ptr(forward_workspace),
+                                    forward_workspace.numel(), _ptr(workspace),
+                                    0 if workspace is None else workspace.numel(), _stream(A.device))
+    _lib.check(s, "ozk2_dgemm_backward")
+    return dA, dB
+
+
+def backward_exponents(m, n, k, num_moduli=12, workspace=None, device=None):
+    """(g, h): the exponents of dC's rows and columns used by the last dgemm_backward of
+    these sizes (int32 CUDA tensors)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    g = torch.empty(m, dtype=torch.int32, device=dev)
+    h = torch.empty(n, dtype=torch.int32, device=dev)
+    s = _lib.load().ozk2_debug_backward_exponents(m, n, k, num_moduli, _ptr(workspace), _ptr(g), _ptr(h),
+                                                  _stream(dev))
+    _lib.check(s, "ozk2_debug_backward_exponents")
+    return g, h
 
 
 def workspace_size_host(m, n, k, num_moduli=12, mode="accurate"):
@@ -220,8 +284,12 @@ class BatchPlan:
     device work, so it can be captured into a CUDA graph.  The plan keeps references to
     the operands and outputs it was built for."""
 
-    def __init__(self, As, Bs, num_moduli=12, outs=None, mode="accurate", workspace=None):
+    def __init__(self, As, Bs, num_moduli=12, outs=None, mode="accurate", workspace=None, tile_n=None):
         self._lib = _lib.load()
+        if tile_n is not None:
+            with tile_width(tile_n):
+                self.__init__(As, Bs, num_moduli, outs, mode, workspace)
+            return
         count, arrs, self.outs, dev = _batch_arrays(As, Bs, outs)
         if count == 0:
             raise ValueError("empty batch")
@@ -243,6 +311,10 @@ class BatchPlan:
 
     def workspace_ptr(self):
         return self._lib.ozk2_batch_plan_workspace(self._plan)
+
+    def tile_n(self):
+        """Tile width the plan's FP8 products run with."""
+        return int(self._lib.ozk2_batch_plan_tile_n(self._plan))
 
     def status(self):
         """Device flag status of the plan's workspace (synchronises the current stream)."""

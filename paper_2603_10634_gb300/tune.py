@@ -7,8 +7,13 @@ data (phi, k, the spread of its rows and columns), so the tuner measures it: for
 candidate N it takes the exponents of the WHOLE problem (the real scaling, computed by
 the library's scaling kernels), emulates a sampled block of rows and columns of C with
 them, and compares the block with the same block emulated at N = 20 (whose error is the
-final FP64 rounding alone).  The other tunables of the path are fixed by design: one
-tile shape, and k-blocks set by exactness (2^15 / 2^16).
+final FP64 rounding alone).
+
+The tile width of the FP8 products (128 x 256 or 128 x 128 output tiles) does not change
+any result bit, only the time: choose_tile times a problem with both widths and
+choose_plan times a whole batch plan with both (after choose_moduli_batch has fixed N).
+The k-block is not a tunable: it is set by exactness (2^15 terms for the square moduli'
+shared accumulator, 2^16 for the Karatsuba moduli; Eq. error-free-FP8-matmult).
 
 Every step runs in libozk2's kernels; torch.matmul appears only as the native-FP64
 yardstick of target="fp64" and for the |A||B| normaliser of the sampled block.
@@ -90,3 +95,39 @@ def choose_moduli_batch(As, Bs, target="fp64", mode="accurate", probes=4, **kw):
         reports.append((i, N, rep))
         best = max(best, N)
     return best, reports
+
+
+def _time(fn, reps, warmup=1):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record()
+    for _ in range(reps):
+        fn()
+    s1.record()
+    torch.cuda.synchronize()
+    return s0.elapsed_time(s1) / reps
+
+
+def choose_tile(A, B, num_moduli=12, mode="accurate", reps=3):
+    """The faster tile width for this problem, measured: (tile_n, {tile_n: ms})."""
+    out = torch.empty((A.shape[0], B.shape[1]), dtype=torch.float64, device=A.device)
+    times = {}
+    for t in (256, 128):
+        with ozk2.tile_width(t):
+            times[t] = _time(lambda: ozk2.dgemm(A, B, num_moduli=num_moduli, out=out, mode=mode), reps)
+    return min(times, key=times.get), times
+
+
+def choose_plan(As, Bs, target="fp64", mode="accurate", probes=4, reps=3, **kw):
+    """Moduli count for the requested accuracy (choose_moduli_batch) and the faster tile
+    width of the whole batch plan, measured: (N, tile_n, report)."""
+    N, reports = choose_moduli_batch(As, Bs, target, mode, probes, **kw)
+    times = {}
+    for t in (256, 128):
+        plan = ozk2.BatchPlan(As, Bs, num_moduli=N, mode=mode, tile_n=t)
+        times[t] = _time(plan.execute, reps)
+        plan.close()
+    return N, min(times, key=times.get), {"moduli": reports, "plan_ms": times}
+

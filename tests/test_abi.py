@@ -224,3 +224,12 @@ def test_wait_limit_setting(lib):
     assert lib.ozk2_set_wait_limit(1000) == 0
     assert lib.ozk2_set_wait_limit(0) == 1000
     assert lib.ozk2_set_wait_limit(0) == 0
+
+
+def test_tile_setting(lib):
+    """ozk2_set_tile_n takes 0, 128 or 256 and returns the previous value."""
+    assert lib.ozk2_set_tile_n(64) == -1
+    assert lib.ozk2_set_tile_n(128) == 0
+    assert lib.ozk2_set_tile_n(256) == 128
+    assert lib.ozk2_set_tile_n(0) == 256
+    assert lib.ozk2_batch_plan_tile_n(None) == -1

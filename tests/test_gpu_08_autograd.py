@@ -25,18 +25,22 @@ def _leaf(X, cuda):
     return X.to(cuda).requires_grad_(True)
 
 
-def test_gradcheck_small(cuda):
+@pytest.mark.parametrize("reuse", [True, False])
+def test_gradcheck_small(cuda, reuse):
     A, B = workloads.problem(8, 5, 6, 1.0, seed=20)
     Ad, Bd = _leaf(A, cuda), _leaf(B, cuda)
-    assert torch.autograd.gradcheck(lambda a, b: ozk.matmul(a, b, 14), (Ad, Bd), eps=1e-6, atol=1e-9, rtol=1e-7)
+    assert torch.autograd.gradcheck(lambda a, b: ozk.matmul(a, b, 14, reuse=reuse), (Ad, Bd), eps=1e-6, atol=1e-9,
+                                    rtol=1e-7)
 
 
-def test_finite_differences_64(cuda):
+@pytest.mark.parametrize("reuse", [True, False])
+def test_finite_differences_64(cuda, reuse):
     n = 64
     A, B = workloads.problem(n, n, n, 1.0, seed=21)
     W = workloads.normal_matrix(n, n, seed=23)
     Ad, Bd, Wd = _leaf(A, cuda), _leaf(B, cuda), W.to(cuda)
-    (ozk.matmul(Ad, Bd, 14) * Wd).sum().backward()
+    (ozk.matmul(Ad, Bd, 14, reuse=reuse) * Wd).sum().backward()
+    torch_gA, torch_gB = (Wd @ B.to(cuda).T).cpu().numpy(), (A.to(cuda).T @ Wd).cpu().numpy()
     gA, gB = Ad.grad.cpu().numpy(), Bd.grad.cpu().numpy()
 
     def loss(a, b):
@@ -56,15 +60,19 @@ def test_finite_differences_64(cuda):
         bm[i, j] -= h
         fd = (loss(A.to(cuda), bp.to(cuda)) - loss(A.to(cuda), bm.to(cuda))) / (2 * h)
         assert abs(fd - gB[i, j]) <= 1e-9 * float((A.abs().T @ W.abs()).max())
+    # and against torch float64's gradients: within a few FP64 roundings of the scale
+    assert np.abs(gA - torch_gA).max() <= n * 2.0**-52 * scale
+    assert np.abs(gB - torch_gB).max() <= n * 2.0**-52 * float((A.abs().T @ W.abs()).max())
 
 
 @pytest.mark.parametrize("mode", ["accurate", "fast"])
-def test_gradients_are_emulated_products(cuda, mode):
+def test_fresh_gradients_are_emulated_products(cuda, mode):
+    """reuse=False: each gradient is a fresh emulation of the transposed product."""
     m, k, n, N = 70, 50, 40, 13
     A, B = workloads.problem(m, n, k, 1.0, seed=24)
     W = workloads.normal_matrix(m, n, seed=26)
     Ad, Bd, Wd = _leaf(A, cuda), _leaf(B, cuda), W.to(cuda)
-    C = ozk.matmul(Ad, Bd, N, mode)
+    C = ozk.matmul(Ad, Bd, N, mode, reuse=False)
     C.backward(Wd)
     assert torch.equal(C.detach(), ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=N, mode=mode))
     BT = B.T.contiguous().to(cuda)
@@ -77,12 +85,38 @@ def test_gradients_are_emulated_products(cuda, mode):
     assert ozk.device_status() == "OZK2_OK"
 
 
-def test_only_requested_gradients(cuda):
+def test_reuse_gradients_are_the_backward_call(cuda):
+    """The default (reuse=True): the gradients are ozk2_dgemm_backward's, bit-identical to
+    the oracle's reuse route given the GPU's exponents."""
+    m, k, n, N = 70, 50, 40, 13
+    A, B = workloads.problem(m, n, k, 1.0, seed=24)
+    W = workloads.normal_matrix(m, n, seed=26)
+    Ad, Bd, Wd = _leaf(A, cuda), _leaf(B, cuda), W.to(cuda)
+    C = ozk.matmul(Ad, Bd, N)
+    C.backward(Wd)
+    g, h = ozk.backward_exponents(m, n, k, N)  # before anything else reuses the library workspace
+    assert torch.equal(C.detach(), ozk.dgemm(A.to(cuda), B.to(cuda), num_moduli=N))
+    sc = ozk.scales(A.to(cuda), B.to(cuda), num_moduli=N)
+    r = oz.reuse_gradients(A.numpy(), B.numpy(), W.numpy(), N, e=sc["e"].cpu().numpy(), f=sc["f"].cpu().numpy(),
+                           g=g.cpu().numpy(), h=h.cpu().numpy())
+    assert np.array_equal(Ad.grad.cpu().numpy().view(np.uint64), r["dA"].view(np.uint64))
+    assert np.array_equal(Bd.grad.cpu().numpy().view(np.uint64), r["dB"].view(np.uint64))
+    assert ozk.device_status() == "OZK2_OK"
+
+
+@pytest.mark.parametrize("reuse", [True, False])
+def test_only_requested_gradients(cuda, reuse):
     A, B = workloads.problem(30, 20, 10, 1.0, seed=27)
     Ad, Bd = _leaf(A, cuda), B.to(cuda)
-    ozk.matmul(Ad, Bd).sum().backward()  # broadcast (zero-stride) upstream gradient
+    ozk.matmul(Ad, Bd, reuse=reuse).sum().backward()  # broadcast (zero-stride) upstream gradient
     assert Bd.grad is None
-    ref = ozk.dgemm(torch.ones(30, 20, dtype=torch.float64, device=cuda), B.T.contiguous().to(cuda))
+    ones = torch.ones(30, 20, dtype=torch.float64, device=cuda)
+    if reuse:
+        ws = torch.empty(ozk.workspace_size(30, 20, 10, 12), dtype=torch.uint8, device=cuda)
+        ozk.dgemm(A.to(cuda), B.to(cuda), workspace=ws)
+        ref = ozk.dgemm_backward(A.to(cuda), B.to(cuda), ones, ws, need_dB=False)[0]
+    else:
+        ref = ozk.dgemm(ones, B.T.contiguous().to(cuda))
     assert torch.equal(Ad.grad, ref)
 
 

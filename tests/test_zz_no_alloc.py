@@ -77,15 +77,15 @@ def test_noalloc_trivial_shapes_as_dgemm(cuda):
     ozk2_dgemm refuses them."""
     lib = _lib.load()
     st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    buf = torch.full((3000, 3000), 4.0, dtype=torch.float64, device=cuda)
+    buf = torch.full((3400, 3400), 4.0, dtype=torch.float64, device=cuda)
     p = ctypes.c_void_p(buf.data_ptr())
     assert lib.ozk2_dgemm_noalloc(0, 50000, 50000, p, 50000, p, 50000, p, 50000, 12, st) == 0
     assert lib.ozk2_dgemm_noalloc(50000, 0, 50000, p, 50000, p, 1, p, 1, 12, st) == 0
     torch.cuda.synchronize()
     assert (buf == 4.0).all().item()
-    # k = 0 with a 3000 x 3000 output: C = 0 (its workspace would exceed the array)
-    assert ozk.workspace_size(3000, 3000, 1, 12) > 256 * 1024 * 1024
-    assert lib.ozk2_dgemm_noalloc(3000, 3000, 0, p, 1, p, 3000, p, 3000, 12, st) == 0
+    # k = 0 with a 3400 x 3400 output: C = 0 (its workspace would exceed the array)
+    assert ozk.workspace_size(3400, 3400, 1, 12) > 256 * 1024 * 1024
+    assert lib.ozk2_dgemm_noalloc(3400, 3400, 0, p, 1, p, 3400, p, 3400, 12, st) == 0
     torch.cuda.synchronize()
     assert (buf == 0.0).all().item()
     big = 2**21
