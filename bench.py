@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--sizes", default="1024,4096,8192,16384", help="sweep: square sizes")
     ap.add_argument("--phis", default="0.5,1,2", help="sweep: phi values")
     ap.add_argument("--moduli-list", default="8,9,10,11,12,13,14,16,18,20", help="sweep: N values")
+    ap.add_argument("--tile", type=int, default=None, choices=[0, 128, 256],
+                    help="output tile width of the FP8 products (0: the library's rule; default: leave it)")
+    ap.add_argument("--square-split", type=int, default=None,
+                    help="square moduli as two passes for k up to this (0: never; default: the library's)")
     ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd", "batched", "sweep", "rect"],
                     help="dgemm: the square product above; autograd: forward + backward of "
                          "C = A B with A 8192 x 4096, B 4096 x 4096 and upstream gradient W ~ N(0, 1); "
@@ -70,6 +74,7 @@ def workload_config(a):
         "m": a.size, "n": a.size, "k": a.size, "phi": a.phi, "num_moduli": a.moduli, "seed": 0, "mode": a.mode,
         "l2": "inputs larger than L2 (2 x 8 k^2 bytes), no flush",
         "parallelism": f"replicas x{a.gpus}" if a.gpus > 1 else "single GPU",
+        "settings": {"tile_n": a.tile, "square_split_kmax": a.square_split},
     }
 
 
@@ -621,11 +626,13 @@ def run_batched(a, rank, world):
     As, Bs = workloads.batch_problems(shapes, a.phi, seed=0, device=dev)
     flops = sum(2.0 * m * n * k for (m, n, k) in shapes)
     stream = torch.cuda.current_stream(dev)
-    # moduli count for FP64-level accuracy, picked by the autotuner on the longest problems
+    # moduli count for FP64-level accuracy (sampled on the longest problems) and the faster
+    # tile width of the plan (timed), picked by the autotuner
     t0 = time.perf_counter()
-    N, reports = ozk.choose_moduli_batch(As, Bs, "fp64", mode=a.mode, probes=4)
+    N, tile, tune_rep = ozk.choose_plan(As, Bs, "fp64", mode=a.mode, probes=4)
+    reports = tune_rep["moduli"]
     tune_s = time.perf_counter() - t0
-    plan = ozk.BatchPlan(As, Bs, num_moduli=N, mode=a.mode)
+    plan = ozk.BatchPlan(As, Bs, num_moduli=N, mode=a.mode, tile_n=tile)
 
     def timed(fn, steps):
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -675,13 +682,14 @@ def run_batched(a, rank, world):
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f8e4m3", "emulates": "f64", "data": "synthetic",
             "config": {"workload": f"512 products, m, n, k log-uniform on [64, 2048] (seed 0), phi={a.phi}, "
-                                   f"N={N} (autotuned), {a.mode} mode", "total_flop": flops,
+                                   f"N={N}, tile 128x{tile} (autotuned), {a.mode} mode", "total_flop": flops,
                        "l2": "operands (2.7 GB) larger than L2, no flush"},
             "gpu_launches": launches * a.steps, "clocks": clk.summary(), "device_status": status,
             "plain_calls": {"ms_per_step": plain_ms, "tflops": flops / plain_ms / 1e9, "launches": 512 * single_launches,
                             "bit_identical": bool(same)},
             "cuda_graph": {"ms_per_step": graph_ms, "tflops": flops / graph_ms / 1e9},
-            "autotune": {"num_moduli": N, "target": "within 2x of native FP64 on a sampled block",
+            "autotune": {"num_moduli": N, "tile_n": tile, "plan_ms_by_tile": tune_rep["plan_ms"],
+                         "target": "within 2x of native FP64 on a sampled block",
                          "probes": [{"problem": i, "shape": shapes[i], "num_moduli": n_i,
                                      "native_err": rep["errors"]["native"], "err": rep["errors"][n_i]}
                                     for (i, n_i, rep) in reports], "seconds": tune_s},
@@ -817,9 +825,23 @@ def run_rect(a, rank, world):
             print(json.dumps(r), flush=True)
 
 
+def apply_settings(a):
+    """The library's tuning settings named on the command line (recorded in config)."""
+    if a.impl != "ours" or (a.tile is None and a.square_split is None):
+        return
+    from paper_2603_10634_gb300 import _lib
+
+    lib = _lib.load()
+    if a.tile is not None:
+        lib.ozk2_set_tile_n(a.tile)
+    if a.square_split is not None:
+        lib.ozk2_set_square_split(a.square_split)
+
+
 def main():
     a = parse()
     rank, world = dist_init(a)
+    apply_settings(a)
     if a.impl == "reference":
         run_reference(a, rank, world)
     elif a.workload == "autograd":

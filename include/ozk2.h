@@ -345,6 +345,17 @@ int ozk2_set_tile_n(int tile_n);
 int ozk2_batch_plan_tile_n(ozk2_batch_plan plan);
 
 /*
+ * ozk2_set_square_split - the residue products of a square modulus p = s^2 (Eq.
+ * 3matmult-notKaratsuba: X = A1 B2 + A2 B1, Z = A2 B2, C' = mod(s X + Z, p)) run as one
+ * pass over both tensor-memory accumulators, or, for reductions of at most kmax terms, as
+ * two single-slot passes (X, whose residue is kept, then Z), which lets the epilogue of
+ * one pass overlap the next when k is short.  Applies to calls and batch plans made
+ * after it; results are bit-identical either way.  Default 4096; 0 never splits; a
+ * negative kmax only queries.  Returns the previous (or current) setting.
+ */
+int64_t ozk2_set_square_split(int64_t kmax);
+
+/*
  * ozk2_debug_inject_fault - host-side fault injection for tests of the error paths.
  * Arms one fault that fires once, at the next point where it applies, then disarms:
  *   OZK2_FAULT_ALLOC   the next workspace allocation of the library (the library-owned

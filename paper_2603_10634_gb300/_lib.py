@@ -52,6 +52,7 @@ SIGNATURES = {
     "ozk2_set_wait_limit": (ctypes.c_uint64, [ctypes.c_uint64]),
     "ozk2_set_tile_n": (c_int, [c_int]),
     "ozk2_batch_plan_tile_n": (c_int, [c_void_p]),
+    "ozk2_set_square_split": (c_i64, [c_i64]),
     "ozk2_debug_inject_fault": (c_int, [c_int]),
     "ozk2_status_string": (ctypes.c_char_p, [c_int]),
     "ozk2_device_status": (c_int, [c_void_p, c_void_p]),

@@ -110,6 +110,12 @@ int64_t padded(int64_t n, int64_t t) { return ((n + t - 1) / t) * t; }
 
 int tile_rule(int64_t padded256, int64_t padded128) { return 4 * padded256 >= 5 * padded128 ? 128 : 256; }
 
+// Square moduli run as two single-slot passes (X, then Z) when the reduction is at most
+// this long: with short reductions the drain of both accumulator slots after a one-pass
+// square modulus leaves the tensor cores idle; with long ones the second pass rereads A2
+// and B2 from DRAM.  ozk2_set_square_split sets it.
+std::atomic<int64_t> g_split_kmax{4096};
+
 int tile_for(int64_t n) {
   const int t = g_tile_n.load();
   return t ? t : tile_rule(padded(n, 256), padded(n, 128));
@@ -461,6 +467,7 @@ ozk2_status products_rows(Ctx& c, int64_t i0, int rows, cudaStream_t st) {
   g.plane_stride_a = int64_t(c.m) * L.ldp;
   g.plane_stride_b = int64_t(c.n) * L.ldp;
   g.tile_n = tile_for(c.n);
+  g.split_squares = c.k <= g_split_kmax.load();
   if (!launch_controls(g)) return OZK2_ERR_CUDA;
   OZK2_TRY(launch_fp8_gemm(g, c.at<uint8_t>(L.planesA) + i0 * L.ldp, L.ldp, L.planes, c.at<uint8_t>(L.planesB),
                            L.ldp, L.planes, st));
@@ -958,6 +965,7 @@ cudaError_t bw_products(const Ctx& c, const uint8_t* a, const uint8_t* b, int64_
   g.plane_stride_a = int64_t(rows) * pitch;
   g.plane_stride_b = int64_t(cols) * pitch;
   g.tile_n = tile_for(cols);
+  g.split_squares = len <= g_split_kmax.load();
   if (!launch_controls(g)) return cudaErrorLaunchFailure;
   t_launches += 1;
   return launch_fp8_gemm(g, a, pitch, c.tab->mt.num_planes, b, pitch, c.tab->mt.num_planes, c.st);
@@ -1306,6 +1314,7 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
     plan->tile_n = t ? t : tile_rule(w256, w128);
   }
   std::vector<GemmProblem> gres(probs.size()), gbound(fast ? 0 : probs.size());
+  const int64_t split_kmax = g_split_kmax.load();
   int64_t ures = 0, ubound = 0;
   for (size_t r = 0; r < order.size(); ++r) {
     const BatchProblem& q = probs[size_t(order[r])];
@@ -1318,6 +1327,7 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
     // the products of one problem are addressed like those of a single call, but the
     // planes of the B operand have n rows: the map was encoded with the packed strides
     g.unit_start = ures;
+    g.split = q.k <= split_kmax ? 1 : 0;
     g.cres = q.cres;
     g.ldr = q.ldr;
     g.res_stride = int64_t(q.m) * q.ldr;
@@ -1686,6 +1696,8 @@ int ozk2_set_tile_n(int tile_n) {
 }
 
 int ozk2_batch_plan_tile_n(ozk2_batch_plan plan) { return plan ? plan->tile_n : -1; }
+
+int64_t ozk2_set_square_split(int64_t kmax) { return kmax < 0 ? g_split_kmax.load() : g_split_kmax.exchange(kmax); }
 
 int ozk2_debug_inject_fault(int kind) {
   std::lock_guard<std::mutex> lk(g_fault_mutex);

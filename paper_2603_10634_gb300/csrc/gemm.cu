@@ -103,6 +103,7 @@ struct GemmParams {
   const int32_t* rowshift;
   unsigned long long wait_ns;  // limit of every device wait (the drains of an abort use the default)
   int stall;                   // fault injection: the MMA thread's first wait never completes
+  int split_squares;           // single problems: square moduli in two single-slot passes
 };
 
 __device__ __forceinline__ void decode_unit(int tiles_m, int tiles_n, int tiles, int u, int& mod, int& tm,
@@ -130,6 +131,7 @@ struct UnitCtx {
   float factor;
   float* R;
   float* S;
+  bool split;  // square moduli in two single-slot passes
 };
 
 template <bool GROUPED>
@@ -149,6 +151,7 @@ __device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensor
     c.factor = P.factor;
     c.R = P.R;
     c.S = P.S;
+    c.split = P.split_squares != 0;
   } else {
     int lo = 0, hi = nprobs - 1;
     while (lo < hi) {
@@ -170,6 +173,7 @@ __device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensor
     c.factor = G.factor;
     c.R = G.R;
     c.S = G.S;
+    c.split = G.split != 0;
   }
 }
 
@@ -186,13 +190,17 @@ struct UnitPlan {
   int npasses;    // passes per block
 };
 
+// split: a square modulus runs as two single-slot passes, X = A1 B2 + A2 B1 (its residue
+// parked) and then Z = A2 B2, instead of one pass over both slots; chosen for short
+// reductions, where the drain of both slots after a pair pass would leave the tensor
+// cores idle.
 template <int MODE>
-__device__ __forceinline__ UnitPlan plan_of(int k, int mod) {
+__device__ __forceinline__ UnitPlan plan_of(int k, int mod, bool split) {
   UnitPlan u;
   if (MODE == kModeResidue) {
     const bool square = mod < kNumSquares;
     u.chunk_len = square ? kChunkSquare : kChunkKaratsuba;
-    u.npasses = square ? 1 : 3;
+    u.npasses = square ? (split ? 2 : 1) : 3;
   } else {
     u.chunk_len = ((k + BK - 1) / BK) * BK;
     u.npasses = 1;
@@ -201,29 +209,32 @@ __device__ __forceinline__ UnitPlan plan_of(int k, int mod) {
   return u;
 }
 
-// A pass uses both slots (a square modulus) or one.
+// A pass uses both slots (a square modulus in one pass) or one.
 template <int MODE>
-__device__ __forceinline__ bool pair_pass(int mod) {
-  return MODE == kModeResidue && mod < kNumSquares;
+__device__ __forceinline__ bool pair_pass(int mod, bool split) {
+  return MODE == kModeResidue && mod < kNumSquares && !split;
 }
 
 // Products of one pass per k-step, the digit planes (pa, pb) of product x and the
 // accumulator (0: the pass's first slot, 1: slot 1 of a pair pass) it adds to.
 template <int MODE>
-__device__ __forceinline__ int num_products(int mod) {
-  return pair_pass<MODE>(mod) ? 3 : 1;
+__device__ __forceinline__ int num_products(int mod, int pass, bool split) {
+  if (pair_pass<MODE>(mod, split)) return 3;
+  if (MODE == kModeResidue && mod < kNumSquares) return pass == 0 ? 2 : 1;  // split square: X, then Z
+  return 1;
 }
 
 template <int MODE>
-__device__ __forceinline__ void product_of(int mod, int pass, int x, int& pa, int& pb, int& acc) {
+__device__ __forceinline__ void product_of(int mod, int pass, int x, bool split, int& pa, int& pb, int& acc) {
   if (MODE != kModeResidue) {
     pa = pb = 0;
     acc = 0;
   } else if (mod < kNumSquares) {
     const int a0 = 2 * mod;  // (A1, B2) -> X, (A2, B1) -> X, (A2, B2) -> Z
-    pa = (x == 0) ? a0 : a0 + 1;
-    pb = (x == 1) ? a0 : a0 + 1;
-    acc = (x == 2) ? 1 : 0;
+    const int xs = split ? (pass == 0 ? x : 2) : x;
+    pa = (xs == 0) ? a0 : a0 + 1;
+    pb = (xs == 1) ? a0 : a0 + 1;
+    acc = (!split && xs == 2) ? 1 : 0;
   } else {
     pa = pb = 2 * kNumSquares + 3 * (mod - kNumSquares) + pass;  // (Ax, Bx) -> Dx
     acc = 0;
@@ -390,12 +401,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           last_prob = uc.prob;
         }
         const int mod = uc.mod;
-        const UnitPlan up = plan_of<MODE>(uc.k, mod);
+        const UnitPlan up = plan_of<MODE>(uc.k, mod, uc.split);
         for (int c = 0; ok && c < up.nchunks; ++c) {
           const int k0 = c * up.chunk_len;
           const int ksteps = (min(uc.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
           for (int ps = 0; ok && ps < up.npasses; ++ps) {
-            const int np = num_products<MODE>(mod);
+            const int np = num_products<MODE>(mod, ps, uc.split);
             for (int s = 0; ok && s < ksteps; ++s) {
               for (int x = 0; x < np; ++x) {
                 if (!mbar_wait_bounded(empty + stage, phase ^ 1u, abort_flag, wait_ns)) {
@@ -403,7 +414,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   break;
                 }
                 int pa, pb, acc;
-                product_of<MODE>(mod, ps, x, pa, pb, acc);
+                product_of<MODE>(mod, ps, x, uc.split, pa, pb, acc);
                 uint8_t* dst = tiles + stage * kStageBytes;
                 mbar_arrive_expect_tx(full + stage, kStageBytes);
                 tma_load_3d(dst, uc.ta, full + stage, k0 + s * BK, uc.tm * BM, pa);
@@ -441,12 +452,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         UnitCtx uc;
         resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
         const int mod = uc.mod;
-        const UnitPlan up = plan_of<MODE>(uc.k, mod);
+        const UnitPlan up = plan_of<MODE>(uc.k, mod, uc.split);
         for (int c = 0; ok && c < up.nchunks; ++c) {
           const int k0 = c * up.chunk_len;
           const int ksteps = (min(uc.k, k0 + up.chunk_len) - k0 + BK - 1) / BK;
           for (int ps = 0; ok && ps < up.npasses; ++ps) {
-            const bool pair = pair_pass<MODE>(mod);
+            const bool pair = pair_pass<MODE>(mod, uc.split);
             const uint32_t first_slot = pair ? 0u : sl.next;
             for (uint32_t j = 0; j < 2 && ok; ++j) {
               if (!pair && j != first_slot) continue;
@@ -454,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (!ok) break;
             tc_fence_after();
-            const int np = num_products<MODE>(mod);
+            const int np = num_products<MODE>(mod, ps, uc.split);
             for (int s = 0; ok && s < ksteps; ++s) {
               for (int x = 0; x < np; ++x) {
                 if (!mbar_wait_bounded(full + stage, phase, abort_flag, wait_ns)) {
@@ -463,8 +474,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 int pa, pb, acc;
-                product_of<MODE>(mod, ps, x, pa, pb, acc);
-                const bool first = (x == 0 || x == 2) && s == 0;  // first product into its slot
+                product_of<MODE>(mod, ps, x, uc.split, pa, pb, acc);
+                const bool first = s == 0 && (pair ? (x == 0 || x == 2) : x == 0);  // first into its slot
                 const uint32_t dtm = tmem_base + (first_slot + static_cast<uint32_t>(acc)) * static_cast<uint32_t>(BN);
                 const uint32_t sa = smem_addr(tiles + stage * kStageBytes);
                 const uint64_t adesc = sw128_kmajor_desc(sa);
@@ -517,11 +528,11 @@ __global__ void __launch_bounds__(kThreads, 1)
       UnitCtx uc;
       resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
       const int mod = uc.mod, tn = uc.tn;
-      const UnitPlan up = plan_of<MODE>(uc.k, mod);
+      const UnitPlan up = plan_of<MODE>(uc.k, mod, uc.split);
       const int gi = uc.tm * BM + row;
       for (int c = 0; ok && c < up.nchunks; ++c) {
         for (int ps = 0; ok && ps < up.npasses; ++ps) {
-          const bool pair = pair_pass<MODE>(mod);
+          const bool pair = pair_pass<MODE>(mod, uc.split);
           const uint32_t slot = pair ? 0u : sl.next;
           for (uint32_t j = 0; j < 2 && ok; ++j) {
             if (!pair && j != slot) continue;
@@ -564,6 +575,37 @@ __global__ void __launch_bounds__(kThreads, 1)
               auto lo16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x & 0xFFFFu)); };
               auto hi16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x >> 16)); };
               auto pack = [](int a, int b) { return (static_cast<uint32_t>(a) & 0xFFFFu) | (static_cast<uint32_t>(b) << 16); };
+              if (mod < kNumSquares) {  // square modulus in two passes
+                const float sqf = static_cast<float>(sq);
+                if (ps == 0) {  // park x = X mod p (the exact float of mod_near_f32, |x| < 0.51 p)
+#pragma unroll
+                  for (int w = 0; w < 4; ++w) {
+                    uint32_t pk[4];
+#pragma unroll
+                    for (int z = 0; z < 4; ++z)
+                      pk[z] = pack(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)),
+                                   __float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)));
+                    sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                  }
+                  continue;
+                }
+                int res[32];  // C' = mod(s x + Z, p), as the one-pass form computes it
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                  const uint4 pv = sp[w];
+                  const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+                  for (int z = 0; z < 4; ++z) {
+                    const int j = 8 * w + 2 * z;
+                    const float y0 = __fmaf_rn(sqf, static_cast<float>(lo16(pr[z])), __uint_as_float(v[j]));
+                    const float y1 = __fmaf_rn(sqf, static_cast<float>(hi16(pr[z])), __uint_as_float(v[j + 1]));
+                    res[j] = sym_fix(__float2int_rn(mod_near_f32(y0, pf, ip)), p, h);
+                    res[j + 1] = sym_fix(__float2int_rn(mod_near_f32(y1, pf, ip)), p, h);
+                  }
+                }
+                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
+                continue;
+              }
               if (ps == 0) {  // Karatsuba pass 1: park d1 = mod(D1, p)
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
@@ -749,6 +791,7 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.rowshift = g.rowshift;
   prm.wait_ns = g.wait_ns;
   prm.stall = g.stall ? 1 : 0;
+  prm.split_squares = g.split_squares ? 1 : 0;
 
   CUtensorMap ta, tb;
   if (!encode_fp8_map(&ta, a, g.k, g.m, planes_a, lda8, g.plane_stride_a, BM, BK)) return cudaErrorInvalidValue;

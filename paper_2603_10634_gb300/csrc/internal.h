@@ -157,6 +157,7 @@ struct GemmArgs {
   unsigned long long wait_ns;  // limit of each device wait (wait_limit_ns())
   bool stall;                  // fault injection: the kernel's first MMA wait never completes
   int tile_n;                  // output tile width: 128, or 256 (any other value)
+  bool split_squares;          // residue products: square moduli in two single-slot passes
 };
 // A operand: `planes_a` digit planes (K-major, m x k bytes, row stride lda8 bytes, plane
 // stride plane_stride_a); B operand the same with n rows.
@@ -249,6 +250,7 @@ struct GemmProblem {  // CUtensorMap carries the 64-byte alignment TMA needs
   float factor;
   float* R;
   float* S;
+  int split;  // residue products: square moduli in two single-slot passes
 };
 // Units of one problem in a GEMM of mode `mode` with N moduli and tiles of width tile_n.
 int64_t fp8_gemm_units(int mode, int m, int n, int N, int tile_n);

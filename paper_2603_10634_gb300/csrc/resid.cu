@@ -469,6 +469,7 @@ struct GradArgs {
   bool do_g, do_h;  // which of the two outputs to write
 };
 
+template <int NM>
 __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const __grid_constant__ ModTable mt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* tile = reinterpret_cast<double*>(smem_raw);
@@ -515,8 +516,8 @@ __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const
         any_tp |= tp[u];
       }
       uint8_t* colp = a.planesH + static_cast<int64_t>(j < a.n ? j : 0) * a.ldh + (ib < a.m ? ib : 0);
-      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<0, true>(ah, mt, pow2_s, cc, tp, colp, active);
-      else cols_planes<0, false>(ah, mt, pow2_s, cc, tp, colp, active);
+      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(ah, mt, pow2_s, cc, tp, colp, active);
+      else cols_planes<NM, false>(ah, mt, pow2_s, cc, tp, colp, active);
     }
     // row pass: G' (lines i, positions j); warp w, round s: rows 4 (8 s + w) + lane / 8
 #pragma unroll 1
@@ -536,8 +537,8 @@ __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const
         any_tp |= tp[u];
       }
       uint8_t* rowp = a.planesG + static_cast<int64_t>(i < a.m ? i : 0) * a.ldg + (jb < a.n ? jb : 0);
-      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<0, true>(ag, mt, pow2_s, cc, tp, rowp, active);
-      else cols_planes<0, false>(ag, mt, pow2_s, cc, tp, rowp, active);
+      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(ag, mt, pow2_s, cc, tp, rowp, active);
+      else cols_planes<NM, false>(ag, mt, pow2_s, cc, tp, rowp, active);
     }
     __syncthreads();  // the tile is reloaded
   }
@@ -629,6 +630,24 @@ void launch_unrolled(const ModTable& mt, int grid, cudaStream_t st, const ResidA
   }
 }
 
+// The gradient kernel with the modulus loop unrolled for N in [kUnrollLo, kUnrollHi].
+template <int NM = kUnrollLo>
+void launch_grad_unrolled(const ModTable& mt, int grid, cudaStream_t st, const GradArgs& a) {
+  if constexpr (NM > kUnrollHi) {
+    static bool done[64] = {};
+    allow_cols_smem(grad_residues_kernel<0>, done);
+    grad_residues_kernel<0><<<grid, 256, kColsSmem, st>>>(a, mt);
+  } else {
+    if (mt.N == NM) {
+      static bool done[64] = {};
+      allow_cols_smem(grad_residues_kernel<NM>, done);
+      grad_residues_kernel<NM><<<grid, 256, kColsSmem, st>>>(a, mt);
+    } else {
+      launch_grad_unrolled<NM + 1>(mt, grid, st, a);
+    }
+  }
+}
+
 int grid_for(int64_t warps) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -678,14 +697,12 @@ cudaError_t launch_grad_residues(const double* dC, int64_t lddc, int m, int n, c
                                  const int32_t* h, const int32_t* e, uint8_t* planesG, int64_t ldg, uint8_t* planesH,
                                  int64_t ldh, const ModTable& mt, uint32_t* flags, cudaStream_t st) {
   GradArgs a{dC, lddc, m, n, g, f, h, e, planesG, ldg, planesH, ldh, flags, planesG != nullptr, planesH != nullptr};
-  static bool done[64] = {};
-  allow_cols_smem(grad_residues_kernel, done);
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = static_cast<int64_t>((n + kTileCols - 1) / kTileCols) * ((m + kTileK - 1) / kTileK);
   const int grid = static_cast<int>(std::min<int64_t>(tiles, 3 * static_cast<int64_t>(sms)));
-  grad_residues_kernel<<<grid, 256, kColsSmem, st>>>(a, mt);
+  launch_grad_unrolled(mt, grid, st, a);
   return cudaGetLastError();
 }
 

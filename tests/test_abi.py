@@ -233,3 +233,11 @@ def test_tile_setting(lib):
     assert lib.ozk2_set_tile_n(256) == 128
     assert lib.ozk2_set_tile_n(0) == 256
     assert lib.ozk2_batch_plan_tile_n(None) == -1
+
+
+def test_square_split_setting(lib):
+    prev = lib.ozk2_set_square_split(-1)
+    assert prev == 4096
+    assert lib.ozk2_set_square_split(0) == 4096
+    assert lib.ozk2_set_square_split(8192) == 0
+    assert lib.ozk2_set_square_split(prev) == 8192

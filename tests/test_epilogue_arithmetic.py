@@ -76,8 +76,10 @@ def test_fp32_reduction_sums_stay_exact():
     for p in oz.hybrid_moduli(20):
         kind, s = oz.modulus_kind(p)
         if kind == "square":
-            # s (X mod p) + Z with |Z| <= 2^15 * 16 * 16 = 2^23
+            # s (X mod p) + Z with |Z| <= 2^15 * 16 * 16 = 2^23; in the two-pass form
+            # X mod p is parked as int16 between the passes
             assert s * bound * p + 2**23 < 2**24, p
+            assert bound * p < 2**15, p
         else:
             # 240 d1 - 15 (D2 mod p) with |d1| <= p/2, and v + 16 (D3 mod p) with |v| <= p/2
             assert 240 * (p // 2) + 15 * bound * p < 2**24, p

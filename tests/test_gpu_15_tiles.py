@@ -37,7 +37,7 @@ def test_narrow_tile_residue_products_bit_exact(cuda, m, n, k, N):
 
 
 def test_narrow_tile_raw_product_exact(cuda):
-    m, n, k = 300, 200, 1000
+    m, n, k = 300, 200, 1024  # row strides of the raw hook are multiples of 16 bytes
     g = torch.Generator().manual_seed(3)
     a = torch.randint(-16, 17, (m, k), generator=g).to(torch.float32)
     b = torch.randint(-16, 17, (n, k), generator=g).to(torch.float32)
@@ -76,3 +76,33 @@ def test_tuner_choices(cuda):
     As, Bs = workloads.batch_problems(shapes, 1.0, seed=6, device=cuda)
     N, tile, rep = ozk.choose_plan(As, Bs, "fp64", probes=2, reps=2)
     assert 8 <= N <= 20 and tile in (128, 256) and set(rep["plan_ms"]) == {128, 256}
+
+
+@pytest.mark.parametrize("m,n,k,N,kmax", [(200, 300, 500, 12, 4096), (130, 260, 33000, 13, 1 << 20),
+                                          (300, 128, 129, 6, 4096), (64, 70, 2048, 16, 4096)])
+def test_split_square_passes_bit_exact(cuda, m, n, k, N, kmax):
+    """Square moduli as two single-slot passes (X parked, then Z) give the residues of the
+    one-pass form, also across exactness blocks (k > 2^15 with the split forced on)."""
+    lib = _lib.load()
+    A, B = workloads.problem(m, n, k, 1.0, seed=k + 7)
+    Ad, Bd = A.to(cuda), B.to(cuda)
+    sc = ozk.scales(Ad, Bd, num_moduli=N)
+    prev = lib.ozk2_set_square_split(kmax)
+    try:
+        split = ozk.residue_products(Ad, Bd, sc["e"], sc["f"], num_moduli=N)
+        C_split = ozk.dgemm(Ad, Bd, num_moduli=N)
+        lib.ozk2_set_square_split(0)
+        whole = ozk.residue_products(Ad, Bd, sc["e"], sc["f"], num_moduli=N)
+        C_whole = ozk.dgemm(Ad, Bd, num_moduli=N)
+    finally:
+        lib.ozk2_set_square_split(prev)
+    assert torch.equal(split, whole)
+    assert torch.equal(C_split, C_whole)
+    res = split.cpu().numpy()
+    e, f = sc["e"].cpu().numpy().astype(np.int64), sc["f"].cpu().numpy().astype(np.int64)
+    da = oz.scaled_decomposition(A.numpy(), e)
+    db = oz.scaled_decomposition(B.numpy().T, f)
+    for l, p in enumerate(oz.hybrid_moduli(N)[:6]):
+        pa = oz.digit_split(oz.residues_of_decomposition(*da, p), p)
+        pb = [x.T for x in oz.digit_split(oz.residues_of_decomposition(*db, p), p)]
+        assert np.array_equal(res[l].astype(np.int64), np.asarray(oz.residue_product(pa, pb, p), dtype=np.int64)), p
