@@ -350,8 +350,9 @@ int ozk2_batch_plan_tile_n(ozk2_batch_plan plan);
  * pass over both tensor-memory accumulators, or, for reductions of at most kmax terms, as
  * two single-slot passes (X, whose residue is kept, then Z), which lets the epilogue of
  * one pass overlap the next when k is short.  Applies to calls and batch plans made
- * after it; results are bit-identical either way.  Default 4096; 0 never splits; a
- * negative kmax only queries.  Returns the previous (or current) setting.
+ * after it; results are bit-identical either way.  Default 0 (never split: measured
+ * neutral or slower on this GPU); a negative kmax only queries.  Returns the previous (or
+ * current) setting.
  */
 int64_t ozk2_set_square_split(int64_t kmax);
 

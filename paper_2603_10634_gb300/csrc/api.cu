@@ -111,10 +111,11 @@ int64_t padded(int64_t n, int64_t t) { return ((n + t - 1) / t) * t; }
 int tile_rule(int64_t padded256, int64_t padded128) { return 4 * padded256 >= 5 * padded128 ? 128 : 256; }
 
 // Square moduli run as two single-slot passes (X, then Z) when the reduction is at most
-// this long: with short reductions the drain of both accumulator slots after a one-pass
-// square modulus leaves the tensor cores idle; with long ones the second pass rereads A2
-// and B2 from DRAM.  ozk2_set_square_split sets it.
-std::atomic<int64_t> g_split_kmax{4096};
+// this long (ozk2_set_square_split).  Off by default: measured on the 512-product batch,
+// the 65536 x 1024 x 1024 product and square sizes 1024-8192, the split was neutral or
+// slower (the drain of both slots after a one-pass square modulus is not what limits
+// short reductions).
+std::atomic<int64_t> g_split_kmax{0};
 
 int tile_for(int64_t n) {
   const int t = g_tile_n.load();

@@ -237,7 +237,7 @@ def test_tile_setting(lib):
 
 def test_square_split_setting(lib):
     prev = lib.ozk2_set_square_split(-1)
-    assert prev == 4096
-    assert lib.ozk2_set_square_split(0) == 4096
-    assert lib.ozk2_set_square_split(8192) == 0
+    assert prev == 0
+    assert lib.ozk2_set_square_split(4096) == 0
+    assert lib.ozk2_set_square_split(8192) == 4096
     assert lib.ozk2_set_square_split(prev) == 8192
