@@ -585,7 +585,14 @@ def run_autograd(a, rank, world):
 
     step = make_step(True)
     step()
-    launches = ozk.last_launch_count() + 9  # the backward call, plus the forward's 9
+    # launches per step: the forward call and the backward call, counted on this thread
+    # (autograd runs the backward on its own thread, whose count this thread cannot read)
+    ws = torch.empty(ozk.workspace_size(m, n, k, N), dtype=torch.uint8, device=dev)
+    ozk.dgemm(A.detach(), B.detach(), num_moduli=N, workspace=ws)
+    fwd_launches = ozk.last_launch_count()
+    ozk.dgemm_backward(A.detach(), B.detach(), W, ws, N)
+    launches = fwd_launches + ozk.last_launch_count()
+    del ws
     with ClockSampler(local) as clk:
         ms = timed(step)
     err_reuse = grad_errors() if rank == 0 else None

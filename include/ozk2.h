@@ -291,7 +291,9 @@ const char *ozk2_status_string(ozk2_status status);
 /*
  * ozk2_device_status - synchronises `stream`, then reads and clears the device flag
  * word of the given workspace (NULL: the library-owned workspace of the current
- * device).  Returns OZK2_OK, OZK2_ERR_TIMEOUT, OZK2_ERR_RANGE or OZK2_ERR_NONFINITE
+ * device).  Returns OZK2_OK, OZK2_ERR_INTERNAL (only in a library built with
+ * -DOZK2_DEBUG: a kernel's range check failed, e.g. a digit beyond |d| <= 16 or a residue
+ * outside its symmetric range), OZK2_ERR_TIMEOUT, OZK2_ERR_RANGE or OZK2_ERR_NONFINITE
  * (most severe first), or OZK2_ERR_CUDA if the synchronisation fails.
  */
 ozk2_status ozk2_device_status(void *workspace, ozk2_stream_t stream);

@@ -20,6 +20,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libozk2.so")
+# the debug build (range checks in the kernels, -DOZK2_DEBUG) lives beside it
+BUILD_DEBUG = os.path.join(PKG, "_build_debug")
+LIB_DEBUG = os.path.join(PKG, "libozk2_debug.so")
 SOURCES = ["api.cu", "scale.cu", "resid.cu", "gemm.cu", "crt.cu", "noalloc.cu", "moduli.cpp"]
 HEADERS = ["internal.h", "device.cuh"]
 
@@ -45,13 +48,13 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src, verbose):
-    obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
+def _compile(src, verbose, debug=False):
+    obj = os.path.join(BUILD_DEBUG if debug else BUILD, os.path.splitext(src)[0] + ".o")
     deps = [os.path.join(CSRC, src)] + [os.path.join(CSRC, h) for h in HEADERS] + [
         os.path.join(ROOT, "include", "ozk2.h")]
     if not _stale(obj, deps):
         return obj, ""
-    cmd = [nvcc()] + ARCH + COMMON + ["-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc()] + ARCH + COMMON + (["-DOZK2_DEBUG"] if debug else []) + ["-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu") and verbose:
         cmd += ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -60,32 +63,35 @@ def _compile(src, verbose):
     return obj, r.stderr
 
 
-def build(force=False, verbose=False):
-    """Compile every CUDA / C++ source and link libozk2.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, debug=False):
+    """Compile every CUDA / C++ source and link libozk2.so (debug: libozk2_debug.so, with
+    the kernels' range checks); returns the library path."""
+    bdir, lib = (BUILD_DEBUG, LIB_DEBUG) if debug else (BUILD, LIB)
+    os.makedirs(bdir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
-            os.remove(os.path.join(BUILD, f))
+        for f in os.listdir(bdir):
+            os.remove(os.path.join(bdir, f))
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(lambda s: _compile(s, verbose), SOURCES))
+        results = list(ex.map(lambda s: _compile(s, verbose, debug), SOURCES))
     objs = [o for o, _ in results]
     if verbose:
         for _, log in results:
             if log:
                 sys.stderr.write(log)
-    if force or _stale(LIB, objs):
-        tmp = LIB + ".tmp"
+    if force or _stale(lib, objs):
+        tmp = lib + ".tmp"
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-ldl", "-lpthread", "-lrt"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--force", action="store_true")
     ap.add_argument("-v", "--verbose", action="store_true")
+    ap.add_argument("--debug", action="store_true", help="libozk2_debug.so with the kernels' range checks")
     a = ap.parse_args()
-    print(build(force=a.force, verbose=a.verbose))
+    print(build(force=a.force, verbose=a.verbose, debug=a.debug))

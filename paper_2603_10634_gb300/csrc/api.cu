@@ -1603,6 +1603,7 @@ ozk2_status ozk2_device_status(void* workspace, ozk2_stream_t stream) {
   uint32_t flags = 0;
   if (cudaMemcpy(&flags, ws, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return OZK2_ERR_CUDA;
   if (cudaMemset(ws, 0, 4) != cudaSuccess) return OZK2_ERR_CUDA;
+  if (flags & kFlagDebug) return OZK2_ERR_INTERNAL;
   if (flags & kFlagTimeout) return OZK2_ERR_TIMEOUT;
   if (flags & kFlagRange) return OZK2_ERR_RANGE;
   if (flags & kFlagNonfinite) return OZK2_ERR_NONFINITE;

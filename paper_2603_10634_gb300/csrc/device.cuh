@@ -10,6 +10,20 @@
 
 namespace ozk2 {
 
+// Range checks of the debug build (compiled with -DOZK2_DEBUG): a failed check sets
+// kFlagDebug in the call's flag word (ozk2_device_status reports OZK2_ERR_INTERNAL); it
+// never traps, so the kernel runs to its end either way.
+#ifdef OZK2_DEBUG
+#define OZK2_DCHECK(cond, flags)                    \
+  do {                                              \
+    if (!(cond)) atomicOr((flags), ozk2::kFlagDebug); \
+  } while (0)
+#else
+#define OZK2_DCHECK(cond, flags) \
+  do {                           \
+  } while (0)
+#endif
+
 // Default limit of a device wait in nanoseconds (the host may set another per launch);
 // a wait that reaches its limit makes the kernel record kFlagTimeout and return instead
 // of hanging.  The waits of an aborting kernel for its own copies and products in

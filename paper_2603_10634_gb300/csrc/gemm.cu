@@ -295,9 +295,18 @@ __device__ __forceinline__ int kara_c(int v, uint32_t d3_bits, float pf, float i
 }
 
 // Store 32 int16 residues of one row (adding the previous block's residues when
-// `accumulate`), vectorised when the 32 columns are all inside the matrix.
+// `accumulate`), vectorised when the 32 columns are all inside the matrix.  The debug
+// build checks that every residue lies in the symmetric range [-h, p - 1 - h].
 __device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int (&res)[32], bool accumulate,
-                                               int p, int h) {
+                                               int p, int h, uint32_t* flags) {
+#ifdef OZK2_DEBUG
+  bool in_range = true;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) in_range = in_range && res[j] >= -h && res[j] <= p - 1 - h;
+  OZK2_DCHECK(in_range, flags);
+#else
+  (void)flags;
+#endif
   if (gc + 32 <= n) {
     uint4* o = reinterpret_cast<uint4*>(dst + gc);
 #pragma unroll
@@ -519,9 +528,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int chalf = (warp - 2) >> 2;      // column half of the tile
     const int row = q * 32 + lane;
     const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
-    // the CTA's parking tile: BM x BN int16 (the first half of its scratch words)
-    int16_t* scr = reinterpret_cast<int16_t*>(prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BNMAX)) +
-                   row * BN + chalf * (BN / 2);
+    // Residues kept between the passes of a unit (Karatsuba d1, then v; the X residue of
+    // a two-pass square modulus): every pass of a unit gives this thread the same row and
+    // the same BN / 2 columns, so they stay in registers, 32 int16 per chunk of 32
+    // columns, two per word.
+    uint32_t park[BN / 64][16];
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
     for (int u = u_first; ok && u < prm.num_units; u += u_step) {
@@ -548,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float pf = static_cast<float>(p);
             const bool last = ps == up.npasses - 1;
             int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
-#pragma unroll 1
+#pragma unroll
             for (int cb = 0; cb < BN / 64; ++cb) {
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
               if (pair) {  // square modulus: X in slot 0, Z in slot 1
@@ -565,13 +576,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                   const float y = __fmaf_rn(sqf, mod_near_f32(__uint_as_float(vx[j]), pf, ip), __uint_as_float(vz[j]));
                   res[j] = sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
                 }
-                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
+                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
                 continue;
               }
               uint32_t v[32];
               tmem_ld_32cols(ts + cb * 32, v);
               tmem_ld_wait();
-              uint4* sp = reinterpret_cast<uint4*>(scr + cb * 32);  // 32 int16 = 4 x 16 bytes
+              uint32_t* sp = park[cb];  // this thread's 32 parked int16 of chunk cb, two per word
               auto lo16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x & 0xFFFFu)); };
               auto hi16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x >> 16)); };
               auto pack = [](int a, int b) { return (static_cast<uint32_t>(a) & 0xFFFFu) | (static_cast<uint32_t>(b) << 16); };
@@ -585,15 +596,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int z = 0; z < 4; ++z)
                       pk[z] = pack(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)),
                                    __float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)));
-                    sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+#pragma unroll
+                    for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
                   }
                   continue;
                 }
                 int res[32];  // C' = mod(s x + Z, p), as the one-pass form computes it
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                  const uint4 pv = sp[w];
-                  const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+                  const uint32_t pr[4] = {sp[4 * w], sp[4 * w + 1], sp[4 * w + 2], sp[4 * w + 3]};
 #pragma unroll
                   for (int z = 0; z < 4; ++z) {
                     const int j = 8 * w + 2 * z;
@@ -603,7 +614,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     res[j + 1] = sym_fix(__float2int_rn(mod_near_f32(y1, pf, ip)), p, h);
                   }
                 }
-                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
+                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
                 continue;
               }
               if (ps == 0) {  // Karatsuba pass 1: park d1 = mod(D1, p)
@@ -614,29 +625,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                   for (int z = 0; z < 4; ++z)
                     pk[z] = pack(sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)), p, h),
                                  sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)), p, h));
-                  sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+#pragma unroll
+                  for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
                 }
                 continue;
               }
               if (!last) {  // Karatsuba pass 2: park v = mod(240 d1 - 15 D2, p)
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                  const uint4 pv = sp[w];
-                  const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+                  const uint32_t pr[4] = {sp[4 * w], sp[4 * w + 1], sp[4 * w + 2], sp[4 * w + 3]};
                   uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z)
                     pk[z] = pack(kara_v(lo16(pr[z]), v[8 * w + 2 * z], pf, ip, p, h),
                                  kara_v(hi16(pr[z]), v[8 * w + 2 * z + 1], pf, ip, p, h));
-                  sp[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+#pragma unroll
+                  for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
                 }
                 continue;
               }
               int res[32];  // Karatsuba pass 3: C' = mod(v + 16 D3, p)
 #pragma unroll
               for (int w = 0; w < 4; ++w) {
-                const uint4 pv = sp[w];
-                const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
+                const uint32_t pr[4] = {sp[4 * w], sp[4 * w + 1], sp[4 * w + 2], sp[4 * w + 3]};
 #pragma unroll
                 for (int z = 0; z < 4; ++z) {
                   const int j = 8 * w + 2 * z;
@@ -644,7 +655,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   res[j + 1] = kara_c(hi16(pr[z]), v[j + 1], pf, ip, p, h);
                 }
               }
-              if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h);
+              if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
             }
           } else if constexpr (MODE == kModeBound) {
             float rmax = 0.0f;

@@ -20,6 +20,7 @@ constexpr int kNumSquares = 6;  // squares lead the hybrid list (Sec. III-D)
 constexpr uint32_t kFlagTimeout = 1u;    // a bounded device wait gave up
 constexpr uint32_t kFlagRange = 2u;      // a scaled value exceeded the supported range
 constexpr uint32_t kFlagNonfinite = 4u;  // NaN / Inf input seen
+constexpr uint32_t kFlagDebug = 8u;      // a range check of the debug build (OZK2_DEBUG) failed
 
 // Line status bits (one byte per row of A / column of B)
 constexpr uint8_t kLineZero = 1;       // no nonzero finite entry

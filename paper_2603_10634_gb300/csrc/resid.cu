@@ -248,6 +248,10 @@ __device__ __forceinline__ void rows_planes(const ResidArgs& a, const ModTable& 
 #pragma unroll
     for (int xp = 0; xp < 3; ++xp) {
       if (xp < nplanes) {
+        // every digit |d| <= 16: E4M3 magnitude code at most 0x58 (= 16)
+        OZK2_DCHECK(__vcmpgtu4(words[xp][0] & 0x7F7F7F7Fu, 0x58585858u) == 0u &&
+                        __vcmpgtu4(words[xp][1] & 0x7F7F7F7Fu, 0x58585858u) == 0u,
+                    a.flags);
         if (store0) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride) = words[xp][0];
         if (store1) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride + 128) = words[xp][1];
       }
@@ -270,7 +274,12 @@ __device__ __forceinline__ void cols_planes(const ResidArgs& a, const ModTable& 
     if (active) {
 #pragma unroll
       for (int xp = 0; xp < 3; ++xp)
-        if (xp < nplanes) *reinterpret_cast<uint2*>(pl + xp * a.plane_stride) = make_uint2(words[xp][0], words[xp][1]);
+        if (xp < nplanes) {
+          OZK2_DCHECK(__vcmpgtu4(words[xp][0] & 0x7F7F7F7Fu, 0x58585858u) == 0u &&
+                          __vcmpgtu4(words[xp][1] & 0x7F7F7F7Fu, 0x58585858u) == 0u,
+                      a.flags);
+          *reinterpret_cast<uint2*>(pl + xp * a.plane_stride) = make_uint2(words[xp][0], words[xp][1]);
+        }
     }
   }
 }
@@ -546,45 +555,68 @@ __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const
 }
 
 // dst[p][x][y] = src[p][y][x] for y < lines, x < len: the digit planes of an operand
-// (lines x len bytes, K-major) as the planes of its transpose, through 64 x 64 byte
-// tiles in shared memory (row pitch 68 bytes: the 16 bytes a thread gathers along y
-// fall in 16 different banks).
-constexpr int kTrTile = 64, kTrPitch = 68;
+// (lines x len bytes, K-major) as the planes of its transpose.  A block moves 128 x 128
+// byte tiles through shared memory (row pitch 33 words: the words a warp reads along a
+// column fall in 32 different banks); each thread then reads a 16 x 4 byte block (16
+// rows, 4 columns) as 16 words, transposes it four 4 x 4 blocks at a time with byte
+// permutes, and writes 4 destination rows of 16 bytes.
+constexpr int kTrTile = 128, kTrPitchW = 33;
+
+// 4 x 4 byte block: in[r] holds bytes (r, 0..3); out[c] gets bytes (0..3, c).
+__device__ __forceinline__ void transpose4x4(const uint32_t (&in)[4], uint32_t (&out)[4]) {
+  const uint32_t t0 = __byte_perm(in[0], in[1], 0x5140), t1 = __byte_perm(in[0], in[1], 0x7362);
+  const uint32_t t2 = __byte_perm(in[2], in[3], 0x5140), t3 = __byte_perm(in[2], in[3], 0x7362);
+  out[0] = __byte_perm(t0, t2, 0x5410);
+  out[1] = __byte_perm(t0, t2, 0x7632);
+  out[2] = __byte_perm(t1, t3, 0x5410);
+  out[3] = __byte_perm(t1, t3, 0x7632);
+}
 
 __global__ void __launch_bounds__(256) transpose_planes_kernel(const uint8_t* __restrict__ src, int64_t src_pitch,
                                                                int64_t src_stride, int lines, int len,
                                                                uint8_t* __restrict__ dst, int64_t dst_pitch,
                                                                int64_t dst_stride, int planes) {
-  __shared__ __align__(16) uint8_t tile[kTrTile * kTrPitch];
+  __shared__ uint32_t tile[kTrTile * kTrPitchW];
   const int tx = (len + kTrTile - 1) / kTrTile, ty = (lines + kTrTile - 1) / kTrTile;
   const int64_t total = static_cast<int64_t>(tx) * ty * planes;
-  const int t = threadIdx.x, r = t >> 2, c16 = (t & 3) * 16;
+  const int t = threadIdx.x;
   for (int64_t b = blockIdx.x; b < total; b += gridDim.x) {
     const int p = static_cast<int>(b / (static_cast<int64_t>(tx) * ty));
     const int rem = static_cast<int>(b - static_cast<int64_t>(p) * tx * ty);
     const int y0 = (rem / tx) * kTrTile, x0 = (rem % tx) * kTrTile;
-    // load: row y0 + r, bytes x0 + c16 .. + 15 (inside the source row's pitch)
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (y0 + r < lines && x0 + c16 < len)
-      v = *reinterpret_cast<const uint4*>(src + p * src_stride + static_cast<int64_t>(y0 + r) * src_pitch + x0 + c16);
-    uint32_t* tw = reinterpret_cast<uint32_t*>(tile + r * kTrPitch + c16);
-    tw[0] = v.x;
-    tw[1] = v.y;
-    tw[2] = v.z;
-    tw[3] = v.w;
+    // load: 128 rows of 128 bytes, 16 bytes per thread and round (inside the source pitch)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int r = q * 32 + (t >> 3), c16 = (t & 7) * 16;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (y0 + r < lines && x0 + c16 < len)
+        v = *reinterpret_cast<const uint4*>(src + p * src_stride + static_cast<int64_t>(y0 + r) * src_pitch + x0 +
+                                            c16);
+      uint32_t* tw = tile + r * kTrPitchW + c16 / 4;
+      tw[0] = v.x;
+      tw[1] = v.y;
+      tw[2] = v.z;
+      tw[3] = v.w;
+    }
     __syncthreads();
-    // store: destination row x0 + r, bytes y0 + c16 .. + 15
-    if (x0 + r < len && y0 + c16 < lines) {
-      uint32_t w[4];
+    // store: destination rows x0 + 4 cw .. + 3, bytes y0 + 16 yb .. + 15
+    const int cw = t & 31, yb = t >> 5;
+    uint32_t out[4][4];  // out[c][w]: destination row 4 cw + c, word w (4 y's)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        uint32_t word = 0;
+    for (int w = 0; w < 4; ++w) {
+      uint32_t in[4], o[4];
 #pragma unroll
-        for (int z = 0; z < 4; ++z) word |= static_cast<uint32_t>(tile[(c16 + 4 * q + z) * kTrPitch + r]) << (8 * z);
-        w[q] = word;
-      }
-      *reinterpret_cast<uint4*>(dst + p * dst_stride + static_cast<int64_t>(x0 + r) * dst_pitch + y0 + c16) =
-          make_uint4(w[0], w[1], w[2], w[3]);
+      for (int r = 0; r < 4; ++r) in[r] = tile[(16 * yb + 4 * w + r) * kTrPitchW + cw];
+      transpose4x4(in, o);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) out[c][w] = o[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int x = x0 + 4 * cw + c, y = y0 + 16 * yb;
+      if (x < len && y < lines)
+        *reinterpret_cast<uint4*>(dst + p * dst_stride + static_cast<int64_t>(x) * dst_pitch + y) =
+            make_uint4(out[c][0], out[c][1], out[c][2], out[c][3]);
     }
     __syncthreads();
   }
