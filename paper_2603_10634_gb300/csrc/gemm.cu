@@ -340,7 +340,8 @@ __device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int 
 }
 
 // GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).  TN: tile width.
-template <int MODE, bool GROUPED, int TN>
+// REGPARK: residues parked between passes in registers (see the epilogue).
+template <int MODE, bool GROUPED, int TN, bool REGPARK>
 __global__ void __launch_bounds__(kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ GemmParams prm, const GemmProblem* __restrict__ probs, int nprobs) {
@@ -529,10 +530,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int row = q * 32 + lane;
     const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
     // Residues kept between the passes of a unit (Karatsuba d1, then v; the X residue of
-    // a two-pass square modulus): every pass of a unit gives this thread the same row and
-    // the same BN / 2 columns, so they stay in registers, 32 int16 per chunk of 32
-    // columns, two per word.
-    uint32_t park[BN / 64][16];
+    // a two-pass square modulus), 32 int16 per chunk of 32 columns, two per word.  Every
+    // pass of a unit gives this thread the same row and the same BN / 2 columns, so with
+    // REGPARK they stay in registers (the chunk loop unrolled); otherwise they go to the
+    // CTA's scratch tile in L2 (BM x BN int16), which keeps the rolled epilogue small:
+    // the unrolled one is faster with long reductions (no parking traffic leaving L2)
+    // and slower with short ones.
+    uint32_t park[REGPARK ? BN / 64 : 1][16];
+    uint32_t* scr = reinterpret_cast<uint32_t*>(prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BNMAX)) +
+                    (row * BN + chalf * (BN / 2)) / 2;
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
     for (int u = u_first; ok && u < prm.num_units; u += u_step) {
@@ -559,8 +565,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float pf = static_cast<float>(p);
             const bool last = ps == up.npasses - 1;
             int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
+            // one chunk of 32 columns; sp: this thread's 32 parked int16 of the chunk (two
+            // per word), in registers (REGPARK) or in the CTA's scratch tile
+            // words 4w .. 4w + 3 of a chunk's parked values: registers, or one 16-byte
+            // access of the scratch tile (16-byte aligned: 64-byte rows of the tile)
+            auto store4 = [](uint32_t* sp, int w, const uint32_t (&pk)[4]) {
+              if constexpr (REGPARK) {
 #pragma unroll
-            for (int cb = 0; cb < BN / 64; ++cb) {
+                for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
+              } else {
+                reinterpret_cast<uint4*>(sp)[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+              }
+            };
+            auto load4 = [](const uint32_t* sp, int w, uint32_t (&pr)[4]) {
+              if constexpr (REGPARK) {
+#pragma unroll
+                for (int z = 0; z < 4; ++z) pr[z] = sp[4 * w + z];
+              } else {
+                const uint4 v4 = reinterpret_cast<const uint4*>(sp)[w];
+                pr[0] = v4.x;
+                pr[1] = v4.y;
+                pr[2] = v4.z;
+                pr[3] = v4.w;
+              }
+            };
+            auto chunk = [&](int cb, uint32_t* sp) {
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
               if (pair) {  // square modulus: X in slot 0, Z in slot 1
                 uint32_t vx[32], vz[32];
@@ -577,12 +606,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                   res[j] = sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
                 }
                 if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
-                continue;
+                return;
               }
               uint32_t v[32];
               tmem_ld_32cols(ts + cb * 32, v);
               tmem_ld_wait();
-              uint32_t* sp = park[cb];  // this thread's 32 parked int16 of chunk cb, two per word
               auto lo16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x & 0xFFFFu)); };
               auto hi16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x >> 16)); };
               auto pack = [](int a, int b) { return (static_cast<uint32_t>(a) & 0xFFFFu) | (static_cast<uint32_t>(b) << 16); };
@@ -596,15 +624,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int z = 0; z < 4; ++z)
                       pk[z] = pack(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)),
                                    __float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)));
-#pragma unroll
-                    for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
+                    store4(sp, w, pk);
                   }
-                  continue;
+                  return;
                 }
                 int res[32];  // C' = mod(s x + Z, p), as the one-pass form computes it
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                  const uint32_t pr[4] = {sp[4 * w], sp[4 * w + 1], sp[4 * w + 2], sp[4 * w + 3]};
+                  uint32_t pr[4];
+                  load4(sp, w, pr);
 #pragma unroll
                   for (int z = 0; z < 4; ++z) {
                     const int j = 8 * w + 2 * z;
@@ -615,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                   }
                 }
                 if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
-                continue;
+                return;
               }
               if (ps == 0) {  // Karatsuba pass 1: park d1 = mod(D1, p)
 #pragma unroll
@@ -625,29 +653,29 @@ __global__ void __launch_bounds__(kThreads, 1)
                   for (int z = 0; z < 4; ++z)
                     pk[z] = pack(sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)), p, h),
                                  sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)), p, h));
-#pragma unroll
-                  for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
+                  store4(sp, w, pk);
                 }
-                continue;
+                return;
               }
               if (!last) {  // Karatsuba pass 2: park v = mod(240 d1 - 15 D2, p)
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                  const uint32_t pr[4] = {sp[4 * w], sp[4 * w + 1], sp[4 * w + 2], sp[4 * w + 3]};
+                  uint32_t pr[4];
+                  load4(sp, w, pr);
                   uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z)
                     pk[z] = pack(kara_v(lo16(pr[z]), v[8 * w + 2 * z], pf, ip, p, h),
                                  kara_v(hi16(pr[z]), v[8 * w + 2 * z + 1], pf, ip, p, h));
-#pragma unroll
-                  for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
+                  store4(sp, w, pk);
                 }
-                continue;
+                return;
               }
               int res[32];  // Karatsuba pass 3: C' = mod(v + 16 D3, p)
 #pragma unroll
               for (int w = 0; w < 4; ++w) {
-                const uint32_t pr[4] = {sp[4 * w], sp[4 * w + 1], sp[4 * w + 2], sp[4 * w + 3]};
+                uint32_t pr[4];
+                load4(sp, w, pr);
 #pragma unroll
                 for (int z = 0; z < 4; ++z) {
                   const int j = 8 * w + 2 * z;
@@ -656,6 +684,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
               }
               if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
+            };
+            if constexpr (REGPARK) {
+#pragma unroll
+              for (int cb = 0; cb < BN / 64; ++cb) chunk(cb, park[cb]);
+            } else {
+#pragma unroll 1
+              for (int cb = 0; cb < BN / 64; ++cb) chunk(cb, scr + cb * 16);
             }
           } else if constexpr (MODE == kModeBound) {
             float rmax = 0.0f;
@@ -732,7 +767,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int MODE, bool GROUPED, int TN>
+template <int MODE, bool GROUPED, int TN, bool REGPARK>
 cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
                         const GemmProblem* probs, int nprobs, cudaStream_t st) {
   static bool configured[64] = {false};
@@ -740,21 +775,30 @@ cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUte
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED, TN>,
+    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED, TN, REGPARK>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     configured[dev] = true;
   }
-  fp8_gemm_kernel<MODE, GROUPED, TN><<<grid, kThreads, smem, st>>>(ta, tb, prm, probs, nprobs);
+  fp8_gemm_kernel<MODE, GROUPED, TN, REGPARK><<<grid, kThreads, smem, st>>>(ta, tb, prm, probs, nprobs);
   return cudaGetLastError();
 }
 
 template <int MODE, bool GROUPED>
-cudaError_t launch_tile(int tn, const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
-                        const GemmProblem* probs, int nprobs, cudaStream_t st) {
-  if (tn == 128) return launch_mode<MODE, GROUPED, 128>(prm, ta, tb, grid, probs, nprobs, st);
-  return launch_mode<MODE, GROUPED, 256>(prm, ta, tb, grid, probs, nprobs, st);
+cudaError_t launch_tile(int tn, bool regpark, const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb,
+                        int grid, const GemmProblem* probs, int nprobs, cudaStream_t st) {
+  if constexpr (MODE == kModeResidue && !GROUPED) {
+    if (regpark) {
+      if (tn == 128) return launch_mode<MODE, GROUPED, 128, true>(prm, ta, tb, grid, probs, nprobs, st);
+      return launch_mode<MODE, GROUPED, 256, true>(prm, ta, tb, grid, probs, nprobs, st);
+    }
+  }
+  if (tn == 128) return launch_mode<MODE, GROUPED, 128, false>(prm, ta, tb, grid, probs, nprobs, st);
+  return launch_mode<MODE, GROUPED, 256, false>(prm, ta, tb, grid, probs, nprobs, st);
 }
+
+// Reductions at least this long park residues in registers (single problems).
+constexpr int kRegParkMinK = 8192;
 
 int tile_width(int tile_n) { return tile_n == 128 ? 128 : 256; }
 
@@ -811,11 +855,11 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {
     case kModeResidue:
-      return launch_tile<kModeResidue, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeResidue, false>(BN, g.k >= kRegParkMinK, prm, ta, tb, grid, nullptr, 0, st);
     case kModeBound:
-      return launch_tile<kModeBound, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeBound, false>(BN, false, prm, ta, tb, grid, nullptr, 0, st);
     default:
-      return launch_tile<kModeRaw, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeRaw, false>(BN, false, prm, ta, tb, grid, nullptr, 0, st);
   }
 }
 
@@ -860,8 +904,8 @@ cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs,
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   const int BN = tile_width(g.tile_n);
   if (g.mode == kModeResidue)
-    return launch_tile<kModeResidue, true>(BN, prm, unused, unused, grid, probs, count, st);
-  return launch_tile<kModeBound, true>(BN, prm, unused, unused, grid, probs, count, st);
+    return launch_tile<kModeResidue, true>(BN, false, prm, unused, unused, grid, probs, count, st);
+  return launch_tile<kModeBound, true>(BN, false, prm, unused, unused, grid, probs, count, st);
 }
 
 }  // namespace ozk2
