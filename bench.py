@@ -59,12 +59,16 @@ def parse():
                     help="output tile width of the FP8 products (0: the library's rule; default: leave it)")
     ap.add_argument("--square-split", type=int, default=None,
                     help="square moduli as two passes for k up to this (0: never; default: the library's)")
+    ap.add_argument("--shapes", default="4096x4096x65536,65536x1024x1024",
+                    help="rect: comma-separated m x n x k shapes")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="batched: plan with --moduli and --tile (default 256) instead of the autotuner")
     ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd", "batched", "sweep", "rect"],
                     help="dgemm: the square product above; autograd: forward + backward of "
                          "C = A B with A 8192 x 4096, B 4096 x 4096 and upstream gradient W ~ N(0, 1); "
                          "batched: 512 products with m, n, k log-uniform on [64, 2048]; "
                          "sweep: error and TFLOP/s over sizes x phi x N (one JSON line each); "
-                         "rect: 4096 x 4096 x 65536 and 65536 x 1024 x 1024")
+                         "rect: 4096 x 4096 x 65536 and 65536 x 1024 x 1024 (or --shapes)")
     return ap.parse_args()
 
 
@@ -189,8 +193,9 @@ def kernel_source_hash():
 
 
 def recorded_traffic(size, moduli):
-    """DRAM bytes per residue-product launch from the committed ncu summary, if it was
-    taken on the current kernel source and this workload."""
+    """DRAM bytes per residue-product launch from the committed ncu summary and how they
+    were obtained, if the summary was taken on the current kernel source for this
+    workload; (None, None) otherwise."""
     p = os.path.join(PROFILES, "residue_gemm_traffic.txt")
     try:
         kv = {}
@@ -200,12 +205,12 @@ def recorded_traffic(size, moduli):
                     key, v = line.split(":", 1)
                     kv[key.strip()] = v.strip()
         if kv.get("kernel_source_sha256_16") != kernel_source_hash():
-            return None
+            return None, None
         if int(kv.get("size", -1)) != size or int(kv.get("num_moduli", -1)) != moduli:
-            return None
-        return float(kv["dram_bytes_per_launch"])
+            return None, None
+        return float(kv["dram_bytes_per_launch"]), kv.get("traffic_method", "ncu capture")
     except (OSError, KeyError, ValueError):
-        return None
+        return None, None
 
 
 # ------------------------------------------------------------------ exact error samples
@@ -476,9 +481,9 @@ def run_ours(a, rank, world):
     fp8_peak = 2.0 * float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops", 1700.0)))
     gemm_flops = 3 * N * flops  # residue products only; the bound product is its own phase
     achieved = gemm_flops / (phases["residue_gemm"] * 1e-3) / 1e12
-    traffic = recorded_traffic(a.size, N)
+    traffic, traffic_method = recorded_traffic(a.size, N)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp8_peak, "traffic": traffic,
+                "frac": achieved / fp8_peak, "traffic": traffic, "traffic_method": traffic_method,
                 "kernel": "fp8_gemm_kernel<residue> (3N FP8 products + mod-reduce)",
                 "peak_source": f"{src} bf16_tflops_sustained x 2 (dense FP8 / BF16 nominal ratio)"}
     conv_bytes = (16 + 1 + (2 * N if N <= 6 else 3 * N - 6)) * (m * k + k * n) + 8 * m * n
@@ -636,7 +641,10 @@ def run_batched(a, rank, world):
     # moduli count for FP64-level accuracy (sampled on the longest problems) and the faster
     # tile width of the plan (timed), picked by the autotuner
     t0 = time.perf_counter()
-    N, tile, tune_rep = ozk.choose_plan(As, Bs, "fp64", mode=a.mode, probes=4)
+    if a.no_autotune:
+        N, tile, tune_rep = a.moduli, a.tile if a.tile in (128, 256) else 256, {"moduli": [], "plan_ms": {}}
+    else:
+        N, tile, tune_rep = ozk.choose_plan(As, Bs, "fp64", mode=a.mode, probes=4)
     reports = tune_rep["moduli"]
     tune_s = time.perf_counter() - t0
     plan = ozk.BatchPlan(As, Bs, num_moduli=N, mode=a.mode, tile_n=tile)
@@ -689,7 +697,7 @@ def run_batched(a, rank, world):
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f8e4m3", "emulates": "f64", "data": "synthetic",
             "config": {"workload": f"512 products, m, n, k log-uniform on [64, 2048] (seed 0), phi={a.phi}, "
-                                   f"N={N}, tile 128x{tile} (autotuned), {a.mode} mode", "total_flop": flops,
+                                   f"N={N}, tile 128x{tile} ({'given' if a.no_autotune else 'autotuned'}), {a.mode} mode", "total_flop": flops,
                        "l2": "operands (2.7 GB) larger than L2, no flush"},
             "gpu_launches": launches * a.steps, "clocks": clk.summary(), "device_status": status,
             "plain_calls": {"ms_per_step": plain_ms, "tflops": flops / plain_ms / 1e9, "launches": 512 * single_launches,
@@ -827,7 +835,8 @@ def run_rect(a, rank, world):
         return
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    for (m, n, k) in [(4096, 4096, 65536), (65536, 1024, 1024)]:
+    for shape in a.shapes.split(","):
+        m, n, k = (int(x) for x in shape.lower().split("x"))
         for r in measure_shape(m, n, k, a.phi, [a.moduli], a.mode, a.steps, a.warmup, a.samples, dev):
             print(json.dumps(r), flush=True)
 
