@@ -204,9 +204,9 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N, bool fast) {
   L.flags = take(256);
   L.R = take(4 * size_t(m));
   L.S = take(4 * size_t(n));
-  L.colmaxA = take(8 * size_t(m));
+  L.colmaxA = take(4 * size_t(m));
   L.colbadA = take(4 * size_t(m));
-  L.colmaxB = take(8 * size_t(n));
+  L.colmaxB = take(4 * size_t(n));
   L.colbadB = take(4 * size_t(n));
   L.zero_end = o;
   L.eprime = take(4 * size_t(m));
@@ -359,7 +359,7 @@ ozk2_status scale_operand(Ctx& c, const Operand& op, int64_t first, int lines, c
                                c.at<uint32_t>(L.flags), c.st));
     t_launches += 1;
   } else {
-    unsigned long long* cm = c.at<unsigned long long>(sd.colmax) + first;
+    uint32_t* cm = c.at<uint32_t>(sd.colmax) + first;
     uint32_t* cb = c.at<uint32_t>(sd.colbad) + first;
     OZK2_TRY(launch_colmax(op.ptr, op.ld, c.k, lines, cm, cb, c.st));
     OZK2_TRY(launch_scale_cols(op.ptr, op.ld, c.k, lines, int(L.kp), cm, cb, ep, stat, bar,
@@ -895,9 +895,9 @@ BwLayout make_bw_layout(int64_t m, int64_t n, int64_t k, int N) {
   L.S = take(4 * size_t(n));
   L.Rk = take(4 * size_t(k));
   L.Sk = take(4 * size_t(k));
-  L.colmaxA = take(8 * size_t(k));
+  L.colmaxA = take(4 * size_t(k));
   L.colbadA = take(4 * size_t(k));
-  L.colmaxC = take(8 * size_t(n));
+  L.colmaxC = take(4 * size_t(n));
   L.colbadC = take(4 * size_t(n));
   L.zk = take(4 * size_t(k));
   L.zero_end = o;
@@ -1025,12 +1025,12 @@ ozk2_status run_backward(int64_t m, int64_t n, int64_t k, const double* A, int64
     t_launches += 2;
   }
   if (wantB) {
-    unsigned long long* cmC = reinterpret_cast<unsigned long long*>(at(L.colmaxC));
+    uint32_t* cmC = reinterpret_cast<uint32_t*>(at(L.colmaxC));
     uint32_t* cbC = reinterpret_cast<uint32_t*>(at(L.colbadC));
     OZK2_TRY(launch_colmax(dC, lddc, c.m, c.n, cmC, cbC, st));
     OZK2_TRY(launch_scale_cols(dC, lddc, c.m, c.n, int(L.mp), cmC, cbC, hp, at(L.cstatC), at(L.HhatT), nullptr,
                                nullptr, false, flags, st));
-    unsigned long long* cmA = reinterpret_cast<unsigned long long*>(at(L.colmaxA));
+    uint32_t* cmA = reinterpret_cast<uint32_t*>(at(L.colmaxA));
     uint32_t* cbA = reinterpret_cast<uint32_t*>(at(L.colbadA));
     OZK2_TRY(launch_colmax(A, lda, c.m, c.k, cmA, cbA, st));
     OZK2_TRY(launch_scale_cols(A, lda, c.m, c.k, int(L.mp), cmA, cbA, reinterpret_cast<int32_t*>(at(L.tA)),
@@ -1148,11 +1148,11 @@ BatchLayout batch_layout(int count, const int64_t* m, const int64_t* n, const in
   for (int i = 0, j = 0; i < count; ++i) {
     if (!active_problem(m[i], n[i], k[i])) continue;
     const size_t R = take(4 * size_t(m[i])), S = take(4 * size_t(n[i]));
-    const size_t cm = take(8 * size_t(n[i])), cb = take(4 * size_t(n[i]));
+    const size_t cm = take(4 * size_t(n[i])), cb = take(4 * size_t(n[i]));
     if (probs) {
       P(j).R = reinterpret_cast<float*>(at(R));
       P(j).S = reinterpret_cast<float*>(at(S));
-      P(j).colmaxB = reinterpret_cast<unsigned long long*>(at(cm));
+      P(j).colmaxB = reinterpret_cast<uint32_t*>(at(cm));
       P(j).colbadB = reinterpret_cast<uint32_t*>(at(cb));
     }
     ++j;

@@ -198,23 +198,13 @@ __global__ void __launch_bounds__(256, 2)
   crt_body<N>(cres, ldr, rstride, m, n, e, f, rowstat, colstat, C, ldc, ct, blockIdx.x, gridDim.x);
 }
 
-__device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int64_t b) {
-  int lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].first_block[kBkCrt] <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 template <int N>
 __global__ void __launch_bounds__(256, 2)
-    crt_batch(const BatchProblem* __restrict__ probs, int count, const __grid_constant__ CrtTable ct) {
-  const int p = batch_problem(probs, count, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  crt_body<N>(P.cres, P.ldr, static_cast<int64_t>(P.m) * P.ldr, P.m, P.n, P.e, P.f, P.rowstat, P.colstat, P.C,
-              P.ldc, ct, blockIdx.x - P.first_block[kBkCrt], P.nblocks[kBkCrt]);
+    crt_batch(const BatchProblem* __restrict__ probs, int count, int64_t total, const __grid_constant__ CrtTable ct) {
+  for_each_vblock(probs, count, kBkCrt, total, [&](const BatchProblem& P, int64_t v) {
+    crt_body<N>(P.cres, P.ldr, static_cast<int64_t>(P.m) * P.ldr, P.m, P.n, P.e, P.f, P.rowstat, P.colstat, P.C,
+                P.ldc, ct, v, P.nblocks[kBkCrt]);
+  });
 }
 
 template <int N>
@@ -235,7 +225,7 @@ cudaError_t launch_N(const int16_t* cres, int64_t ldr, int64_t rs, int m, int n,
 template <int N>
 cudaError_t launch_batch_N(const BatchProblem* probs, int count, int64_t blocks, const CrtTable& ct,
                            cudaStream_t st) {
-  crt_batch<N><<<static_cast<unsigned>(blocks), 256, 0, st>>>(probs, count, ct);
+  crt_batch<N><<<grouped_grid(blocks, 8), 256, 0, st>>>(probs, count, blocks, ct);
   return cudaGetLastError();
 }
 

@@ -173,6 +173,44 @@ __host__ __device__ constexpr uint32_t fp8_idesc(int M, int N) {
          | (static_cast<uint32_t>(M >> 4) << 24);    // M / 16
 }
 
+// ---------------------------------------------------------------- grouped launches
+// Problem of virtual block b of grouped launch w: the last p with first_block[w] <= b.
+__device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (probs[mid].first_block[w] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// A grouped launch w over `total` virtual blocks (problem p owns the virtual blocks
+// [first_block[w], first_block[w] + nblocks[w])).  Each physical block serves one
+// contiguous range of virtual blocks in order: one binary search finds its first
+// problem, and it steps to the following ones, so that the per-block cost of finding a
+// problem is paid once per physical block.  fn(P, v) runs for each virtual block, v its
+// index within problem P; every thread of the block makes the same calls.
+template <class F>
+__device__ __forceinline__ void for_each_vblock(const BatchProblem* __restrict__ probs, int count, int w,
+                                                int64_t total, F&& fn) {
+  const int64_t per = (total + gridDim.x - 1) / gridDim.x;
+  int64_t v = static_cast<int64_t>(blockIdx.x) * per;
+  const int64_t end = v + per < total ? v + per : total;
+  if (v >= end) return;
+  int p = batch_problem(probs, count, w, v);
+  int64_t first = probs[p].first_block[w];
+  int64_t next = p + 1 < count ? probs[p + 1].first_block[w] : total;
+  for (; v < end; ++v) {
+    while (v >= next) {
+      ++p;
+      first = next;
+      next = p + 1 < count ? probs[p + 1].first_block[w] : total;
+    }
+    fn(probs[p], v - first);
+  }
+}
+
 // ---------------------------------------------------------------- integers
 // Normalise a value in [-2h, 2(p-1-h)] (a sum of two symmetric residues).
 __device__ __forceinline__ int smod_small(int x, int p, int h) {

@@ -91,10 +91,12 @@ float bound_factor_f32(int64_t k);   // RU_fp32(1 + k 2^-24)
 cudaError_t launch_scale_rows(const double* A, int64_t lda, int m, int k, int kp,
                               int32_t* eprime, uint8_t* rowstat, uint8_t* Abar, float* sq,
                               bool fast, uint32_t* flags, cudaStream_t st);
+// colmax: per column, floor(log2 max |b|) + 1075 (0 for a zero column), accumulated
+// with atomicMax into a zeroed array.
 cudaError_t launch_colmax(const double* B, int64_t ldb, int k, int n,
-                          unsigned long long* colmax, uint32_t* colbad, cudaStream_t st);
+                          uint32_t* colmax, uint32_t* colbad, cudaStream_t st);
 cudaError_t launch_scale_cols(const double* B, int64_t ldb, int k, int n, int kp,
-                              const unsigned long long* colmax, const uint32_t* colbad,
+                              const uint32_t* colmax, const uint32_t* colbad,
                               int32_t* fprime, uint8_t* colstat, uint8_t* BbarT, float* part,
                               float* sq, bool fast, uint32_t* flags, cudaStream_t st);
 cudaError_t launch_exponents(int m, int n, const int32_t* eprime, const int32_t* fprime,
@@ -211,7 +213,7 @@ struct BatchProblem {
   float* R;
   float* S;
   float* partB;
-  unsigned long long* colmaxB;
+  uint32_t* colmaxB;  // log2 keys of the column maxima
   uint32_t* colbadB;
   uint8_t* planesA;
   uint8_t* planesB;
@@ -223,6 +225,27 @@ struct BatchProblem {
 // Tile of the column residue kernel: kResidTileCols columns x kResidTileK k per block
 // (one block per tile in a grouped launch).
 constexpr int kResidTileCols = 64, kResidTileK = 128;
+
+// Items of the row residue kernel: a warp covers 2^s lanes x 8 k of 32 / 2^s rows, s = 5
+// (256 consecutive k of one row) for kp >= 256, else the smallest s with 2^s 8 >= kp
+// (kp is a multiple of 32).
+__host__ __device__ constexpr int resid_rows_lane_log(int kp) {
+  return kp >= 256 ? 5 : (kp <= 32 ? 2 : (kp <= 64 ? 3 : (kp <= 128 ? 4 : 5)));
+}
+__host__ __device__ constexpr int64_t resid_rows_items(int lines, int kp) {
+  return static_cast<int64_t>((lines + (32 >> resid_rows_lane_log(kp)) - 1) / (32 >> resid_rows_lane_log(kp))) *
+         ((kp + (8 << resid_rows_lane_log(kp)) - 1) / (8 << resid_rows_lane_log(kp)));
+}
+
+// Physical blocks of a grouped launch over `total` virtual blocks: at most four waves of
+// per_sm resident blocks per SM (each physical block walks a contiguous range).
+inline int grouped_grid(int64_t total, int per_sm) {
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t cap = static_cast<int64_t>(sms) * per_sm * 4;
+  return static_cast<int>(total < cap ? total : cap);
+}
 
 // Blocks of each grouped launch for one problem (the same decomposition the
 // single-problem launchers use, without their grid caps).

@@ -40,8 +40,9 @@ constexpr int kElems = 8;  // elements per thread
 constexpr int kPairs = kElems / 2;
 
 // Signed byte pieces of a' (as floats) and t'.
-__device__ __forceinline__ void decode_element(double a, int e, float (&c)[kPieces], int& tp, bool& range_err) {
-  const unsigned long long bits = static_cast<unsigned long long>(__double_as_longlong(a));
+// a: the element's IEEE-754 bits (the kernels move elements as 64-bit integers).
+__device__ __forceinline__ void decode_element(unsigned long long bits, int e, float (&c)[kPieces], int& tp,
+                                               bool& range_err) {
   const unsigned long long mag = bits & kAbsMask;
   unsigned long long Mp = 0;
   tp = 0;
@@ -155,70 +156,105 @@ struct ResidArgs {
   uint32_t* flags;
 };
 
-__device__ __forceinline__ void load_table(const ModTable& mt, float* pow2_s) {
-  const int total = mt.N * kPow2Table;
-  for (int i = threadIdx.x; i < total; i += blockDim.x)
-    pow2_s[i] = static_cast<float>(mt.pow2[i / kPow2Table][i % kPow2Table]);
+// The residue kernels' constants in shared memory (the modulus loops index them by a
+// loop counter): per modulus the FP32 pairs and the table of 2^t mod p.
+struct __align__(16) ModConsts {
+  f2 neg_p, inv_p, neg_s, inv_s;
+  f2 w[kPieces];
+  float is1024, pad;  // p = 1024: the floor-based reduction
+};
+struct Tables {
+  ModConsts c[kMaxModuli];
+  float pow2[kMaxModuli * kPow2Table];
+};
+
+__device__ __forceinline__ void load_tables(const ModTable& mt, Tables& tb) {
+  for (int i = threadIdx.x; i < mt.N * kPow2Table; i += blockDim.x)
+    tb.pow2[i] = static_cast<float>(mt.pow2[i / kPow2Table][i % kPow2Table]);
+  for (int l = threadIdx.x; l < mt.N; l += blockDim.x) {
+    ModConsts& c = tb.c[l];
+    c.neg_p = mt.neg_p2[l];
+    c.inv_p = mt.inv_p2[l];
+    c.neg_s = mt.neg_s2[l];
+    c.inv_s = mt.inv_s2[l];
+#pragma unroll
+    for (int j = 0; j < kPieces; ++j) c.w[j] = mt.w2[l][j];
+    c.is1024 = mt.p[l] == 1024 ? 1.0f : 0.0f;
+    c.pad = 0.0f;
+  }
   __syncthreads();
 }
 
-__device__ __forceinline__ ModF consts_of(const ModTable& mt, int l) {
+// SQUARE: the modulus is one of the squares, the only kind that contains p = 1024.
+template <bool SQUARE>
+__device__ __forceinline__ ModF consts_of(const ModConsts& c) {
   ModF m;
-  m.neg_p = mt.neg_p2[l];
-  m.inv_p = mt.inv_p2[l];
+  m.neg_p = c.neg_p;
+  m.inv_p = c.inv_p;
 #pragma unroll
-  for (int j = 0; j < kPieces; ++j) m.w[j] = mt.w2[l][j];
-  m.pow2_modulus = (mt.p[l] == 1024);
+  for (int j = 0; j < kPieces; ++j) m.w[j] = c.w[j];
+  m.pow2_modulus = SQUARE && c.is1024 != 0.0f;
   return m;
 }
 
-__host__ __device__ constexpr int plane_of(int l) {
-  return l < kNumSquares ? 2 * l : 2 * kNumSquares + 3 * (l - kNumSquares);
-}
+// t' of the thread's 8 elements, one byte each (t' < kPow2Table).
+struct TpPack {
+  uint32_t w[2];
+};
+__device__ __forceinline__ int tp_of(const TpPack& p, int t) { return (p.w[t >> 2] >> (8 * (t & 3))) & 0xFF; }
 
-// Digits of the thread's 8 elements (4 pairs) for modulus l, packed as E4M3 bytes:
-// words[x][q] holds plane x's bytes of elements 4q .. 4q+3.
+// Digits of the thread's 8 elements (4 pairs) for square modulus l, packed as E4M3
+// bytes: words[x][q] holds plane x's bytes of elements 4q .. 4q+3.
 template <bool P2>
-__device__ __forceinline__ void digits_of(const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems],
-                                          const ModTable& mt, int l, const float* pow2_s,
-                                          uint32_t (&words)[3][2]) {
-  const ModF m = consts_of(mt, l);
-  const float* pw = pow2_s + l * kPow2Table;
-  if (l < kNumSquares) {
-    const f2 neg_s = mt.neg_s2[l];
-    const f2 inv_s = mt.inv_s2[l];
+__device__ __forceinline__ void square_words(const f2 (&c)[kPairs][kPieces], const TpPack& tp,
+                                             const Tables& tb, int l, uint32_t (&words)[2][2]) {
+  const ModConsts& cs = tb.c[l];
+  const ModF m = consts_of<true>(cs);
+  const float* pw = tb.pow2 + l * kPow2Table;
+  const f2 neg_s = cs.neg_s;
+  const f2 inv_s = cs.inv_s;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      f2 d1[2], d2[2];
+  for (int q = 0; q < 2; ++q) {
+    f2 d1[2], d2[2];
 #pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int pr = 2 * q + u;
-        square_digits(residue_of<P2>(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw), neg_s, inv_s, d1[u], d2[u]);
-      }
-      words[0][q] = e4m3x4(d1[0], d1[1]);
-      words[1][q] = e4m3x4(d2[0], d2[1]);
+    for (int u = 0; u < 2; ++u) {
+      const int pr = 2 * q + u;
+      square_digits(residue_of<P2>(c[pr], tp_of(tp, 2 * pr), tp_of(tp, 2 * pr + 1), m, pw), neg_s, inv_s, d1[u], d2[u]);
     }
-  } else {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      f2 d1[2], d2[2], d3[2];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int pr = 2 * q + u;
-        karatsuba_digits(residue_of<P2>(c[pr], tp[2 * pr], tp[2 * pr + 1], m, pw), d1[u], d2[u], d3[u]);
-      }
-      words[0][q] = e4m3x4(d1[0], d1[1]);
-      words[1][q] = e4m3x4(d2[0], d2[1]);
-      words[2][q] = e4m3x4(d3[0], d3[1]);
-    }
+    words[0][q] = e4m3x4(d1[0], d1[1]);
+    words[1][q] = e4m3x4(d2[0], d2[1]);
   }
 }
 
-// Pieces of element t of the thread's 8, into its pair slot.
-__device__ __forceinline__ void decode_into(f2 (&c)[kPairs][kPieces], int t, double a, int e, int& tp,
-                                            bool& range_err) {
+// The same for Karatsuba modulus l (three planes).
+template <bool P2>
+__device__ __forceinline__ void karatsuba_words(const f2 (&c)[kPairs][kPieces], const TpPack& tp,
+                                                const Tables& tb, int l, uint32_t (&words)[3][2]) {
+  const ModF m = consts_of<false>(tb.c[l]);
+  const float* pw = tb.pow2 + l * kPow2Table;
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    f2 d1[2], d2[2], d3[2];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int pr = 2 * q + u;
+      karatsuba_digits(residue_of<P2>(c[pr], tp_of(tp, 2 * pr), tp_of(tp, 2 * pr + 1), m, pw), d1[u], d2[u], d3[u]);
+    }
+    words[0][q] = e4m3x4(d1[0], d1[1]);
+    words[1][q] = e4m3x4(d2[0], d2[1]);
+    words[2][q] = e4m3x4(d3[0], d3[1]);
+  }
+}
+
+// Pieces of element t of the thread's 8, into its pair slot; its t' into tp (zeroed
+// before the first element) and any_tp.
+__device__ __forceinline__ void decode_into(f2 (&c)[kPairs][kPieces], int t, unsigned long long a, int e,
+                                            TpPack& tp, int& any_tp, bool& range_err) {
   float v[kPieces];
-  decode_element(a, e, v, tp, range_err);
+  int tpt;
+  decode_element(a, e, v, tpt, range_err);
+  tp.w[t >> 2] |= static_cast<uint32_t>(tpt) << (8 * (t & 3));
+  any_tp |= tpt;
 #pragma unroll
   for (int j = 0; j < kPieces; ++j) {
     if (t & 1) c[t >> 1][j].y = v[j];
@@ -226,109 +262,121 @@ __device__ __forceinline__ void decode_into(f2 (&c)[kPairs][kPieces], int t, dou
   }
 }
 
-// NM > 0: the number of moduli fixed at compile time (the modulus loop unrolls, every
-// constant sits at a known offset of the table); NM = 0: the table's own count.
-template <int NM>
-__device__ __forceinline__ int moduli_count(const ModTable& mt) {
-  return NM > 0 ? NM : mt.N;
+// Destination of a task that owns 8 consecutive bytes of every digit plane: the planes
+// are written in order, each store moving the pointer to the next plane.
+struct PlaneStore {
+  uint8_t* dst;    // the task's bytes in the next plane
+  int64_t stride;  // bytes from one plane to the next
+  bool active;
+  __device__ __forceinline__ void put(const uint32_t (&w)[2]) {
+    if (active) *reinterpret_cast<uint2*>(dst) = make_uint2(w[0], w[1]);
+    dst += stride;
+  }
+};
+
+// every digit |d| <= 16: E4M3 magnitude code at most 0x58 (= 16)
+__device__ __forceinline__ void check_digits(const uint32_t (&w)[2], uint32_t* flags) {
+  OZK2_DCHECK(__vcmpgtu4(w[0] & 0x7F7F7F7Fu, 0x58585858u) == 0u && __vcmpgtu4(w[1] & 0x7F7F7F7Fu, 0x58585858u) == 0u,
+              flags);
 }
 
-// The planes of one warp item of the row kernel: the lane's 4 bytes at rowp (when
-// store0: inside kp) and at rowp + 128 (when store1).
-template <int NM, bool P2>
-__device__ __forceinline__ void rows_planes(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
-                                            const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems], uint8_t* rowp,
-                                            bool store0, bool store1) {
-#pragma unroll (NM > 0 ? NM : 1)
-  for (int l = 0; l < moduli_count<NM>(mt); ++l) {
-    uint32_t words[3][2];
-    digits_of<P2>(c, tp, mt, l, pow2_s, words);
-    uint8_t* pl = rowp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
-    const int nplanes = (l < kNumSquares) ? 2 : 3;
+// Every digit plane of the thread's 8 elements, one modulus at a time.  The modulus loops
+// stay rolled: unrolled over all N moduli, the body outgrew the instruction cache and the
+// warps waited on instruction fetch more than on anything else.
+template <bool P2>
+__device__ __forceinline__ void all_planes(int N, const Tables& tb, const f2 (&c)[kPairs][kPieces],
+                                           const TpPack& tp, PlaneStore st, uint32_t* flags) {
+  const int nsq = N < kNumSquares ? N : kNumSquares;
+  // planes in order: 2 per square modulus, then 3 per Karatsuba modulus
+#pragma unroll 1
+  for (int l = 0; l < nsq; ++l) {
+    uint32_t w[2][2];
+    square_words<P2>(c, tp, tb, l, w);
 #pragma unroll
-    for (int xp = 0; xp < 3; ++xp) {
-      if (xp < nplanes) {
-        // every digit |d| <= 16: E4M3 magnitude code at most 0x58 (= 16)
-        OZK2_DCHECK(__vcmpgtu4(words[xp][0] & 0x7F7F7F7Fu, 0x58585858u) == 0u &&
-                        __vcmpgtu4(words[xp][1] & 0x7F7F7F7Fu, 0x58585858u) == 0u,
-                    a.flags);
-        if (store0) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride) = words[xp][0];
-        if (store1) *reinterpret_cast<uint32_t*>(pl + xp * a.plane_stride + 128) = words[xp][1];
-      }
+    for (int x = 0; x < 2; ++x) {
+      check_digits(w[x], flags);
+      st.put(w[x]);
+    }
+  }
+#pragma unroll 1
+  for (int l = kNumSquares; l < N; ++l) {
+    uint32_t w[3][2];
+    karatsuba_words<P2>(c, tp, tb, l, w);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      check_digits(w[x], flags);
+      st.put(w[x]);
     }
   }
 }
 
-// The planes of one task of the column kernel (8 consecutive k of one column): the
-// thread's 8 bytes at colp.
-template <int NM, bool P2>
-__device__ __forceinline__ void cols_planes(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
-                                            const f2 (&c)[kPairs][kPieces], const int (&tp)[kElems], uint8_t* colp,
-                                            bool active) {
-#pragma unroll (NM > 0 ? NM : 1)
-  for (int l = 0; l < moduli_count<NM>(mt); ++l) {
-    uint32_t words[3][2];
-    digits_of<P2>(c, tp, mt, l, pow2_s, words);
-    uint8_t* pl = colp + static_cast<int64_t>(plane_of(l)) * a.plane_stride;
-    const int nplanes = (l < kNumSquares) ? 2 : 3;
-    if (active) {
-#pragma unroll
-      for (int xp = 0; xp < 3; ++xp)
-        if (xp < nplanes) {
-          OZK2_DCHECK(__vcmpgtu4(words[xp][0] & 0x7F7F7F7Fu, 0x58585858u) == 0u &&
-                          __vcmpgtu4(words[xp][1] & 0x7F7F7F7Fu, 0x58585858u) == 0u,
-                      a.flags);
-          *reinterpret_cast<uint2*>(pl + xp * a.plane_stride) = make_uint2(words[xp][0], words[xp][1]);
-        }
-    }
-  }
+// The planes of one task: the P2 form only when some element of the warp needs it.
+__device__ __forceinline__ void task_planes(int N, const Tables& tb, const f2 (&c)[kPairs][kPieces],
+                                            const TpPack& tp, int any_tp, const PlaneStore& st,
+                                            uint32_t* flags) {
+  if (__any_sync(0xffffffffu, any_tp != 0)) all_planes<true>(N, tb, c, tp, st, flags);
+  else all_planes<false>(N, tb, c, tp, st, flags);
 }
 
-// Rows of A.  One warp covers 256 consecutive k of one row: lane l owns elements
-// base + 128 g + 4 l + {0..3}, g = 0, 1, so loads and 4-byte plane stores coalesce.
-constexpr int kRowSpan = 256;
+// Rows of A.  A warp item covers 2^s lanes x 8 k of 32 / 2^s rows: all 32 lanes on 256
+// consecutive k of one row when kp >= 256, else the smallest power of two of lanes that
+// covers the row (kp / 8 elements), so that short rows do not leave lanes idle.  Lane l
+// owns 8 consecutive elements (four 16-byte loads when the row is 16-byte aligned) and
+// writes 8 bytes of each plane.
+static_assert(kElems == 8, "the row kernel's item shapes assume 8 elements per lane");
 
 // vblock / vgrid: the block's index among, and the number of, the blocks serving this
 // operand (the warps stride over its items).
-template <int NM>
-__device__ __forceinline__ void residues_rows_body(const ResidArgs& a, const ModTable& mt, const float* pow2_s,
-                                                   int64_t vblock, int64_t vgrid) {
+__device__ __forceinline__ void residues_rows_body(const ResidArgs& a, int N, const Tables& tb, int64_t vblock,
+                                                   int64_t vgrid) {
   const int lane = threadIdx.x & 31;
   const int warps_per_block = blockDim.x >> 5;
-  const int nkw = (a.kp + kRowSpan - 1) / kRowSpan;
-  const int64_t items = static_cast<int64_t>(a.lines) * nkw;
+  const int ls = resid_rows_lane_log(a.kp);
+  const int rpi = 32 >> ls, span = kElems << ls;  // rows per item, k per item
+  const int nkw = (a.kp + span - 1) / span;
+  const int groups = (a.lines + rpi - 1) / rpi;
+  const int64_t items = static_cast<int64_t>(groups) * nkw;
   const int64_t stride = vgrid * warps_per_block;
   const int64_t first = vblock * warps_per_block + (threadIdx.x >> 5);
   if (first >= items) return;
-  // (row, k chunk) of the item, advanced by the stride's quotient and remainder
+  // (row group, k chunk) of the item, advanced by the stride's quotient and remainder
   // instead of a 64-bit division per item (the stride is at most a few grids of warps)
-  int row = static_cast<int>(first / nkw), chunk = static_cast<int>(first % nkw);
-  const int drow = static_cast<int>(stride / nkw), dchunk = static_cast<int>(stride % nkw);
+  int grp = static_cast<int>(first / nkw), chunk = static_cast<int>(first % nkw);
+  const int dgrp = static_cast<int>(stride / nkw), dchunk = static_cast<int>(stride % nkw);
+  // every line of X starts on a 16-byte boundary: 16-byte loads
+  const bool vec = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0 && (a.ldx & 1) == 0;
   bool range_err = false;
-  for (; row < a.lines; row += drow, chunk += dchunk) {
+  for (; grp < groups; grp += dgrp, chunk += dchunk) {
     if (chunk >= nkw) {
       chunk -= nkw;
-      if (++row >= a.lines) break;
+      if (++grp >= groups) break;
     }
-    const int base = chunk * kRowSpan;
-    const double* x = a.X + static_cast<int64_t>(row) * a.ldx;
-    const int e = a.exps[row];
+    const int row = grp * rpi + (lane >> ls);
+    const bool row_ok = row < a.lines;
+    const int h0 = chunk * span + (lane & ((1 << ls) - 1)) * kElems;
+    const unsigned long long* x =
+        reinterpret_cast<const unsigned long long*>(a.X + static_cast<int64_t>(row_ok ? row : 0) * a.ldx + h0);
+    const int e = row_ok ? a.exps[row] : 0;
+    unsigned long long v[kElems];
+    if (vec && row_ok && h0 + kElems <= a.k) {
+#pragma unroll
+      for (int q = 0; q < kElems / 2; ++q) {
+        const ulonglong2 d = __ldg(reinterpret_cast<const ulonglong2*>(x) + q);
+        v[2 * q] = d.x;
+        v[2 * q + 1] = d.y;
+      }
+    } else {
+#pragma unroll
+      for (int t = 0; t < kElems; ++t) v[t] = (row_ok && h0 + t < a.k) ? __ldg(x + t) : 0ull;
+    }
     f2 c[kPairs][kPieces];
-    int tp[kElems];
+    TpPack tp{};
     int any_tp = 0;
 #pragma unroll
-    for (int g = 0; g < 2; ++g) {
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int h = base + g * 128 + lane * 4 + t;
-        decode_into(c, 4 * g + t, (h < a.k) ? __ldg(x + h) : 0.0, e, tp[4 * g + t], range_err);
-        any_tp |= tp[4 * g + t];
-      }
-    }
-    uint8_t* rowp = a.planes + static_cast<int64_t>(row) * a.ldp + base + lane * 4;
-    const bool store0 = base + lane * 4 < a.kp, store1 = base + 128 + lane * 4 < a.kp;
-    if (__any_sync(0xffffffffu, any_tp != 0)) rows_planes<NM, true>(a, mt, pow2_s, c, tp, rowp, store0, store1);
-    else rows_planes<NM, false>(a, mt, pow2_s, c, tp, rowp, store0, store1);
+    for (int t = 0; t < kElems; ++t) decode_into(c, t, v[t], e, tp, any_tp, range_err);
+    const PlaneStore st{a.planes + static_cast<int64_t>(row_ok ? row : 0) * a.ldp + h0, a.plane_stride,
+                        row_ok && h0 < a.kp};
+    task_planes(N, tb, c, tp, any_tp, st, a.flags);
   }
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
@@ -352,10 +400,8 @@ __device__ __forceinline__ int tile_slot(int h) {  // position of k offset h wit
 
 // Tiles t0, t0 + tstride, ... of the operand (tiles numbered with the column tile
 // fastest).
-template <int NM>
-__device__ __forceinline__ void residues_cols_tiled_body(const ResidArgs& a, const ModTable& mt,
-                                                         const float* pow2_s, double* tile, int64_t t0,
-                                                         int64_t tstride) {
+__device__ __forceinline__ void residues_cols_tiled_body(const ResidArgs& a, int N, const Tables& tb,
+                                                         unsigned long long* tile, int64_t t0, int64_t tstride) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tiles_n = (a.lines + kTileCols - 1) / kTileCols, tiles_k = (a.kp + kTileK - 1) / kTileK;
   const int64_t tiles = static_cast<int64_t>(tiles_n) * tiles_k;
@@ -367,11 +413,11 @@ __device__ __forceinline__ void residues_cols_tiled_body(const ResidArgs& a, con
 #pragma unroll 4
     for (int r = warp; r < kTileK; r += 8) {
       const int h = k0 + r;
-      const double* row = a.X + static_cast<int64_t>(h) * a.ldx;
+      const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.X + static_cast<int64_t>(h) * a.ldx);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int c = lane + 32 * u, j = j0 + c;
-        tile[c * kTilePitch + tile_slot(r)] = (h < a.k && j < a.lines) ? __ldg(row + j) : 0.0;
+        tile[c * kTilePitch + tile_slot(r)] = (h < a.k && j < a.lines) ? __ldg(row + j) : 0ull;
       }
     }
     __syncthreads();
@@ -383,74 +429,64 @@ __device__ __forceinline__ void residues_cols_tiled_body(const ResidArgs& a, con
       const int j = j0 + c, h0 = k0 + chunk * 8;
       const bool active = j < a.lines && h0 < a.kp;
       const int e = j < a.lines ? a.exps[j] : 0;
-      const double* src = tile + c * kTilePitch + chunk * 8;
+      const unsigned long long* src = tile + c * kTilePitch + chunk * 8;
       f2 cc[kPairs][kPieces];
-      int tp[kElems];
+      TpPack tp{};
       int any_tp = 0;
 #pragma unroll
       for (int u = 0; u < kElems; ++u) {
-        decode_into(cc, u, src[u ^ ((chunk >> 1) & 7)], e, tp[u], range_err);
-        any_tp |= tp[u];
+        decode_into(cc, u, src[u ^ ((chunk >> 1) & 7)], e, tp, any_tp, range_err);
       }
-      uint8_t* colp = a.planes + static_cast<int64_t>(j < a.lines ? j : 0) * a.ldp + (h0 < a.kp ? h0 : 0);
-      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(a, mt, pow2_s, cc, tp, colp, active);
-      else cols_planes<NM, false>(a, mt, pow2_s, cc, tp, colp, active);
+      const PlaneStore st{a.planes + static_cast<int64_t>(j < a.lines ? j : 0) * a.ldp + (h0 < a.kp ? h0 : 0),
+                          a.plane_stride, active};
+      task_planes(N, tb, cc, tp, any_tp, st, a.flags);
     }
     __syncthreads();  // the tile is reloaded
   }
   if (range_err) atomicOr(a.flags, kFlagRange);
 }
 
-template <int NM>
 __global__ void __launch_bounds__(256, 3) residues_cols_tiled_kernel(ResidArgs a,
                                                                     const __grid_constant__ ModTable mt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* pow2_s = reinterpret_cast<float*>(smem_raw + kTileBytes);
-  load_table(mt, pow2_s);
-  residues_cols_tiled_body<NM>(a, mt, pow2_s, reinterpret_cast<double*>(smem_raw), blockIdx.x, gridDim.x);
+  Tables& tb = *reinterpret_cast<Tables*>(smem_raw + kTileBytes);
+  load_tables(mt, tb);
+  residues_cols_tiled_body(a, mt.N, tb, reinterpret_cast<unsigned long long*>(smem_raw), blockIdx.x, gridDim.x);
 }
 
-template <int NM>
 __global__ void __launch_bounds__(256, 3) residues_rows_kernel(ResidArgs a, const __grid_constant__ ModTable mt) {
-  __shared__ float pow2_s[kMaxModuli * kPow2Table];
-  load_table(mt, pow2_s);
-  residues_rows_body<NM>(a, mt, pow2_s, blockIdx.x, gridDim.x);
+  __shared__ Tables tb;
+  load_tables(mt, tb);
+  residues_rows_body(a, mt.N, tb, blockIdx.x, gridDim.x);
 }
 
-__device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
-  int lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].first_block[w] <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
-// Grouped: rows of every A; columns of every B (one block per tile).
-__global__ void __launch_bounds__(256, 3) residues_rows_batch(const BatchProblem* __restrict__ probs, int count,
-                                                           uint32_t* flags, const __grid_constant__ ModTable mt) {
-  __shared__ float pow2_s[kMaxModuli * kPow2Table];
-  load_table(mt, pow2_s);
-  const int p = batch_problem(probs, count, kBkResidRows, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.ldp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.ldp, flags};
-  residues_rows_body<0>(a, mt, pow2_s, blockIdx.x - P.first_block[kBkResidRows], P.nblocks[kBkResidRows]);
+// Grouped: rows of every A; columns of every B (one virtual block per tile).
+__global__ void __launch_bounds__(256, 2) residues_rows_batch(const BatchProblem* __restrict__ probs, int count,
+                                                           int64_t total, uint32_t* flags,
+                                                           const __grid_constant__ ModTable mt) {
+  __shared__ Tables tb;
+  load_tables(mt, tb);
+  for_each_vblock(probs, count, kBkResidRows, total, [&](const BatchProblem& P, int64_t v) {
+    const ResidArgs a{P.A, P.lda, P.m, P.k, P.kp, P.ldp, P.e, P.planesA, static_cast<int64_t>(P.m) * P.ldp, flags};
+    residues_rows_body(a, mt.N, tb, v, P.nblocks[kBkResidRows]);
+  });
 }
 
 __global__ void __launch_bounds__(256, 3) residues_cols_batch(const BatchProblem* __restrict__ probs, int count,
-                                                           uint32_t* flags, const __grid_constant__ ModTable mt) {
+                                                           int64_t total, uint32_t* flags,
+                                                           const __grid_constant__ ModTable mt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* pow2_s = reinterpret_cast<float*>(smem_raw + kTileBytes);
-  load_table(mt, pow2_s);
-  const int p = batch_problem(probs, count, kBkResidCols, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.ldp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.ldp, flags};
-  residues_cols_tiled_body<0>(a, mt, pow2_s, reinterpret_cast<double*>(smem_raw),
-                              blockIdx.x - P.first_block[kBkResidCols], P.nblocks[kBkResidCols]);
+  Tables& tb = *reinterpret_cast<Tables*>(smem_raw + kTileBytes);
+  load_tables(mt, tb);
+  for_each_vblock(probs, count, kBkResidCols, total, [&](const BatchProblem& P, int64_t v) {
+    const ResidArgs a{P.B, P.ldb, P.n, P.k, P.kp, P.ldp, P.f, P.planesB, static_cast<int64_t>(P.n) * P.ldp, flags};
+    residues_cols_tiled_body(a, mt.N, tb, reinterpret_cast<unsigned long long*>(smem_raw), v,
+                             P.nblocks[kBkResidCols]);
+  });
 }
 
-constexpr size_t kColsSmem = kTileBytes + sizeof(float) * kMaxModuli * kPow2Table;
+constexpr size_t kColsSmem = kTileBytes + sizeof(Tables);
+static_assert(kTileBytes % 16 == 0, "the tables follow the tile on a 16-byte boundary");
 
 // ------------------------------------------------------------------ gradient operands
 // The upstream gradient dC (m x n, row-major) of C = A B enters both gradient products
@@ -478,18 +514,15 @@ struct GradArgs {
   bool do_g, do_h;  // which of the two outputs to write
 };
 
-template <int NM>
 __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const __grid_constant__ ModTable mt) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* tile = reinterpret_cast<double*>(smem_raw);
-  float* pow2_s = reinterpret_cast<float*>(smem_raw + kTileBytes);
-  load_table(mt, pow2_s);
+  unsigned long long* tile = reinterpret_cast<unsigned long long*>(smem_raw);
+  Tables& tb = *reinterpret_cast<Tables*>(smem_raw + kTileBytes);
+  load_tables(mt, tb);
+  const int N = mt.N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int tiles_n = (a.n + kTileCols - 1) / kTileCols, tiles_m = (a.m + kTileK - 1) / kTileK;
   const int64_t tiles = static_cast<int64_t>(tiles_n) * tiles_m;
-  // plane strides of the two outputs (a task's ResidArgs carries the destination's)
-  ResidArgs ah{nullptr, 0, a.n, a.m, a.m, a.ldh, nullptr, a.planesH, static_cast<int64_t>(a.n) * a.ldh, a.flags};
-  ResidArgs ag{nullptr, 0, a.m, a.n, a.n, a.ldg, nullptr, a.planesG, static_cast<int64_t>(a.m) * a.ldg, a.flags};
   bool range_err = false;
   for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
     const int j0 = static_cast<int>(t % tiles_n) * kTileCols;
@@ -497,11 +530,11 @@ __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const
 #pragma unroll 4
     for (int r = warp; r < kTileK; r += 8) {
       const int i = i0 + r;
-      const double* row = a.dC + static_cast<int64_t>(i) * a.lddc;
+      const unsigned long long* row = reinterpret_cast<const unsigned long long*>(a.dC + static_cast<int64_t>(i) * a.lddc);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int c = lane + 32 * u, j = j0 + c;
-        tile[c * kTilePitch + tile_slot(r)] = (i < a.m && j < a.n) ? __ldg(row + j) : 0.0;
+        tile[c * kTilePitch + tile_slot(r)] = (i < a.m && j < a.n) ? __ldg(row + j) : 0ull;
       }
     }
     __syncthreads();
@@ -513,20 +546,19 @@ __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const
       const int j = j0 + c, ib = i0 + chunk * 8;
       const bool active = j < a.n && ib < a.m;
       const int hj = j < a.n ? a.h[j] : 0;
-      const double* src = tile + c * kTilePitch + chunk * 8;
+      const unsigned long long* src = tile + c * kTilePitch + chunk * 8;
       f2 cc[kPairs][kPieces];
-      int tp[kElems];
+      TpPack tp{};
       int any_tp = 0;
 #pragma unroll
       for (int u = 0; u < kElems; ++u) {
         const int i = ib + u;
         const int ex = hj - (i < a.m ? a.e[i] : 0);
-        decode_into(cc, u, src[u ^ ((chunk >> 1) & 7)], ex, tp[u], range_err);
-        any_tp |= tp[u];
+        decode_into(cc, u, src[u ^ ((chunk >> 1) & 7)], ex, tp, any_tp, range_err);
       }
-      uint8_t* colp = a.planesH + static_cast<int64_t>(j < a.n ? j : 0) * a.ldh + (ib < a.m ? ib : 0);
-      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(ah, mt, pow2_s, cc, tp, colp, active);
-      else cols_planes<NM, false>(ah, mt, pow2_s, cc, tp, colp, active);
+      const PlaneStore st{a.planesH + static_cast<int64_t>(j < a.n ? j : 0) * a.ldh + (ib < a.m ? ib : 0),
+                          static_cast<int64_t>(a.n) * a.ldh, active};
+      task_planes(N, tb, cc, tp, any_tp, st, a.flags);
     }
     // row pass: G' (lines i, positions j); warp w, round s: rows 4 (8 s + w) + lane / 8
 #pragma unroll 1
@@ -536,18 +568,17 @@ __global__ void __launch_bounds__(256, 3) grad_residues_kernel(GradArgs a, const
       const bool active = i < a.m && jb < a.n;
       const int gi = i < a.m ? a.g[i] : 0;
       f2 cc[kPairs][kPieces];
-      int tp[kElems];
+      TpPack tp{};
       int any_tp = 0;
 #pragma unroll
       for (int u = 0; u < kElems; ++u) {
         const int c = chunk * 8 + u, j = jb + u;
         const int ex = gi - (j < a.n ? a.f[j] : 0);
-        decode_into(cc, u, tile[c * kTilePitch + tile_slot(r)], ex, tp[u], range_err);
-        any_tp |= tp[u];
+        decode_into(cc, u, tile[c * kTilePitch + tile_slot(r)], ex, tp, any_tp, range_err);
       }
-      uint8_t* rowp = a.planesG + static_cast<int64_t>(i < a.m ? i : 0) * a.ldg + (jb < a.n ? jb : 0);
-      if (__any_sync(0xffffffffu, any_tp != 0)) cols_planes<NM, true>(ag, mt, pow2_s, cc, tp, rowp, active);
-      else cols_planes<NM, false>(ag, mt, pow2_s, cc, tp, rowp, active);
+      const PlaneStore st{a.planesG + static_cast<int64_t>(i < a.m ? i : 0) * a.ldg + (jb < a.n ? jb : 0),
+                          static_cast<int64_t>(a.m) * a.ldg, active};
+      task_planes(N, tb, cc, tp, any_tp, st, a.flags);
     }
     __syncthreads();  // the tile is reloaded
   }
@@ -633,53 +664,6 @@ void allow_cols_smem(K* kernel, bool (&done)[64]) {
     done[dev] = true;
 }
 
-// Launch with the modulus loop unrolled for N in [kUnrollLo, kUnrollHi] (the counts the
-// moduli tuner and the benchmarks use), the generic loop otherwise.
-constexpr int kUnrollLo = 8, kUnrollHi = 16;
-
-struct RowsKernel {
-  template <int NM>
-  static void launch(int grid, cudaStream_t st, const ResidArgs& a, const ModTable& mt) {
-    residues_rows_kernel<NM><<<grid, 256, 0, st>>>(a, mt);
-  }
-};
-struct ColsKernel {
-  template <int NM>
-  static void launch(int grid, cudaStream_t st, const ResidArgs& a, const ModTable& mt) {
-    static bool done[64] = {};  // per device and instantiation
-    allow_cols_smem(residues_cols_tiled_kernel<NM>, done);
-    residues_cols_tiled_kernel<NM><<<grid, 256, kColsSmem, st>>>(a, mt);
-  }
-};
-
-template <class K, int NM = kUnrollLo>
-void launch_unrolled(const ModTable& mt, int grid, cudaStream_t st, const ResidArgs& a) {
-  if constexpr (NM > kUnrollHi) {
-    K::template launch<0>(grid, st, a, mt);
-  } else {
-    if (mt.N == NM) K::template launch<NM>(grid, st, a, mt);
-    else launch_unrolled<K, NM + 1>(mt, grid, st, a);
-  }
-}
-
-// The gradient kernel with the modulus loop unrolled for N in [kUnrollLo, kUnrollHi].
-template <int NM = kUnrollLo>
-void launch_grad_unrolled(const ModTable& mt, int grid, cudaStream_t st, const GradArgs& a) {
-  if constexpr (NM > kUnrollHi) {
-    static bool done[64] = {};
-    allow_cols_smem(grad_residues_kernel<0>, done);
-    grad_residues_kernel<0><<<grid, 256, kColsSmem, st>>>(a, mt);
-  } else {
-    if (mt.N == NM) {
-      static bool done[64] = {};
-      allow_cols_smem(grad_residues_kernel<NM>, done);
-      grad_residues_kernel<NM><<<grid, 256, kColsSmem, st>>>(a, mt);
-    } else {
-      launch_grad_unrolled<NM + 1>(mt, grid, st, a);
-    }
-  }
-}
-
 int grid_for(int64_t warps) {
   int dev = 0, sms = 148;
   cudaGetDevice(&dev);
@@ -695,9 +679,7 @@ cudaError_t launch_residues_rows(const double* A, int64_t lda, int m, int k, int
                                  const ModTable& mt, uint8_t* planes, uint32_t* flags, cudaStream_t st,
                                  int64_t plane_stride) {
   ResidArgs a{A, lda, m, k, kp, ldp, e, planes, plane_stride ? plane_stride : static_cast<int64_t>(m) * ldp, flags};
-  const int64_t warps = static_cast<int64_t>(m) * ((kp + kRowSpan - 1) / kRowSpan);
-  const int grid = grid_for(warps);
-  launch_unrolled<RowsKernel>(mt, grid, st, a);
+  residues_rows_kernel<<<grid_for(resid_rows_items(m, kp)), 256, 0, st>>>(a, mt);
   return cudaGetLastError();
 }
 
@@ -710,7 +692,9 @@ cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = static_cast<int64_t>((n + kTileCols - 1) / kTileCols) * ((kp + kTileK - 1) / kTileK);
   const int grid = static_cast<int>(std::min<int64_t>(tiles, 3 * static_cast<int64_t>(sms)));
-  launch_unrolled<ColsKernel>(mt, grid, st, a);
+  static bool done[64] = {};  // per device
+  allow_cols_smem(residues_cols_tiled_kernel, done);
+  residues_cols_tiled_kernel<<<grid, 256, kColsSmem, st>>>(a, mt);
   return cudaGetLastError();
 }
 
@@ -720,8 +704,8 @@ cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t 
     return cudaErrorInvalidValue;
   static bool done[64] = {};
   allow_cols_smem(residues_cols_batch, done);
-  residues_rows_batch<<<static_cast<unsigned>(rows_blocks), 256, 0, st>>>(probs, count, flags, mt);
-  residues_cols_batch<<<static_cast<unsigned>(cols_blocks), 256, kColsSmem, st>>>(probs, count, flags, mt);
+  residues_rows_batch<<<grouped_grid(rows_blocks, 3), 256, 0, st>>>(probs, count, rows_blocks, flags, mt);
+  residues_cols_batch<<<grouped_grid(cols_blocks, 3), 256, kColsSmem, st>>>(probs, count, cols_blocks, flags, mt);
   return cudaGetLastError();
 }
 
@@ -734,7 +718,9 @@ cudaError_t launch_grad_residues(const double* dC, int64_t lddc, int m, int n, c
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t tiles = static_cast<int64_t>((n + kTileCols - 1) / kTileCols) * ((m + kTileK - 1) / kTileK);
   const int grid = static_cast<int>(std::min<int64_t>(tiles, 3 * static_cast<int64_t>(sms)));
-  launch_grad_unrolled(mt, grid, st, a);
+  static bool done[64] = {};  // per device
+  allow_cols_smem(grad_residues_kernel, done);
+  grad_residues_kernel<<<grid, 256, kColsSmem, st>>>(a, mt);
   return cudaGetLastError();
 }
 

@@ -14,73 +14,85 @@
 // encoding: no FP64 arithmetic and no 2^e' factor is ever formed (e' reaches 1081
 // for subnormal rows, beyond the double range).  Non-finite entries count as 0 and
 // mark their row / column; a row with no nonzero finite entry gets e' = e = 0.
+#include <algorithm>
+
 #include "device.cuh"
 
 namespace ozk2 {
 namespace {
 
-constexpr unsigned long long kAbsMask = 0x7FFFFFFFFFFFFFFFull;
-constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
-constexpr unsigned long long kFracMask = (1ull << 52) - 1;
+// A double's magnitude as two 32-bit words: hi (sign cleared: 11 exponent bits and the
+// top 20 fraction bits) and lo (the low 32 fraction bits).  The kernels below work on
+// these words with 32-bit integer operations only.
+struct Mag {
+  uint32_t hi, lo;
+};
+__device__ __forceinline__ Mag mag_of(double x) {
+  return Mag{static_cast<uint32_t>(__double2hiint(x)) & 0x7FFFFFFFu, static_cast<uint32_t>(__double2loint(x))};
+}
+__device__ __forceinline__ bool nonfinite(Mag m) { return (m.hi >> 20) == 0x7FFu; }
 
-// floor(log2 x) of a positive finite double given by its bits.
-__device__ __forceinline__ int floor_log2_bits(unsigned long long mag) {
-  const int be = static_cast<int>(mag >> 52);
-  if (be != 0) return be - 1023;
-  return (63 - __clzll(mag)) - 1074;  // subnormal
+// floor(log2 |x|) + 1075 for a finite nonzero x, a key from 1 (2^-1074) to 2098 that
+// orders like |x|; 0 for zero and for a non-finite x, which also sets bad.  No branch,
+// so that the loops below keep their loads in flight together.
+__device__ __forceinline__ uint32_t log2_key(Mag m, bool& bad) {
+  const uint32_t be = m.hi >> 20;
+  const uint32_t z = m.hi != 0u ? __clz(m.hi) : 32u + __clz(m.lo);  // leading zeros of the 64-bit magnitude
+  bad |= be == 0x7FFu;
+  return be == 0x7FFu ? 0u : (be != 0u ? be + 52u : 64u - z);  // normal: floor(log2) = be - 1023
 }
 
-// E4M3 code of the least E4M3 value >= |x| 2^sh, for |x| given by its (finite) bits and
-// |x| 2^sh < 2^8.  Positive values below 2^-9 give the smallest subnormal, 2^-9.
-// E4M3 codes of non-negative values increase with the value, so rounding the
-// 3-bit mantissa up may carry into the exponent field and stay correct.
-__device__ __forceinline__ uint32_t ru_e4m3_scaled(unsigned long long mag, int sh) {
-  if (mag == 0) return 0;
-  int be = static_cast<int>(mag >> 52);
-  unsigned long long f52 = mag & kFracMask;
-  int lg;
-  if (be == 0) {
-    const int top = 63 - __clzll(f52);
-    lg = top - 1074;
-    f52 = (f52 << (52 - top)) & kFracMask;
-  } else {
-    lg = be - 1023;
+// e' = 7 - floor(log2 max |x|) from the key of the line's maximum; 0 for a zero line.
+__device__ __forceinline__ int prelim_exponent(uint32_t key) { return key ? 1082 - static_cast<int>(key) : 0; }
+
+// floor(log2 |x|) and the 52 fraction bits of |x| normalised (the top 20 in f20, the rest
+// in lo) for a finite nonzero x; subnormals are shifted up (rare, 64-bit operations).
+__device__ __forceinline__ int normalise(Mag& m) {
+  const int be = static_cast<int>(m.hi >> 20);
+  if (be != 0) {
+    m.hi &= 0xFFFFFu;
+    return be - 1023;
   }
-  const int ev = lg + sh;  // floor(log2) of the scaled value, <= 7
-  if (ev >= -6) {          // E4M3 normal range
-    return static_cast<uint32_t>(((ev + 7) << 3) + static_cast<int>(f52 >> 49) +
-                                 ((f52 & ((1ull << 49) - 1)) != 0 ? 1 : 0));
-  }
-  if (ev >= -9) {  // E4M3 subnormal m 2^-9, m = ceil(v 2^9) in 1..8
-    const int shr = 52 - (ev + 9);
-    const unsigned long long mant = f52 | (1ull << 52);
-    return static_cast<uint32_t>((mant >> shr) + ((mant & ((1ull << shr) - 1)) != 0 ? 1 : 0));
-  }
-  return 1;
+  const unsigned long long f52 = (static_cast<unsigned long long>(m.hi) << 32) | m.lo;
+  const int top = 63 - __clzll(f52);
+  const unsigned long long n52 = (f52 << (52 - top)) & ((1ull << 52) - 1);
+  m.hi = static_cast<uint32_t>(n52 >> 32);
+  m.lo = static_cast<uint32_t>(n52);
+  return top - 1074;
 }
 
-// RU_fp32(|x| 2^sh) for |x| given by its (finite, nonzero) bits and |x| 2^sh < 2^8: the
-// float bit pattern is assembled from the exponent and the top 23 fraction bits, plus one
-// unit when any lower bit is set (a carry into the exponent field stays correct).
-// Results below the FP32 normal range are replaced by 2^-126, still an upper bound.
-__device__ __forceinline__ float ru_f32_scaled(unsigned long long mag, int sh) {
-  if (mag == 0) return 0.0f;
-  int be = static_cast<int>(mag >> 52);
-  unsigned long long f52 = mag & kFracMask;
-  int lg;
-  if (be == 0) {
-    const int top = 63 - __clzll(f52);
-    lg = top - 1074;
-    f52 = (f52 << (52 - top)) & kFracMask;
-  } else {
-    lg = be - 1023;
+// E4M3 code of the least E4M3 value >= |x| 2^sh, for a finite x with |x| 2^sh < 2^8.
+// Positive values below 2^-9 give the smallest subnormal, 2^-9.  E4M3 codes of
+// non-negative values increase with the value, so rounding the 3-bit mantissa up may
+// carry into the exponent field and stay correct.
+__device__ __forceinline__ uint32_t ru_e4m3_scaled(Mag m, int sh) {
+  if ((m.hi | m.lo) == 0u) return 0u;
+  const int ev = normalise(m) + sh;  // floor(log2) of the scaled value, <= 7
+  if (ev >= -6)                      // E4M3 normal range: the top 3 fraction bits, rounded up
+    return static_cast<uint32_t>((ev + 7) << 3) + (m.hi >> 17) + (((m.hi & 0x1FFFFu) | m.lo) != 0u ? 1u : 0u);
+  if (ev >= -9) {  // E4M3 subnormal k 2^-9, k = ceil(|x| 2^(sh + 9)) in 1..8
+    const uint32_t mant = m.hi | (1u << 20);  // the significand's top 21 bits
+    const int s = 11 - ev;                    // 18 .. 20
+    return (mant >> s) + (((mant & ((1u << s) - 1u)) | m.lo) != 0u ? 1u : 0u);
   }
-  const int ev = lg + sh;
+  return 1u;
+}
+
+// RU_fp32(|x| 2^sh) for a finite nonzero x with |x| 2^sh < 2^8: the float bit pattern
+// is assembled from the exponent and the top 23 fraction bits, plus one unit when any
+// lower bit is set (a carry into the exponent field stays correct).  Results below the
+// FP32 normal range are replaced by 2^-126, still an upper bound.
+__device__ __forceinline__ float ru_f32_scaled(Mag m, int sh) {
+  if ((m.hi | m.lo) == 0u) return 0.0f;
+  const int ev = normalise(m) + sh;
   if (ev < -126) return 1.1754943508222875e-38f;  // 2^-126
-  const uint32_t bits = (static_cast<uint32_t>(ev + 127) << 23) + static_cast<uint32_t>(f52 >> 29) +
-                        ((f52 & ((1ull << 29) - 1)) != 0 ? 1u : 0u);
+  const uint32_t bits = (static_cast<uint32_t>(ev + 127) << 23) + ((m.hi << 3) | (m.lo >> 29)) +
+                        ((m.lo & 0x1FFFFFFFu) != 0u ? 1u : 0u);
   return __uint_as_float(bits);
 }
+
+// Loads a thread keeps in flight per batch (the column kernels take twice as many).
+constexpr int kBatch = 4;
 
 // One warp per row of A: row maximum, e'_i, row status, then Abar (m x kp bytes).
 // FAST: instead of Abar, the sum of squares s_i = sum_h RU_fp32(2^e'_i |a_ih|)^2 with
@@ -95,31 +107,30 @@ __device__ __forceinline__ void scale_rows_body(const double* __restrict__ A, in
   const int row = static_cast<int>(vblock) * (blockDim.x >> 5) + warp;
   if (row >= m) return;
   const double* a = A + static_cast<int64_t>(row) * lda;
-  unsigned long long mx = 0;
+  uint32_t key = 0u;
   bool bad = false;
-  for (int h = lane; h < k; h += 32) {
-    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
-    if (b >= kInfBits) bad = true;
-    else mx = b > mx ? b : mx;
-  }
+  for (int h = lane; h < k; h += 32 * kBatch) {
+    double v[kBatch];  // the loads of a batch are issued before any is used
 #pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
-    mx = o > mx ? o : mx;
+    for (int u = 0; u < kBatch; ++u) v[u] = h + 32 * u < k ? __ldg(a + h + 32 * u) : 0.0;
+#pragma unroll
+    for (int u = 0; u < kBatch; ++u) key = max(key, log2_key(mag_of(v[u]), bad));
   }
+  key = __reduce_max_sync(0xffffffffu, key);
   bad = __any_sync(0xffffffffu, bad);
-  const int ep = (mx == 0) ? 0 : 7 - floor_log2_bits(mx);
+  const int ep = prelim_exponent(key);
   if (lane == 0) {
     eprime[row] = ep;
-    rowstat[row] = static_cast<uint8_t>((mx == 0 ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
+    rowstat[row] = static_cast<uint8_t>((key == 0u ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
     if (bad) atomicOr(flags, kFlagNonfinite);
   }
   if constexpr (FAST) {
     float acc = 0.0f;
+#pragma unroll 4
     for (int h = lane; h < k; h += 32) {
-      const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
-      if (b != 0 && b < kInfBits) {
-        const float v = ru_f32_scaled(b, ep);
+      const Mag mg = mag_of(__ldg(a + h));
+      if (!nonfinite(mg)) {
+        const float v = ru_f32_scaled(mg, ep);
         acc = __fmaf_ru(v, v, acc);
       }
     }
@@ -128,17 +139,23 @@ __device__ __forceinline__ void scale_rows_body(const double* __restrict__ A, in
     if (lane == 0) sq[row] = acc;
   } else {
     uint8_t* out = Abar + static_cast<int64_t>(row) * kp;
-    for (int h0 = lane * 4; h0 < kp; h0 += 128) {
-      uint32_t word = 0;
+    for (int h0 = lane * 4; h0 < kp; h0 += 256) {
+      double v[8];  // two words of 4 bytes, 128 bytes apart; loads first
 #pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int h = h0 + t;
-        if (h < k) {
-          const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(__ldg(a + h))) & kAbsMask;
-          if (b < kInfBits) word |= ru_e4m3_scaled(b, ep) << (8 * t);
-        }
+      for (int t = 0; t < 8; ++t) {
+        const int h = h0 + (t >> 2) * 128 + (t & 3);
+        v[t] = h < k ? __ldg(a + h) : 0.0;
       }
-      *reinterpret_cast<uint32_t*>(out + h0) = word;
+#pragma unroll
+      for (int g = 0; g < 2; ++g) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const Mag mg = mag_of(v[4 * g + t]);
+          if (!nonfinite(mg)) word |= ru_e4m3_scaled(mg, ep) << (8 * t);
+        }
+        if (h0 + 128 * g < kp) *reinterpret_cast<uint32_t*>(out + h0 + 128 * g) = word;
+      }
     }
   }
 }
@@ -153,31 +170,32 @@ __global__ void __launch_bounds__(256) scale_rows_kernel(const double* __restric
 
 constexpr int kColRows = 256;
 
-// Column maxima of |B| (as ordered IEEE bit patterns) and non-finite flags.  Block
-// (bx, by): columns 256 bx .. 256 bx + 255, rows kColRows by ...
+// Column maxima of |B| (as log2 keys) and non-finite flags.  Block (bx, by): columns
+// 256 bx .. 256 bx + 255, rows rpb by .. rpb by + rpb - 1.
 __device__ __forceinline__ void colmax_body(const double* __restrict__ B, int64_t ldb, int k, int n,
-                                            unsigned long long* __restrict__ colmax, uint32_t* __restrict__ colbad,
-                                            int bx, int by) {
+                                            uint32_t* __restrict__ colmax, uint32_t* __restrict__ colbad, int bx,
+                                            int by, int rpb) {
   const int j = bx * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const int h0 = by * kColRows;
-  const int h1 = min(k, h0 + kColRows);
-  unsigned long long mx = 0;
+  const int h0 = by * rpb;
+  const int h1 = min(k, h0 + rpb);
+  uint32_t key = 0u;
   bool bad = false;
-  for (int h = h0; h < h1; ++h) {
-    const unsigned long long b =
-        static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
-    if (b >= kInfBits) bad = true;
-    else mx = b > mx ? b : mx;
+  for (int h = h0; h < h1; h += 2 * kBatch) {
+    double v[2 * kBatch];  // the loads of a batch are issued before any is used
+#pragma unroll
+    for (int u = 0; u < 2 * kBatch; ++u) v[u] = h + u < h1 ? __ldg(B + static_cast<int64_t>(h + u) * ldb + j) : 0.0;
+#pragma unroll
+    for (int u = 0; u < 2 * kBatch; ++u) key = max(key, log2_key(mag_of(v[u]), bad));
   }
-  if (mx) atomicMax(colmax + j, mx);
+  if (key) atomicMax(colmax + j, key);
   if (bad) atomicOr(colbad + j, 1u);
 }
 
 __global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ B, int64_t ldb, int k, int n,
-                                                     unsigned long long* __restrict__ colmax,
-                                                     uint32_t* __restrict__ colbad) {
-  colmax_body(B, ldb, k, n, colmax, colbad, blockIdx.x, blockIdx.y);
+                                                     uint32_t* __restrict__ colmax, uint32_t* __restrict__ colbad,
+                                                     int rpb) {
+  colmax_body(B, ldb, k, n, colmax, colbad, blockIdx.x, blockIdx.y, rpb);
 }
 
 // Bbar^T (n x kp bytes): thread (column j, 32 consecutive h) writes 32 bytes of row j.
@@ -185,18 +203,18 @@ __global__ void __launch_bounds__(256) colmax_kernel(const double* __restrict__ 
 // part[hb * n + j]; sumsq_reduce_kernel adds the partials of a column in a fixed order.
 template <bool FAST>
 __device__ __forceinline__ void scale_cols_body(const double* __restrict__ B, int64_t ldb, int k, int n, int kp,
-                                                const unsigned long long* __restrict__ colmax,
+                                                const uint32_t* __restrict__ colmax,
                                                 const uint32_t* __restrict__ colbad, int32_t* __restrict__ fprime,
                                                 uint8_t* __restrict__ colstat, uint8_t* __restrict__ BbarT,
                                                 float* __restrict__ part, uint32_t* flags, int bx, int hb) {
   const int j = bx * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  const unsigned long long mx = colmax[j];
+  const uint32_t key = colmax[j];
   const bool bad = colbad[j] != 0;
-  const int fp = (mx == 0) ? 0 : 7 - floor_log2_bits(mx);
+  const int fp = prelim_exponent(key);
   if (hb == 0) {
     fprime[j] = fp;
-    colstat[j] = static_cast<uint8_t>((mx == 0 ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
+    colstat[j] = static_cast<uint8_t>((key == 0u ? kLineZero : 0) | (bad ? kLineNonfinite : 0));
     if (bad) atomicOr(flags, kFlagNonfinite);
   }
   if constexpr (FAST) {
@@ -205,10 +223,9 @@ __device__ __forceinline__ void scale_cols_body(const double* __restrict__ B, in
     for (int t = 0; t < 32; ++t) {
       const int h = hb * 32 + t;
       if (h < k) {
-        const unsigned long long b =
-            static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
-        if (b != 0 && b < kInfBits) {
-          const float v = ru_f32_scaled(b, fp);
+        const Mag mg = mag_of(__ldg(B + static_cast<int64_t>(h) * ldb + j));
+        if (!nonfinite(mg)) {
+          const float v = ru_f32_scaled(mg, fp);
           acc = __fmaf_ru(v, v, acc);
         }
       }
@@ -219,12 +236,18 @@ __device__ __forceinline__ void scale_cols_body(const double* __restrict__ B, in
 #pragma unroll
     for (int q = 0; q < 8; ++q) w[q] = 0;
 #pragma unroll
-    for (int t = 0; t < 32; ++t) {
-      const int h = hb * 32 + t;
-      if (h < k) {
-        const unsigned long long b =
-            static_cast<unsigned long long>(__double_as_longlong(__ldg(B + static_cast<int64_t>(h) * ldb + j))) & kAbsMask;
-        if (b < kInfBits) w[t >> 2] |= ru_e4m3_scaled(b, fp) << (8 * (t & 3));
+    for (int t0 = 0; t0 < 32; t0 += 2 * kBatch) {
+      double v[2 * kBatch];  // loads first
+#pragma unroll
+      for (int u = 0; u < 2 * kBatch; ++u) {
+        const int h = hb * 32 + t0 + u;
+        v[u] = h < k ? __ldg(B + static_cast<int64_t>(h) * ldb + j) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 2 * kBatch; ++u) {
+        const Mag mg = mag_of(v[u]);
+        const int t = t0 + u;
+        if (!nonfinite(mg)) w[t >> 2] |= ru_e4m3_scaled(mg, fp) << (8 * (t & 3));
       }
     }
     uint4* dst = reinterpret_cast<uint4*>(BbarT + static_cast<int64_t>(j) * kp + hb * 32);
@@ -235,7 +258,7 @@ __device__ __forceinline__ void scale_cols_body(const double* __restrict__ B, in
 
 template <bool FAST>
 __global__ void __launch_bounds__(256) scale_cols_kernel(const double* __restrict__ B, int64_t ldb, int k, int n,
-                                                         int kp, const unsigned long long* __restrict__ colmax,
+                                                         int kp, const uint32_t* __restrict__ colmax,
                                                          const uint32_t* __restrict__ colbad,
                                                          int32_t* __restrict__ fprime, uint8_t* __restrict__ colstat,
                                                          uint8_t* __restrict__ BbarT, float* __restrict__ part,
@@ -330,57 +353,44 @@ __global__ void reuse_exponents_kernel(int m, const int32_t* __restrict__ gp, co
 }
 
 // ------------------------------------------------------------------ grouped launches
-// Problem of block `b` of grouped launch `w`: the last p with first_block[w] <= b.
-__device__ __forceinline__ int batch_problem(const BatchProblem* __restrict__ probs, int count, int w, int64_t b) {
-  int lo = 0, hi = count - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (probs[mid].first_block[w] <= b) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
-
 template <bool FAST>
 __global__ void __launch_bounds__(256) scale_rows_batch(const BatchProblem* __restrict__ probs, int count,
-                                                        uint32_t* flags) {
-  const int p = batch_problem(probs, count, kBkScaleRows, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  scale_rows_body<FAST>(P.A, P.lda, P.m, P.k, P.kp, P.eprime, P.rowstat, P.Abar, P.R, flags,
-                        blockIdx.x - P.first_block[kBkScaleRows]);
+                                                        int64_t total, uint32_t* flags) {
+  for_each_vblock(probs, count, kBkScaleRows, total, [&](const BatchProblem& P, int64_t v) {
+    scale_rows_body<FAST>(P.A, P.lda, P.m, P.k, P.kp, P.eprime, P.rowstat, P.Abar, P.R, flags, v);
+  });
 }
 
-__global__ void __launch_bounds__(256) colmax_batch(const BatchProblem* __restrict__ probs, int count) {
-  const int p = batch_problem(probs, count, kBkColmax, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  const int64_t v = blockIdx.x - P.first_block[kBkColmax];
-  const int gx = (P.n + 255) / 256;
-  colmax_body(P.B, P.ldb, P.k, P.n, P.colmaxB, P.colbadB, static_cast<int>(v % gx), static_cast<int>(v / gx));
+__global__ void __launch_bounds__(256) colmax_batch(const BatchProblem* __restrict__ probs, int count,
+                                                    int64_t total) {
+  for_each_vblock(probs, count, kBkColmax, total, [&](const BatchProblem& P, int64_t v) {
+    const int gx = (P.n + 255) / 256;
+    colmax_body(P.B, P.ldb, P.k, P.n, P.colmaxB, P.colbadB, static_cast<int>(v % gx), static_cast<int>(v / gx),
+                kColRows);
+  });
 }
 
 template <bool FAST>
 __global__ void __launch_bounds__(256) scale_cols_batch(const BatchProblem* __restrict__ probs, int count,
-                                                        uint32_t* flags) {
-  const int p = batch_problem(probs, count, kBkScaleCols, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  const int64_t v = blockIdx.x - P.first_block[kBkScaleCols];
-  const int gx = (P.n + 255) / 256;
-  scale_cols_body<FAST>(P.B, P.ldb, P.k, P.n, P.kp, P.colmaxB, P.colbadB, P.fprime, P.colstat, P.BbarT, P.partB,
-                        flags, static_cast<int>(v % gx), static_cast<int>(v / gx));
+                                                        int64_t total, uint32_t* flags) {
+  for_each_vblock(probs, count, kBkScaleCols, total, [&](const BatchProblem& P, int64_t v) {
+    const int gx = (P.n + 255) / 256;
+    scale_cols_body<FAST>(P.B, P.ldb, P.k, P.n, P.kp, P.colmaxB, P.colbadB, P.fprime, P.colstat, P.BbarT, P.partB,
+                          flags, static_cast<int>(v % gx), static_cast<int>(v / gx));
+  });
 }
 
-__global__ void __launch_bounds__(256) sumsq_batch(const BatchProblem* __restrict__ probs, int count) {
-  const int p = batch_problem(probs, count, kBkSumsq, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  sumsq_body(P.partB, P.kp / 32, P.n, P.S, blockIdx.x - P.first_block[kBkSumsq]);
+__global__ void __launch_bounds__(256) sumsq_batch(const BatchProblem* __restrict__ probs, int count, int64_t total) {
+  for_each_vblock(probs, count, kBkSumsq, total, [&](const BatchProblem& P, int64_t v) {
+    sumsq_body(P.partB, P.kp / 32, P.n, P.S, v);
+  });
 }
 
 __global__ void __launch_bounds__(256) exponents_batch(const BatchProblem* __restrict__ probs, int count,
-                                                       float pprime, float delta) {
-  const int p = batch_problem(probs, count, kBkExponents, blockIdx.x);
-  const BatchProblem& P = probs[p];
-  exponents_body(P.m, P.n, P.eprime, P.fprime, P.rowstat, P.colstat, P.R, P.S, pprime, delta, P.e, P.f,
-                 blockIdx.x - P.first_block[kBkExponents]);
+                                                       int64_t total, float pprime, float delta) {
+  for_each_vblock(probs, count, kBkExponents, total, [&](const BatchProblem& P, int64_t v) {
+    exponents_body(P.m, P.n, P.eprime, P.fprime, P.rowstat, P.colstat, P.R, P.S, pprime, delta, P.e, P.f, v);
+  });
 }
 
 bool grid_ok(int64_t blocks) { return blocks > 0 && blocks <= 0x7FFFFFFFll; }
@@ -394,7 +404,7 @@ void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nb)[kB
   nb[kBkScaleCols] = gx * (kp / 32);
   nb[kBkSumsq] = fast ? gx : 0;
   nb[kBkExponents] = (static_cast<int64_t>(m) + n + 255) / 256;
-  nb[kBkResidRows] = (static_cast<int64_t>(m) * ((kp + 255) / 256) + 7) / 8;
+  nb[kBkResidRows] = (resid_rows_items(m, kp) + 7) / 8;
   // one block per tile of the column residue kernel
   nb[kBkResidCols] = static_cast<int64_t>((n + kResidTileCols - 1) / kResidTileCols) *
                      ((kp + kResidTileK - 1) / kResidTileK);
@@ -406,16 +416,17 @@ cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64
   for (int w : {int(kBkScaleRows), int(kBkColmax), int(kBkScaleCols), int(kBkExponents)})
     if (!grid_ok(total[w])) return cudaErrorInvalidValue;
   if (fast && !grid_ok(total[kBkSumsq])) return cudaErrorInvalidValue;
+  const int64_t tr = total[kBkScaleRows], tm = total[kBkColmax], tc = total[kBkScaleCols];
   if (fast)
-    scale_rows_batch<true><<<static_cast<unsigned>(total[kBkScaleRows]), 256, 0, st>>>(probs, count, flags);
+    scale_rows_batch<true><<<grouped_grid(tr, 8), 256, 0, st>>>(probs, count, tr, flags);
   else
-    scale_rows_batch<false><<<static_cast<unsigned>(total[kBkScaleRows]), 256, 0, st>>>(probs, count, flags);
-  colmax_batch<<<static_cast<unsigned>(total[kBkColmax]), 256, 0, st>>>(probs, count);
+    scale_rows_batch<false><<<grouped_grid(tr, 8), 256, 0, st>>>(probs, count, tr, flags);
+  colmax_batch<<<grouped_grid(tm, 8), 256, 0, st>>>(probs, count, tm);
   if (fast) {
-    scale_cols_batch<true><<<static_cast<unsigned>(total[kBkScaleCols]), 256, 0, st>>>(probs, count, flags);
-    sumsq_batch<<<static_cast<unsigned>(total[kBkSumsq]), 256, 0, st>>>(probs, count);
+    scale_cols_batch<true><<<grouped_grid(tc, 8), 256, 0, st>>>(probs, count, tc, flags);
+    sumsq_batch<<<grouped_grid(total[kBkSumsq], 8), 256, 0, st>>>(probs, count, total[kBkSumsq]);
   } else {
-    scale_cols_batch<false><<<static_cast<unsigned>(total[kBkScaleCols]), 256, 0, st>>>(probs, count, flags);
+    scale_cols_batch<false><<<grouped_grid(tc, 8), 256, 0, st>>>(probs, count, tc, flags);
   }
   return cudaGetLastError();
 }
@@ -423,7 +434,7 @@ cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64
 cudaError_t launch_exponents_batch(const BatchProblem* probs, int count, int64_t total_blocks, float pprime,
                                    float delta, cudaStream_t st) {
   if (!grid_ok(total_blocks)) return cudaErrorInvalidValue;
-  exponents_batch<<<static_cast<unsigned>(total_blocks), 256, 0, st>>>(probs, count, pprime, delta);
+  exponents_batch<<<grouped_grid(total_blocks, 8), 256, 0, st>>>(probs, count, total_blocks, pprime, delta);
   return cudaGetLastError();
 }
 
@@ -439,15 +450,22 @@ cudaError_t launch_scale_rows(const double* A, int64_t lda, int m, int k, int kp
   return cudaGetLastError();
 }
 
-cudaError_t launch_colmax(const double* B, int64_t ldb, int k, int n, unsigned long long* colmax,
+cudaError_t launch_colmax(const double* B, int64_t ldb, int k, int n, uint32_t* colmax,
                           uint32_t* colbad, cudaStream_t st) {
-  dim3 grid((n + 255) / 256, (k + kColRows - 1) / kColRows);
-  colmax_kernel<<<grid, 256, 0, st>>>(B, ldb, k, n, colmax, colbad);
+  // rows per block: enough blocks for about four per SM, 16 to kColRows rows each
+  int dev = 0, sms = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t gx = (n + 255) / 256;
+  int64_t rpb = (static_cast<int64_t>(k) * gx + 4 * sms - 1) / (4 * sms);
+  rpb = std::min<int64_t>(kColRows, std::max<int64_t>(16, (rpb + 15) / 16 * 16));
+  dim3 grid(static_cast<unsigned>(gx), static_cast<unsigned>((k + rpb - 1) / rpb));
+  colmax_kernel<<<grid, 256, 0, st>>>(B, ldb, k, n, colmax, colbad, static_cast<int>(rpb));
   return cudaGetLastError();
 }
 
 cudaError_t launch_scale_cols(const double* B, int64_t ldb, int k, int n, int kp,
-                              const unsigned long long* colmax, const uint32_t* colbad,
+                              const uint32_t* colmax, const uint32_t* colbad,
                               int32_t* fprime, uint8_t* colstat, uint8_t* BbarT, float* part, float* sq,
                               bool fast, uint32_t* flags, cudaStream_t st) {
   dim3 grid((n + 255) / 256, kp / 32);
