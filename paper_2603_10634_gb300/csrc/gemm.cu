@@ -119,13 +119,17 @@ __device__ __forceinline__ void decode_unit(int tiles_m, int tiles_n, int tiles,
   tn = r / gsz;
 }
 
-// Everything a role needs about one unit (a tile of one modulus of one problem).
+// Everything a role needs about one unit (a tile of one modulus of one problem).  A
+// role walks its units in increasing order and keeps one UnitCtx across them: in a
+// grouped launch the problem's fields are reloaded only when the problem changes.
 struct UnitCtx {
   const CUtensorMap* ta;
   const CUtensorMap* tb;
   int m, n, k;
   int mod, tm, tn;
-  int prob;
+  int prob = -1;  // grouped: problem of the fields below (-1: none yet)
+  int tiles_m, tiles_n, tiles;
+  int64_t unit_start, next_start;  // grouped: units [unit_start, next_start) are this problem's
   int16_t* cres;
   int64_t ldr, res_stride;
   float factor;
@@ -153,27 +157,35 @@ __device__ __forceinline__ void resolve_unit(const GemmParams& P, const CUtensor
     c.S = P.S;
     c.split = P.split_squares != 0;
   } else {
-    int lo = 0, hi = nprobs - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (probs[mid].unit_start <= u) lo = mid;
-      else hi = mid - 1;
+    if (c.prob < 0 || u >= c.next_start) {
+      // the last problem starting at or before u, searched above the current one
+      int lo = c.prob < 0 ? 0 : c.prob + 1, hi = nprobs - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (probs[mid].unit_start <= u) lo = mid;
+        else hi = mid - 1;
+      }
+      const GemmProblem& G = probs[lo];
+      c.ta = &G.ta;
+      c.tb = &G.tb;
+      c.m = G.m;
+      c.n = G.n;
+      c.k = G.k;
+      c.prob = lo;
+      c.tiles_m = G.tiles_m;
+      c.tiles_n = G.tiles_n;
+      c.tiles = G.tiles;
+      c.unit_start = G.unit_start;
+      c.next_start = lo + 1 < nprobs ? probs[lo + 1].unit_start : 0x7FFFFFFFFFFFFFFFll;
+      c.cres = G.cres;
+      c.ldr = G.ldr;
+      c.res_stride = G.res_stride;
+      c.factor = G.factor;
+      c.R = G.R;
+      c.S = G.S;
+      c.split = G.split != 0;
     }
-    const GemmProblem& G = probs[lo];
-    c.ta = &G.ta;
-    c.tb = &G.tb;
-    c.m = G.m;
-    c.n = G.n;
-    c.k = G.k;
-    c.prob = lo;
-    decode_unit(G.tiles_m, G.tiles_n, G.tiles, static_cast<int>(u - G.unit_start), c.mod, c.tm, c.tn);
-    c.cres = G.cres;
-    c.ldr = G.ldr;
-    c.res_stride = G.res_stride;
-    c.factor = G.factor;
-    c.R = G.R;
-    c.S = G.S;
-    c.split = G.split != 0;
+    decode_unit(c.tiles_m, c.tiles_n, c.tiles, static_cast<int>(u - c.unit_start), c.mod, c.tm, c.tn);
   }
 }
 
@@ -402,8 +414,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       uint32_t issued = 0, issued_phase = 0;
       bool ok = true;
       int last_prob = -1;
+      UnitCtx uc;
       for (int u = u_first; ok && u < prm.num_units; u += u_step) {
-        UnitCtx uc;
         resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
         if (GROUPED && uc.prob != last_prob) {
           tensormap_acquire(uc.ta);
@@ -458,8 +470,8 @@ __global__ void __launch_bounds__(kThreads, 1)
       // an injected stall (fault-injection tests): wait for a barrier nothing arrives at,
       // so this wait runs out and the kernel takes its timeout path
       bool ok = prm.stall ? mbar_wait_bounded(never, 0u, abort_flag, wait_ns) : true;
+      UnitCtx uc;
       for (int u = u_first; ok && u < prm.num_units; u += u_step) {
-        UnitCtx uc;
         resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
         const int mod = uc.mod;
         const UnitPlan up = plan_of<MODE>(uc.k, mod, uc.split);
@@ -541,8 +553,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     (row * BN + chalf * (BN / 2)) / 2;
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
+    UnitCtx uc;
     for (int u = u_first; ok && u < prm.num_units; u += u_step) {
-      UnitCtx uc;
       resolve_unit<GROUPED>(prm, &tmA, &tmB, probs, nprobs, u, uc);
       const int mod = uc.mod, tn = uc.tn;
       const UnitPlan up = plan_of<MODE>(uc.k, mod, uc.split);
