@@ -282,72 +282,84 @@ __device__ __forceinline__ float warp_column_max(float (&v)[32], int lane) {
   return v[0];
 }
 
-// x - p round(x / p) for an exact-integer float |x| <= 2^24, in FP32 without a
-// conversion: the quotient comes from one rounded product (x RN(1/p) is within 0.003 of
-// x / p for p >= 443), so the remainder, formed exactly by one FMA, lies in (-0.51p, 0.51p).
-__device__ __forceinline__ float mod_near_f32(float x, float p, float inv_p) {
-  const float q = __fadd_rn(__fmaf_rn(x, inv_p, 12582912.0f), -12582912.0f);  // 1.5 2^23
-  return __fmaf_rn(-p, q, x);
+// The residue epilogue works on pairs of accumulator columns with packed two-wide FP32
+// instructions (__ffma2_rn / __fadd2_rn / __fmul2_rn round each component like the
+// scalar forms), so its results are those of the element-at-a-time arithmetic below.
+constexpr float kMagic = 12582912.0f;  // 1.5 2^23: y + kMagic rounds y to an integer
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 bits2(uint32_t a, uint32_t b) { return make_float2(__uint_as_float(a), __uint_as_float(b)); }
+
+// Per-modulus constants of the epilogue, as pairs.
+struct ModPair {
+  float2 neg_p, inv_p;
+  bool is1024;  // p = 1024, the even modulus: the last step rounds (r + 1/2) / p
+};
+
+// x - p q for exact-integer floats |x| <= 2^24, q = RN(x RN(1/p)): x RN(1/p) is within
+// 0.003 of x / p for p >= 443, so the remainder, formed exactly by one FMA, lies in
+// (-0.51 p, 0.51 p) and is congruent to x.
+__device__ __forceinline__ float2 mod_near2(float2 x, const ModPair& m) {
+  const float2 q = __fadd2_rn(__ffma2_rn(x, m.inv_p, dup2(kMagic)), dup2(-kMagic));
+  return __ffma2_rn(m.neg_p, q, x);
 }
-// An integer in (-p, p) into the symmetric range [-h, p-1-h].
-__device__ __forceinline__ int sym_fix(int r, int p, int h) {
-  r = (r > p - 1 - h) ? r - p : r;
-  return (r < -h) ? r + p : r;
+// The symmetric remainder, in [-h, p - 1 - h], of exact-integer floats |y| < 2^23: for odd
+// p the rounded quotient is then the nearest integer to y / p (never a tie), for p = 1024
+// q = RN((y + 1/2) / 1024) = floor((y + 512) / 1024) (the product and sum are exact for
+// |y| < 2^12, which holds wherever this form is used: after a first reduction).
+__device__ __forceinline__ float2 smod_small2(float2 y, const ModPair& m) {
+  if (m.is1024) {
+    const float2 t = __ffma2_rn(y, m.inv_p, dup2(0.00048828125f));  // (y + 1/2) / 1024, exact
+    const float2 q = __fadd2_rn(__fadd2_rn(t, dup2(kMagic)), dup2(-kMagic));
+    return __ffma2_rn(m.neg_p, q, y);
+  }
+  return mod_near2(y, m);
 }
-// Karatsuba, second pass: mod(240 d1 - 15 D2, p) from the parked d1 and D2 (|D2| <= 2^24):
-// D2 mod p first keeps 240 d1 - 15 (D2 mod p) below 2^18, exact in FP32.
-__device__ __forceinline__ int kara_v(int d1, uint32_t d2_bits, float pf, float ip, int p, int h) {
-  const float y = __fmaf_rn(-15.0f, mod_near_f32(__uint_as_float(d2_bits), pf, ip), 240.0f * static_cast<float>(d1));
-  return sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
+// The symmetric remainder of exact-integer floats |x| <= 2^24: a first reduction to
+// |r| < 0.51 p, then the exact one.
+__device__ __forceinline__ float2 smod2(float2 x, const ModPair& m) { return smod_small2(mod_near2(x, m), m); }
+
+// Two exact-integer floats |r| < 2^15 as two int16 of one word (first in the low half):
+// the low 16 bits of r + 1.5 2^23 are r in two's complement.
+__device__ __forceinline__ uint32_t pack2(float2 r) {
+  const float2 b = __fadd2_rn(r, dup2(kMagic));
+  return __byte_perm(__float_as_uint(b.x), __float_as_uint(b.y), 0x5410);
 }
-// Karatsuba, third pass: C' = mod(v + 16 D3, p), D3 mod p first (|v + 16 (D3 mod p)| < 2^15).
-__device__ __forceinline__ int kara_c(int v, uint32_t d3_bits, float pf, float ip, int p, int h) {
-  const float y = __fmaf_rn(16.0f, mod_near_f32(__uint_as_float(d3_bits), pf, ip), static_cast<float>(v));
-  return sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
+__device__ __forceinline__ float2 unpack2(uint32_t w) {
+  return make_float2(static_cast<float>(static_cast<int16_t>(w & 0xFFFFu)), static_cast<float>(static_cast<int16_t>(w >> 16)));
 }
 
-// Store 32 int16 residues of one row (adding the previous block's residues when
-// `accumulate`), vectorised when the 32 columns are all inside the matrix.  The debug
-// build checks that every residue lies in the symmetric range [-h, p - 1 - h].
-__device__ __forceinline__ void store_residues(int16_t* dst, int gc, int n, int (&res)[32], bool accumulate,
-                                               int p, int h, uint32_t* flags) {
+// Store 8 int16 residues of one row at columns gc .. gc + 7, packed two per word (adding
+// the previous block's residues when `accumulate`), as one 16-byte store when the 8
+// columns are all inside the matrix.  The debug build checks that every residue lies in
+// the symmetric range [-h, p - 1 - h].
+__device__ __forceinline__ void store_residues8(int16_t* dst, int gc, int n, uint32_t (&pk)[4], bool accumulate,
+                                                int p, int h, uint32_t* flags) {
+  if (accumulate) {
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const int j = gc + 2 * z;
+      const int a = smod_small(static_cast<int16_t>(pk[z] & 0xFFFFu) + (j < n ? dst[j] : 0), p, h);
+      const int b = smod_small(static_cast<int16_t>(pk[z] >> 16) + (j + 1 < n ? dst[j + 1] : 0), p, h);
+      pk[z] = (static_cast<uint32_t>(a) & 0xFFFFu) | (static_cast<uint32_t>(b) << 16);
+    }
+  }
 #ifdef OZK2_DEBUG
   bool in_range = true;
 #pragma unroll
-  for (int j = 0; j < 32; ++j) in_range = in_range && res[j] >= -h && res[j] <= p - 1 - h;
+  for (int z = 0; z < 4; ++z) {
+    const int a = static_cast<int16_t>(pk[z] & 0xFFFFu), b = static_cast<int16_t>(pk[z] >> 16);
+    in_range = in_range && a >= -h && a <= p - 1 - h && b >= -h && b <= p - 1 - h;
+  }
   OZK2_DCHECK(in_range, flags);
 #else
   (void)flags;
 #endif
-  if (gc + 32 <= n) {
-    uint4* o = reinterpret_cast<uint4*>(dst + gc);
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-      if (accumulate) {
-        const uint4 pv = o[w];
-        const uint32_t pr[4] = {pv.x, pv.y, pv.z, pv.w};
-#pragma unroll
-        for (int z = 0; z < 4; ++z) {
-          res[w * 8 + 2 * z] = smod_small(res[w * 8 + 2 * z] + static_cast<int16_t>(pr[z] & 0xFFFFu), p, h);
-          res[w * 8 + 2 * z + 1] = smod_small(res[w * 8 + 2 * z + 1] + static_cast<int16_t>(pr[z] >> 16), p, h);
-        }
-      }
-      uint32_t pk[4];
-#pragma unroll
-      for (int z = 0; z < 4; ++z)
-        pk[z] = (static_cast<uint32_t>(res[w * 8 + 2 * z]) & 0xFFFFu) |
-                (static_cast<uint32_t>(res[w * 8 + 2 * z + 1]) << 16);
-      o[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
+  if (gc + 8 <= n) {
+    *reinterpret_cast<uint4*>(dst + gc) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
   } else {
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (gc + j < n) {
-        int r = res[j];
-        if (accumulate) r = smod_small(r + dst[gc + j], p, h);
-        dst[gc + j] = static_cast<int16_t>(r);
-      }
-    }
+    for (int j = 0; j < 8; ++j)
+      if (gc + j < n) dst[gc + j] = static_cast<int16_t>((j & 1) ? (pk[j >> 1] >> 16) : (pk[j >> 1] & 0xFFFFu));
   }
 }
 
@@ -573,8 +585,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t ts = tq + slot * static_cast<uint32_t>(BN);
           if constexpr (MODE == kModeResidue) {
             const int p = prm.mod.p[mod], h = prm.mod.half[mod], sq = prm.mod.s[mod];
-            const float ip = prm.mod.inv_p[mod];
-            const float pf = static_cast<float>(p);
+            const ModPair mp{dup2(-static_cast<float>(p)), dup2(prm.mod.inv_p[mod]), p == 1024};
             const bool last = ps == up.npasses - 1;
             int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
             // one chunk of 32 columns; sp: this thread's 32 parked int16 of the chunk (two
@@ -603,58 +614,56 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
             auto chunk = [&](int cb, uint32_t* sp) {
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
+              const bool keep = gi < uc.m;  // this thread's row is inside the matrix
               if (pair) {  // square modulus: X in slot 0, Z in slot 1
                 uint32_t vx[32], vz[32];
                 tmem_ld_32cols(tq + cb * 32, vx);
                 tmem_ld_32cols(tq + BN + cb * 32, vz);
                 tmem_ld_wait();
-                // mod(s X + Z, p) in FP32: X mod p first keeps s (X mod p) + Z below 2^24
-                // (|X| <= 2^24, |Z| <= 2^23), so every step is exact; one conversion
-                int res[32];
-                const float sqf = static_cast<float>(sq);
+                // mod(s X + Z, p): X mod p first keeps s (X mod p) + Z below 2^24 (|X| <= 2^24,
+                // |Z| <= 2^23), so every step is exact
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                  const float y = __fmaf_rn(sqf, mod_near_f32(__uint_as_float(vx[j]), pf, ip), __uint_as_float(vz[j]));
-                  res[j] = sym_fix(__float2int_rn(mod_near_f32(y, pf, ip)), p, h);
+                for (int w = 0; w < 4; ++w) {
+                  uint32_t pk[4];
+#pragma unroll
+                  for (int z = 0; z < 4; ++z) {
+                    const int j = 8 * w + 2 * z;
+                    const float2 xr = mod_near2(bits2(vx[j], vx[j + 1]), mp);
+                    const float2 y = __ffma2_rn(dup2(static_cast<float>(sq)), xr, bits2(vz[j], vz[j + 1]));
+                    pk[z] = pack2(smod2(y, mp));
+                  }
+                  if (keep) store_residues8(dst, gc + 8 * w, uc.n, pk, c > 0, p, h, prm.flags);
                 }
-                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
                 return;
               }
               uint32_t v[32];
               tmem_ld_32cols(ts + cb * 32, v);
               tmem_ld_wait();
-              auto lo16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x & 0xFFFFu)); };
-              auto hi16 = [](uint32_t x) { return static_cast<int>(static_cast<int16_t>(x >> 16)); };
-              auto pack = [](int a, int b) { return (static_cast<uint32_t>(a) & 0xFFFFu) | (static_cast<uint32_t>(b) << 16); };
               if (mod < kNumSquares) {  // square modulus in two passes
-                const float sqf = static_cast<float>(sq);
-                if (ps == 0) {  // park x = X mod p (the exact float of mod_near_f32, |x| < 0.51 p)
+                if (ps == 0) {  // park x = X mod p (|x| < 0.51 p)
 #pragma unroll
                   for (int w = 0; w < 4; ++w) {
                     uint32_t pk[4];
 #pragma unroll
-                    for (int z = 0; z < 4; ++z)
-                      pk[z] = pack(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)),
-                                   __float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)));
+                    for (int z = 0; z < 4; ++z) pk[z] = pack2(mod_near2(bits2(v[8 * w + 2 * z], v[8 * w + 2 * z + 1]), mp));
                     store4(sp, w, pk);
                   }
                   return;
                 }
-                int res[32];  // C' = mod(s x + Z, p), as the one-pass form computes it
+                // C' = mod(s x + Z, p), as the one-pass form computes it
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
                   uint32_t pr[4];
                   load4(sp, w, pr);
+                  uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z) {
                     const int j = 8 * w + 2 * z;
-                    const float y0 = __fmaf_rn(sqf, static_cast<float>(lo16(pr[z])), __uint_as_float(v[j]));
-                    const float y1 = __fmaf_rn(sqf, static_cast<float>(hi16(pr[z])), __uint_as_float(v[j + 1]));
-                    res[j] = sym_fix(__float2int_rn(mod_near_f32(y0, pf, ip)), p, h);
-                    res[j + 1] = sym_fix(__float2int_rn(mod_near_f32(y1, pf, ip)), p, h);
+                    const float2 y = __ffma2_rn(dup2(static_cast<float>(sq)), unpack2(pr[z]), bits2(v[j], v[j + 1]));
+                    pk[z] = pack2(smod2(y, mp));
                   }
+                  if (keep) store_residues8(dst, gc + 8 * w, uc.n, pk, c > 0, p, h, prm.flags);
                 }
-                if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
                 return;
               }
               if (ps == 0) {  // Karatsuba pass 1: park d1 = mod(D1, p)
@@ -662,40 +671,43 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int w = 0; w < 4; ++w) {
                   uint32_t pk[4];
 #pragma unroll
-                  for (int z = 0; z < 4; ++z)
-                    pk[z] = pack(sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z]), pf, ip)), p, h),
-                                 sym_fix(__float2int_rn(mod_near_f32(__uint_as_float(v[8 * w + 2 * z + 1]), pf, ip)), p, h));
+                  for (int z = 0; z < 4; ++z) pk[z] = pack2(smod2(bits2(v[8 * w + 2 * z], v[8 * w + 2 * z + 1]), mp));
                   store4(sp, w, pk);
                 }
                 return;
               }
-              if (!last) {  // Karatsuba pass 2: park v = mod(240 d1 - 15 D2, p)
+              if (!last) {  // Karatsuba pass 2: park v = mod(240 d1 - 15 D2, p); D2 mod p first
+                            // keeps |240 d1 - 15 (D2 mod p)| below 2^17
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
                   uint32_t pr[4];
                   load4(sp, w, pr);
                   uint32_t pk[4];
 #pragma unroll
-                  for (int z = 0; z < 4; ++z)
-                    pk[z] = pack(kara_v(lo16(pr[z]), v[8 * w + 2 * z], pf, ip, p, h),
-                                 kara_v(hi16(pr[z]), v[8 * w + 2 * z + 1], pf, ip, p, h));
+                  for (int z = 0; z < 4; ++z) {
+                    const int j = 8 * w + 2 * z;
+                    const float2 d2 = mod_near2(bits2(v[j], v[j + 1]), mp);
+                    const float2 y = __ffma2_rn(dup2(-15.0f), d2, __fmul2_rn(dup2(240.0f), unpack2(pr[z])));
+                    pk[z] = pack2(smod_small2(y, mp));
+                  }
                   store4(sp, w, pk);
                 }
                 return;
               }
-              int res[32];  // Karatsuba pass 3: C' = mod(v + 16 D3, p)
+              // Karatsuba pass 3: C' = mod(v + 16 D3, p); D3 mod p first (|v + 16 (D3 mod p)| < 2^14)
 #pragma unroll
               for (int w = 0; w < 4; ++w) {
                 uint32_t pr[4];
                 load4(sp, w, pr);
+                uint32_t pk[4];
 #pragma unroll
                 for (int z = 0; z < 4; ++z) {
                   const int j = 8 * w + 2 * z;
-                  res[j] = kara_c(lo16(pr[z]), v[j], pf, ip, p, h);
-                  res[j + 1] = kara_c(hi16(pr[z]), v[j + 1], pf, ip, p, h);
+                  const float2 d3 = mod_near2(bits2(v[j], v[j + 1]), mp);
+                  pk[z] = pack2(smod_small2(__ffma2_rn(dup2(16.0f), d3, unpack2(pr[z])), mp));
                 }
+                if (keep) store_residues8(dst, gc + 8 * w, uc.n, pk, c > 0, p, h, prm.flags);
               }
-              if (gi < uc.m) store_residues(dst, gc, uc.n, res, c > 0, p, h, prm.flags);
             };
             if constexpr (REGPARK) {
 #pragma unroll

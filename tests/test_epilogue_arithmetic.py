@@ -140,3 +140,61 @@ def test_library_reciprocals_are_correctly_rounded():
         _, s = oz.modulus_kind(p)
         for v in (p, s):
             assert np.float32(1.0 / v) == oz.f32_round_nearest(Fraction(1, v)), v
+
+
+def _smod_small_step(y, p, inv_p):
+    """The epilogue's exact final reduction of an exact integer |y| < 2^23: one rounded
+    product for odd p, q = RN((y + 1/2) / 1024) for p = 1024 (|y| < 2^12 there)."""
+    if p == 1024:
+        t = oz.f32_round_nearest(Fraction(y, 1024) + Fraction(1, 2048))
+        assert Fraction(float(t)) == Fraction(y, 1024) + Fraction(1, 2048)  # the FMA is exact
+        q = Fraction(float(oz.f32_round_nearest(Fraction(float(t)) + MAGIC))) - MAGIC
+        return y - 1024 * int(q)
+    return _mod_near(y, p, inv_p)
+
+
+def test_epilogue_two_step_reduction_is_the_symmetric_remainder():
+    # smod2: a first reduction of |x| <= 2^24 to |r| < 0.51 p, then the exact step
+    rng = random.Random(13)
+    top = 2**24
+    for p in oz.hybrid_moduli(20):
+        inv_p = oz.f32_round_nearest(Fraction(1, p))
+        h = p // 2
+        xs = [0, 1, -1, top, -top, h, -h, h + 1, -h - 1]
+        xs += [k * p + d for k in (1, 9, 15000, -7, -15000) for d in (h, h + 1, -h, -h - 1, p - 1 - h)]
+        xs += [rng.randint(-top, top) for _ in range(300)]
+        for x in xs:
+            r1 = _mod_near(x, p, inv_p)
+            assert abs(r1) < 2**12
+            assert _smod_small_step(r1, p, inv_p) == oz.smod(x, p), (p, x)
+
+
+def test_epilogue_karatsuba_steps_are_exact():
+    # pass 2: y = 240 d1 - 15 (D2 mod_near) with |d1| <= h; pass 3: y = v + 16 (D3 mod_near);
+    # both below 2^23, so the single final step gives the symmetric remainder
+    rng = random.Random(17)
+    for p in oz.hybrid_moduli(20):
+        kind, _ = oz.modulus_kind(p)
+        if kind == "square":
+            continue
+        inv_p = oz.f32_round_nearest(Fraction(1, p))
+        h = p // 2
+        for _ in range(300):
+            d1 = rng.randint(-h, p - 1 - h)
+            D2 = rng.randint(-2**24, 2**24)
+            d2 = _mod_near(D2, p, inv_p)
+            y = 240 * d1 - 15 * d2
+            assert abs(y) < 2**17
+            assert _smod_small_step(y, p, inv_p) == oz.smod(240 * d1 - 15 * D2, p)
+            D3 = rng.randint(-2**24, 2**24)
+            y3 = d1 + 16 * _mod_near(D3, p, inv_p)
+            assert abs(y3) < 2**14
+            assert _smod_small_step(y3, p, inv_p) == oz.smod(d1 + 16 * D3, p)
+
+
+def test_epilogue_int16_packing_by_magic_bias():
+    # r + 1.5 2^23 is exact for |r| < 2^22; its low 16 bits are r in two's complement
+    for r in [0, 1, -1, 511, -512, 544, -544, 2**15 - 1, -2**15] + list(range(-600, 600, 37)):
+        b = np.array([np.float32(r) + np.float32(1.5 * 2**23)], dtype=np.float32).view(np.uint32)[0]
+        assert np.float32(r) + np.float32(1.5 * 2**23) == np.float32(r + 1.5 * 2**23)
+        assert np.int16(np.uint16(int(b) & 0xFFFF)) == r
