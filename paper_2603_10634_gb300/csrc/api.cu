@@ -184,7 +184,7 @@ struct Layout {
   int planes;
   size_t flags, R, S, colmaxA, colbadA, colmaxB, colbadB, zero_end;
   size_t eprime, fprime, e, f, rowstat, colstat;
-  size_t Abar, BbarT, partA, partB, planesA, planesB, cres, scratch, total;
+  size_t Abar, BbarT, partA, partB, planesA, planesB, cres, total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -222,7 +222,6 @@ Layout make_layout(int64_t m, int64_t n, int64_t k, int N, bool fast) {
   L.planesA = take(size_t(L.planes) * m * L.ldp);
   L.planesB = take(size_t(L.planes) * n * L.ldp);
   L.cres = take(2 * size_t(N) * m * L.ldr);
-  L.scratch = take(fp8_gemm_scratch_bytes(kMaxGemmCtas));
   L.total = o;
   return L;
 }
@@ -462,7 +461,6 @@ ozk2_status products_rows(Ctx& c, int64_t i0, int rows, cudaStream_t st) {
   g.cres = c.at<int16_t>(L.cres) + i0 * L.ldr;
   g.ldr = L.ldr;
   g.res_stride = int64_t(c.m) * L.ldr;
-  g.scratch = c.at<uint32_t>(L.scratch);
   g.mt = &c.tab->mt;
   g.flags = c.at<uint32_t>(L.flags);
   g.plane_stride_a = int64_t(c.m) * L.ldp;
@@ -874,7 +872,7 @@ struct BwLayout {
   int planes;
   size_t flags, R, S, Rk, Sk, colmaxA, colbadA, colmaxC, colbadC, zk, zero_end;
   size_t gp, hp, g, h, t, tA, rstatC, cstatC, rstatB, cstatA;
-  size_t Gbar, Bhat, AhatT, HhatT, planesG, planesBT, planesAT, planesH, cresA, cresB, scratch, total;
+  size_t Gbar, Bhat, AhatT, HhatT, planesG, planesBT, planesAT, planesH, cresA, cresB, total;
 };
 
 BwLayout make_bw_layout(int64_t m, int64_t n, int64_t k, int N) {
@@ -921,7 +919,6 @@ BwLayout make_bw_layout(int64_t m, int64_t n, int64_t k, int N) {
   L.planesH = take(size_t(L.planes) * n * L.mp);
   L.cresA = take(2 * size_t(N) * m * L.ldrk);
   L.cresB = take(2 * size_t(N) * k * L.ldrn);
-  L.scratch = take(fp8_gemm_scratch_bytes(kMaxGemmCtas));
   L.total = o;
   return L;
 }
@@ -950,7 +947,7 @@ cudaError_t bw_bound(const Ctx& c, const uint8_t* a, const uint8_t* b, int64_t p
 // Residue products of one gradient: `planes` planes of a (rows lines) and b (cols lines),
 // contraction len, row pitch `pitch`, into cres (N x rows x ldr).
 cudaError_t bw_products(const Ctx& c, const uint8_t* a, const uint8_t* b, int64_t pitch, int rows, int cols, int len,
-                        int16_t* cres, int64_t ldr, uint32_t* scratch, uint32_t* flags) {
+                        int16_t* cres, int64_t ldr, uint32_t* flags) {
   GemmArgs g{};
   g.mode = kModeResidue;
   g.m = rows;
@@ -960,7 +957,6 @@ cudaError_t bw_products(const Ctx& c, const uint8_t* a, const uint8_t* b, int64_
   g.cres = cres;
   g.ldr = ldr;
   g.res_stride = int64_t(rows) * ldr;
-  g.scratch = scratch;
   g.mt = &c.tab->mt;
   g.flags = flags;
   g.plane_stride_a = int64_t(rows) * pitch;
@@ -1046,12 +1042,11 @@ ozk2_status run_backward(int64_t m, int64_t n, int64_t k, const double* A, int64
   OZK2_TRY(launch_grad_residues(dC, lddc, c.m, c.n, g, f, h, e, wantA ? at(L.planesG) : nullptr, L.np,
                                 wantB ? at(L.planesH) : nullptr, L.mp, c.tab->mt, flags, st));
   t_launches += 2;
-  uint32_t* scratch = reinterpret_cast<uint32_t*>(at(L.scratch));
   if (wantA) {
     OZK2_TRY(launch_transpose_planes(planesB, FL.ldp, int64_t(n) * FL.ldp, c.n, c.k, at(L.planesBT), L.np,
                                      int64_t(k) * L.np, P, st));
     OZK2_TRY(bw_products(c, at(L.planesG), at(L.planesBT), L.np, c.m, c.k, c.n,
-                         reinterpret_cast<int16_t*>(at(L.cresA)), L.ldrk, scratch, flags));
+                         reinterpret_cast<int16_t*>(at(L.cresA)), L.ldrk, flags));
     OZK2_TRY(launch_crt(reinterpret_cast<int16_t*>(at(L.cresA)), L.ldrk, int64_t(m) * L.ldrk, c.m, c.k, g, zk,
                         at(L.rstatC), at(L.rstatB), dA, ldda, c.tab->ct, st));
     t_launches += 2;
@@ -1060,7 +1055,7 @@ ozk2_status run_backward(int64_t m, int64_t n, int64_t k, const double* A, int64
     OZK2_TRY(launch_transpose_planes(planesA, FL.ldp, int64_t(m) * FL.ldp, c.m, c.k, at(L.planesAT), L.mp,
                                      int64_t(k) * L.mp, P, st));
     OZK2_TRY(bw_products(c, at(L.planesAT), at(L.planesH), L.mp, c.k, c.n, c.m,
-                         reinterpret_cast<int16_t*>(at(L.cresB)), L.ldrn, scratch, flags));
+                         reinterpret_cast<int16_t*>(at(L.cresB)), L.ldrn, flags));
     OZK2_TRY(launch_crt(reinterpret_cast<int16_t*>(at(L.cresB)), L.ldrn, int64_t(k) * L.ldrn, c.k, c.n, zk, h,
                         at(L.cstatA), at(L.cstatC), dB, lddb, c.tab->ct, st));
     t_launches += 2;
@@ -1079,7 +1074,7 @@ struct ZeroK {
 };
 
 struct BatchLayout {
-  size_t flags, probs, gbound, gres, zero_begin, zero_end, scratch, total;
+  size_t flags, probs, gbound, gres, zero_begin, zero_end, total;
 };
 
 }  // namespace
@@ -1191,7 +1186,6 @@ BatchLayout batch_layout(int count, const int64_t* m, const int64_t* n, const in
     }
     ++j;
   }
-  L.scratch = take(fp8_gemm_scratch_bytes(kMaxGemmCtas));
   L.total = o;
   return L;
 }
@@ -1410,7 +1404,6 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
                                  flags, st));
   g.mode = kModeResidue;
   g.mt = &tab->mt;
-  g.scratch = reinterpret_cast<uint32_t*>(ws + L.scratch);
   if (!launch_controls(g)) return OZK2_ERR_CUDA;
   OZK2_TRY(launch_fp8_gemm_grouped(g, reinterpret_cast<const GemmProblem*>(ws + L.gres), plan->cnt, plan->units_res,
                                    st));

@@ -4,17 +4,20 @@
 //   C'_ij = mod(sum_l w_l C'_l,ij, P),  w_l = q_l P / p_l,  symmetric in [-P/2, P/2)
 //   C_ij  = RN(C'_ij 2^-(e_i + f_j))
 //
-// The sum is formed exactly in integer arithmetic: with u_l = C'_l mod p_l in [0, p_l)
-// and the weights split into 32-bit limbs, limb t of sum_l u_l w_l accumulates in a
-// 64-bit integer (each term < 2^43, N <= 20 terms, sum < 2^48), one wide multiply-add
-// per limb.
-// The quotient Q = round(V / P) comes from the fixed-point estimate
-// sum_l u_l round(2^16 w_l / P) (error < 0.17); V - Q P is normalised to L signed
-// 32-bit limbs.  When the estimate is at least 0.3 away from a rounding boundary the
-// result is already in [-P/2, P/2); otherwise one exact comparison with +-P/2 corrects
-// it.  The double is then assembled bit by bit with round-to-nearest-even at the right
-// position, which gives the correctly rounded value including gradual underflow and
-// overflow to infinity.  No FP64 arithmetic is used.
+// The sum is formed exactly in integer arithmetic from the signed residues c_l in
+// [-p_l/2, p_l/2): sum_l c_l w_l differs from the sum over the non-negative residues by
+// multiples of p_l w_l = q_l P, so it is the same mod P.  The weights are split into
+// balanced 32-bit limbs (each in [-2^31, 2^31)), and limb t of sum_l c_l w_l accumulates
+// in a 64-bit integer (each term below 2^46 in magnitude, N <= 20 terms), one signed wide
+// multiply-add per limb.  The quotient Q = round(V / P) comes from the fixed-point
+// estimate sum_l c_l round(2^16 w_l / P) (error below 0.05); V - Q P is normalised to L
+// signed 32-bit limbs.  When the estimate is at least 0.3 away from a rounding boundary
+// the result is already in [-P/2, P/2); otherwise one exact comparison with +-P/2
+// corrects it.  The double is then assembled bit by bit with round-to-nearest-even at the
+// right position, which gives the correctly rounded value including gradual underflow
+// and overflow to infinity: for a normal result from more than 53 bits (the common case)
+// from a 96-bit window at the leading limb, otherwise bit by bit over all limbs.  No FP64
+// arithmetic is used.
 #include "device.cuh"
 
 namespace ozk2 {
@@ -73,11 +76,38 @@ __device__ __forceinline__ double crt_finish(uint32_t (&v)[L], bool exact_check,
       c = s >> 32;
     }
   }
-  int nbits = 0;
+  // the top nonzero limb, the two below it and whether anything lies lower still
+  uint32_t top = 0u, mid = 0u, low = 0u, rest = 0u, below = 0u;  // below: OR of v[0 .. t - 3]
+  int ti = -1;
 #pragma unroll
-  for (int t = L - 1; t >= 0; --t)
-    if (nbits == 0 && v[t] != 0) nbits = 32 * t + 32 - __clz(v[t]);
-  if (nbits == 0) return 0.0;
+  for (int t = 0; t < L; ++t) {
+    if (v[t] != 0u) {
+      top = v[t];
+      mid = t >= 1 ? v[t >= 1 ? t - 1 : 0] : 0u;
+      low = t >= 2 ? v[t >= 2 ? t - 2 : 0] : 0u;
+      rest = below;
+      ti = t;
+    }
+    if (t >= 2) below |= v[t >= 2 ? t - 2 : 0];
+  }
+  if (ti < 0) return 0.0;
+  const int nbits = 32 * ti + 32 - __clz(top);
+  if (nbits > 53 && nbits - 53 >= scale - 1074) {
+    // the common case, a normal result from more than 53 bits: the 96-bit window
+    // (top : mid : low) shifted left to its leading one holds the 53 significand bits,
+    // the round bit and most of the sticky bits
+    const int sh = __clz(top);
+    const uint32_t w2 = __funnelshift_l(mid, top, sh), w1 = __funnelshift_l(low, mid, sh), w0 = low << sh;
+    uint64_t mant = (static_cast<uint64_t>(w2) << 21) | (w1 >> 11);
+    const bool round_bit = (w1 >> 10) & 1u;
+    const bool sticky = ((w1 & 0x3FFu) | w0 | rest) != 0u;
+    if (round_bit && (sticky || (mant & 1ull))) mant += 1;
+    const int ebias = nbits - 53 - scale + 1074;  // exponent field before the implicit bit
+    uint64_t bits = (ebias >= 2047) ? 0x7FF0000000000000ull : (static_cast<uint64_t>(ebias) << 52) + mant;
+    if ((bits >> 52) >= 2047) bits = 0x7FF0000000000000ull;
+    if (neg) bits |= 0x8000000000000000ull;
+    return __longlong_as_double(static_cast<long long>(bits));
+  }
   // position (bit index of C') of the result's last significand bit
   const int rpos = max(nbits - 53, scale - 1074);
   uint64_t mant;
@@ -142,23 +172,23 @@ __device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64
     }
     const int j0 = jq * 2;
     const int16_t* src = cres + static_cast<int64_t>(i) * ldr + j0;
-    uint64_t acc[2][L];
-    uint32_t est[2] = {0u, 0u};
+    // sum_l C'_l w_l with the signed residues: it differs from the sum over the residues
+    // made non-negative by multiples of p_l w_l = q_l P, so it is the same mod P
+    int64_t acc[2][L];
+    int32_t est[2] = {0, 0};
 #pragma unroll
     for (int z = 0; z < 2; ++z)
 #pragma unroll
-      for (int t = 0; t < L; ++t) acc[z][t] = 0ull;
+      for (int t = 0; t < L; ++t) acc[z][t] = 0;
 #pragma unroll
     for (int l = 0; l < N; ++l) {
-      const int p = ct.p[l];
       const uint32_t raw = __ldg(reinterpret_cast<const unsigned int*>(src + static_cast<int64_t>(l) * rstride));
       const int cz[2] = {static_cast<int16_t>(raw & 0xFFFFu), static_cast<int16_t>(raw >> 16)};
 #pragma unroll
       for (int z = 0; z < 2; ++z) {
-        const uint32_t u = static_cast<uint32_t>(cz[z] < 0 ? cz[z] + p : cz[z]);
 #pragma unroll
-        for (int t = 0; t < L; ++t) acc[z][t] += static_cast<uint64_t>(u) * ct.w32[l][t];
-        est[z] += u * ct.frac16[l];
+        for (int t = 0; t < L; ++t) acc[z][t] += static_cast<int64_t>(cz[z]) * ct.wb[l][t];
+        est[z] += cz[z] * ct.frac16[l];
       }
     }
     const int ei = e[i];
@@ -168,17 +198,16 @@ __device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64
     for (int z = 0; z < 2; ++z) {
       const int j = j0 + z;
       if (j < n) {
-        // Q = round(est / 2^16); est / 2^16 is within 0.17 of V / P
-        const uint32_t q = (est[z] + 0x8000u) >> 16;
-        const int32_t off = static_cast<int32_t>(est[z] - (q << 16));  // in [-2^15, 2^15)
-        const bool exact_check = (off > 19660 || off < -19660);        // |est - Q| > 0.3
+        // Q = round(est / 2^16); est / 2^16 is within 0.05 of V / P
+        const int32_t q = (est[z] + 0x8000) >> 16;                  // arithmetic shift: floor
+        const int32_t off = est[z] - q * 65536;                      // in [-2^15, 2^15)
+        const bool exact_check = (off > 19660 || off < -19660);      // |est - Q| > 0.3
         // v = V - Q P from the 64-bit limb sums, normalised to 32-bit limbs
         uint32_t v[L];
         int64_t carry = 0;
 #pragma unroll
         for (int t = 0; t < L; ++t) {
-          const int64_t x = carry + static_cast<int64_t>(acc[z][t]) -
-                            static_cast<int64_t>(static_cast<uint64_t>(q) * ct.P[t]);
+          const int64_t x = carry + acc[z][t] - static_cast<int64_t>(q) * static_cast<int64_t>(ct.P[t]);
           v[t] = static_cast<uint32_t>(x);
           carry = x >> 32;  // arithmetic: signed carry
         }

@@ -27,8 +27,8 @@
 //                    D1, park d1 = mod(D1, p); D2, park v = mod(240 d1 - 15 D2, p);
 //                    D3, C'_l = mod(v + 16 D3, p)  (256 D1 + D2 + 16 (D3 - D1 - D2)
 //                    = 240 D1 - 15 D2 + 16 D3; every operand of mod is below 2^28).
-// Parked values are int16 in a CTA-private scratch tile (L2-resident).  The
-// bound and raw products are one single-slot pass per unit.  The wide tile halves the
+// Parked values are int16 pairs in the epilogue threads' registers (every pass of a
+// unit gives a thread the same row and columns).  The bound and raw products are one single-slot pass per unit.  The wide tile halves the
 // operand bytes each SM pulls per flop compared with 128 x 128.
 //
 // Roles (320 threads, one persistent CTA per SM):
@@ -52,7 +52,6 @@ namespace ozk2 {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BNMAX = 256;  // the wider of the two tile widths (scratch is sized for it)
 constexpr int BK = 128;  // bytes = FP8 elements per k-step (one 128-byte swizzle row)
 constexpr int kATileBytes = BM * BK;  // 16 KiB
 constexpr int kEpiWarps = 8;
@@ -89,7 +88,6 @@ struct GemmParams {
   int16_t* cres;
   int64_t ldr;
   int64_t res_stride;
-  uint32_t* scratch;  // residue mode: BM x BNMAX words per CTA
   EpiMod mod;
   float factor;
   float* R;
@@ -364,8 +362,7 @@ __device__ __forceinline__ void store_residues8(int16_t* dst, int gc, int n, uin
 }
 
 // GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).  TN: tile width.
-// REGPARK: residues parked between passes in registers (see the epilogue).
-template <int MODE, bool GROUPED, int TN, bool REGPARK>
+template <int MODE, bool GROUPED, int TN>
 __global__ void __launch_bounds__(kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ GemmParams prm, const GemmProblem* __restrict__ probs, int nprobs) {
@@ -555,14 +552,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
     // Residues kept between the passes of a unit (Karatsuba d1, then v; the X residue of
     // a two-pass square modulus), 32 int16 per chunk of 32 columns, two per word.  Every
-    // pass of a unit gives this thread the same row and the same BN / 2 columns, so with
-    // REGPARK they stay in registers (the chunk loop unrolled); otherwise they go to the
-    // CTA's scratch tile in L2 (BM x BN int16), which keeps the rolled epilogue small:
-    // the unrolled one is faster with long reductions (no parking traffic leaving L2)
-    // and slower with short ones.
-    uint32_t park[REGPARK ? BN / 64 : 1][16];
-    uint32_t* scr = reinterpret_cast<uint32_t*>(prm.scratch + static_cast<int64_t>(blockIdx.x) * (BM * BNMAX)) +
-                    (row * BN + chalf * (BN / 2)) / 2;
+    // pass of a unit gives this thread the same row and the same BN / 2 columns, so they
+    // stay in registers (the chunk loop unrolled).  An earlier form parked them in a
+    // CTA-private scratch tile in L2; its round trips made short reductions up to 14%
+    // slower.
+    uint32_t park[MODE == kModeResidue ? BN / 64 : 1][16];
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
     UnitCtx uc;
@@ -588,29 +582,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             const ModPair mp{dup2(-static_cast<float>(p)), dup2(prm.mod.inv_p[mod]), p == 1024};
             const bool last = ps == up.npasses - 1;
             int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
-            // one chunk of 32 columns; sp: this thread's 32 parked int16 of the chunk (two
-            // per word), in registers (REGPARK) or in the CTA's scratch tile
-            // words 4w .. 4w + 3 of a chunk's parked values: registers, or one 16-byte
-            // access of the scratch tile (16-byte aligned: 64-byte rows of the tile)
+            // one chunk of 32 columns; sp: this thread's 32 parked int16 of the chunk, two per
+            // word (registers: every index below is known at compile time)
             auto store4 = [](uint32_t* sp, int w, const uint32_t (&pk)[4]) {
-              if constexpr (REGPARK) {
 #pragma unroll
-                for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
-              } else {
-                reinterpret_cast<uint4*>(sp)[w] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-              }
+              for (int z = 0; z < 4; ++z) sp[4 * w + z] = pk[z];
             };
             auto load4 = [](const uint32_t* sp, int w, uint32_t (&pr)[4]) {
-              if constexpr (REGPARK) {
 #pragma unroll
-                for (int z = 0; z < 4; ++z) pr[z] = sp[4 * w + z];
-              } else {
-                const uint4 v4 = reinterpret_cast<const uint4*>(sp)[w];
-                pr[0] = v4.x;
-                pr[1] = v4.y;
-                pr[2] = v4.z;
-                pr[3] = v4.w;
-              }
+              for (int z = 0; z < 4; ++z) pr[z] = sp[4 * w + z];
             };
             auto chunk = [&](int cb, uint32_t* sp) {
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
@@ -709,13 +689,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (keep) store_residues8(dst, gc + 8 * w, uc.n, pk, c > 0, p, h, prm.flags);
               }
             };
-            if constexpr (REGPARK) {
 #pragma unroll
-              for (int cb = 0; cb < BN / 64; ++cb) chunk(cb, park[cb]);
-            } else {
-#pragma unroll 1
-              for (int cb = 0; cb < BN / 64; ++cb) chunk(cb, scr + cb * 16);
-            }
+            for (int cb = 0; cb < BN / 64; ++cb) chunk(cb, park[cb]);
           } else if constexpr (MODE == kModeBound) {
             float rmax = 0.0f;
             // 2^-s for an integer s clamped to [-126, 126] (an upper bound of 2^-s for
@@ -791,7 +766,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-template <int MODE, bool GROUPED, int TN, bool REGPARK>
+template <int MODE, bool GROUPED, int TN>
 cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
                         const GemmProblem* probs, int nprobs, cudaStream_t st) {
   static bool configured[64] = {false};
@@ -799,30 +774,21 @@ cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUte
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !configured[dev]) {
-    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED, TN, REGPARK>,
+    cudaError_t err = cudaFuncSetAttribute(fp8_gemm_kernel<MODE, GROUPED, TN>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (err != cudaSuccess) return err;
     configured[dev] = true;
   }
-  fp8_gemm_kernel<MODE, GROUPED, TN, REGPARK><<<grid, kThreads, smem, st>>>(ta, tb, prm, probs, nprobs);
+  fp8_gemm_kernel<MODE, GROUPED, TN><<<grid, kThreads, smem, st>>>(ta, tb, prm, probs, nprobs);
   return cudaGetLastError();
 }
 
 template <int MODE, bool GROUPED>
-cudaError_t launch_tile(int tn, bool regpark, const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb,
-                        int grid, const GemmProblem* probs, int nprobs, cudaStream_t st) {
-  if constexpr (MODE == kModeResidue && !GROUPED) {
-    if (regpark) {
-      if (tn == 128) return launch_mode<MODE, GROUPED, 128, true>(prm, ta, tb, grid, probs, nprobs, st);
-      return launch_mode<MODE, GROUPED, 256, true>(prm, ta, tb, grid, probs, nprobs, st);
-    }
-  }
-  if (tn == 128) return launch_mode<MODE, GROUPED, 128, false>(prm, ta, tb, grid, probs, nprobs, st);
-  return launch_mode<MODE, GROUPED, 256, false>(prm, ta, tb, grid, probs, nprobs, st);
+cudaError_t launch_tile(int tn, const GemmParams& prm, const CUtensorMap& ta, const CUtensorMap& tb, int grid,
+                        const GemmProblem* probs, int nprobs, cudaStream_t st) {
+  if (tn == 128) return launch_mode<MODE, GROUPED, 128>(prm, ta, tb, grid, probs, nprobs, st);
+  return launch_mode<MODE, GROUPED, 256>(prm, ta, tb, grid, probs, nprobs, st);
 }
-
-// Reductions at least this long park residues in registers (single problems).
-constexpr int kRegParkMinK = 8192;
 
 int tile_width(int tile_n) { return tile_n == 128 ? 128 : 256; }
 
@@ -836,8 +802,6 @@ void fill_mod(GemmParams& prm, const ModTable& mt) {
 }
 
 }  // namespace
-
-size_t fp8_gemm_scratch_bytes(int num_ctas) { return static_cast<size_t>(num_ctas) * BM * BNMAX * 4; }
 
 cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a, const uint8_t* b,
                             int64_t ldb8, int planes_b, cudaStream_t st) {
@@ -855,11 +819,7 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   prm.cres = g.cres;
   prm.ldr = g.ldr;
   prm.res_stride = g.res_stride;
-  prm.scratch = g.scratch;
-  if (g.mode == kModeResidue) {
-    fill_mod(prm, *g.mt);
-    if (!g.scratch) return cudaErrorInvalidValue;
-  }
+  if (g.mode == kModeResidue) fill_mod(prm, *g.mt);
   prm.factor = g.factor;
   prm.R = g.R;
   prm.S = g.S;
@@ -879,11 +839,11 @@ cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, i
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   switch (g.mode) {
     case kModeResidue:
-      return launch_tile<kModeResidue, false>(BN, g.k >= kRegParkMinK, prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeResidue, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
     case kModeBound:
-      return launch_tile<kModeBound, false>(BN, false, prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeBound, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
     default:
-      return launch_tile<kModeRaw, false>(BN, false, prm, ta, tb, grid, nullptr, 0, st);
+      return launch_tile<kModeRaw, false>(BN, prm, ta, tb, grid, nullptr, 0, st);
   }
 }
 
@@ -914,22 +874,18 @@ cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs,
   GemmParams prm{};
   prm.mode = g.mode;
   prm.num_units = static_cast<int>(total_units);
-  prm.scratch = g.scratch;
   prm.flags = g.flags;
   prm.wait_ns = g.wait_ns;
   prm.stall = g.stall ? 1 : 0;
-  if (g.mode == kModeResidue) {
-    fill_mod(prm, *g.mt);
-    if (!g.scratch) return cudaErrorInvalidValue;
-  }
+  if (g.mode == kModeResidue) fill_mod(prm, *g.mt);
   CUtensorMap unused;
   std::memset(&unused, 0, sizeof(unused));
   const int ctas = g.num_sms < kMaxGemmCtas ? g.num_sms : kMaxGemmCtas;
   const int grid = prm.num_units < ctas ? prm.num_units : ctas;
   const int BN = tile_width(g.tile_n);
   if (g.mode == kModeResidue)
-    return launch_tile<kModeResidue, true>(BN, false, prm, unused, unused, grid, probs, count, st);
-  return launch_tile<kModeBound, true>(BN, false, prm, unused, unused, grid, probs, count, st);
+    return launch_tile<kModeResidue, true>(BN, prm, unused, unused, grid, probs, count, st);
+  return launch_tile<kModeBound, true>(BN, prm, unused, unused, grid, probs, count, st);
 }
 
 }  // namespace ozk2

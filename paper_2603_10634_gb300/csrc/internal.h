@@ -48,8 +48,9 @@ struct CrtTable {
   int N;
   int limbs;                               // L, 32-bit limbs of the signed result
   int p[kMaxModuli];
-  uint32_t w32[kMaxModuli][kMaxLimbs];     // q_l P / p_l mod P in 32-bit limbs
-  uint32_t frac16[kMaxModuli];             // round(2^16 w_l / P) (quotient estimate)
+  int32_t wb[kMaxModuli][kMaxLimbs];       // w_l = q_l P / p_l mod P in balanced 32-bit limbs:
+                                           // w_l = sum_t wb[l][t] 2^(32 t), wb in [-2^31, 2^31)
+  int32_t frac16[kMaxModuli];              // round(2^16 w_l / P) (quotient estimate)
   uint32_t P[kMaxLimbs];
   uint32_t halfP[kMaxLimbs];               // P / 2 (P is even: 1024 is a modulus)
 };
@@ -141,7 +142,6 @@ struct GemmArgs {
   int16_t* cres;
   int64_t ldr;          // int16 elements per row of a residue plane
   int64_t res_stride;   // elements between residue planes
-  uint32_t* scratch;    // fp8_gemm_scratch_bytes(num_sms) bytes, residue products only
   const ModTable* mt;
   // bound product
   float factor;
@@ -164,8 +164,7 @@ struct GemmArgs {
 };
 // A operand: `planes_a` digit planes (K-major, m x k bytes, row stride lda8 bytes, plane
 // stride plane_stride_a); B operand the same with n rows.
-constexpr int kMaxGemmCtas = 192;  // persistent GEMM CTAs (scratch is sized for this many)
-size_t fp8_gemm_scratch_bytes(int num_ctas);
+constexpr int kMaxGemmCtas = 192;  // persistent GEMM CTAs at most
 cudaError_t launch_fp8_gemm(const GemmArgs& g, const uint8_t* a, int64_t lda8, int planes_a,
                             const uint8_t* b, int64_t ldb8, int planes_b, cudaStream_t st);
 
@@ -278,7 +277,7 @@ struct GemmProblem {  // CUtensorMap carries the 64-byte alignment TMA needs
 };
 // Units of one problem in a GEMM of mode `mode` with N moduli and tiles of width tile_n.
 int64_t fp8_gemm_units(int mode, int m, int n, int N, int tile_n);
-// g supplies mode, num_sms, scratch, mt and flags; the problems (device memory, built on
+// g supplies mode, num_sms, mt and flags; the problems (device memory, built on
 // the host with encode_gemm_problem) supply everything else.
 cudaError_t launch_fp8_gemm_grouped(const GemmArgs& g, const GemmProblem* probs, int count, int64_t total_units,
                                     cudaStream_t st);

@@ -204,10 +204,18 @@ bool build_crt_table(int N, CrtTable* ct) {
     div_small(Pl, static_cast<uint32_t>(p), &rem);
     const int q = modinv(static_cast<int>(rem), p);
     const Big w = mul_small(Pl, static_cast<uint32_t>(q));  // < P, already reduced
-    for (size_t t = 0; t < w.size() && t < static_cast<size_t>(kMaxLimbs); ++t) ct->w32[l][t] = w[t];
+    // balanced limbs: a limb of 2^31 or more becomes limb - 2^32 and carries 1 upwards
+    int64_t carry = 0;
+    for (int t = 0; t < limbs; ++t) {
+      int64_t u = (t < static_cast<int>(w.size()) ? static_cast<int64_t>(w[t]) : 0) + carry;
+      carry = u >= (int64_t(1) << 31) ? 1 : 0;
+      u -= carry << 32;
+      ct->wb[l][t] = static_cast<int32_t>(u);
+    }
+    if (carry != 0) return false;  // w_l < P < 2^(32 L - 1): the top limb never carries out
     int ew;
     const double wtop = w.empty() ? 0.0 : top_as_double(w, &ew);
-    ct->frac16[l] = w.empty() ? 0u : static_cast<uint32_t>(std::llround(std::ldexp(wtop / Ptop, ew - eP + 16)));
+    ct->frac16[l] = w.empty() ? 0 : static_cast<int32_t>(std::llround(std::ldexp(wtop / Ptop, ew - eP + 16)));
   }
   for (size_t t = 0; t < P.size(); ++t) ct->P[t] = P[t];
   uint32_t dummy;

@@ -114,10 +114,11 @@ def test_residue_kernel_quotient_is_the_nearest_integer():
 
 
 def test_crt_quotient_estimate_bound():
-    # The CRT kernel estimates Q = round(V / P), V = sum_l u_l w_l with u_l in [0, p_l),
-    # from est = sum_l u_l round(2^16 w_l / P) in a 32-bit integer: the estimate is within
-    # 0.17 of V / P (so a fractional part at least 0.3 from one half decides the
-    # rounding, and the rarer cases take the exact comparison) and est never overflows.
+    # The CRT kernel estimates Q = round(V / P), V = sum_l c_l w_l with the signed residues
+    # c_l in [-h_l, p_l - 1 - h_l], from est = sum_l c_l round(2^16 w_l / P) in a signed
+    # 32-bit integer: the estimate is within 0.05 of V / P (so a fractional part at least
+    # 0.3 from one half decides the rounding, and the rarer cases take the exact
+    # comparison), est never overflows, and V - Q P stays inside the kernel's limbs.
     for N in range(1, 21):
         moduli = oz.hybrid_moduli(N)
         w, P = oz.crt_weights(moduli)
@@ -126,10 +127,31 @@ def test_crt_quotient_estimate_bound():
         for p, wl in zip(moduli, w):
             exact = Fraction(2**16 * wl, P)
             f16 = round(exact)
-            err += (p - 1) * abs(f16 - exact) / 2**16
-            est_max += (p - 1) * f16
-        assert err < Fraction(17, 100), (N, float(err))
-        assert est_max + 0x8000 < 2**32, N
+            err += (p // 2) * abs(f16 - exact) / 2**16
+            est_max += (p // 2) * f16
+        assert err < Fraction(5, 100), (N, float(err))
+        assert est_max + 0x8000 < 2**31, N
+        # V = sum c_l w_l changes by q_l P when c_l < 0 is replaced by c_l + p_l: the same mod P
+        for p, wl in zip(moduli, w):
+            assert (p * wl) % P == 0
+
+
+def test_crt_balanced_weight_limbs():
+    # w_l = sum_t b_t 2^(32 t) with every b_t in [-2^31, 2^31) in the kernel's limb count,
+    # and the 64-bit limb sums of at most 20 terms |c_l b_t| < 2^46 cannot overflow
+    for N in range(1, 21):
+        moduli = oz.hybrid_moduli(N)
+        w, P = oz.crt_weights(moduli)
+        L = (P.bit_length() + 1 + 31) // 32
+        for wl in w:
+            b, carry = [], 0
+            for t in range(L):
+                u = ((wl >> (32 * t)) & 0xFFFFFFFF) + carry
+                carry = 1 if u >= 2**31 else 0
+                b.append(u - (carry << 32))
+            assert carry == 0 and all(-2**31 <= x < 2**31 for x in b)
+            assert sum(x << (32 * t) for t, x in enumerate(b)) == wl
+        assert 20 * 2**15 * 2**31 < 2**63
 
 
 def test_library_reciprocals_are_correctly_rounded():
