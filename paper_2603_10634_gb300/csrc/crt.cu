@@ -163,8 +163,9 @@ __device__ __forceinline__ void crt_body(const int16_t* __restrict__ cres, int64
   if (first >= total) return;
   // (row, column pair) of the item, advanced by the stride's own quotient and remainder
   // instead of a 64-bit division per item (the stride is at most a few grids of threads)
-  int i = static_cast<int>(first / nq), jq = static_cast<int>(first % nq);
-  const int di = static_cast<int>(stride / nq), dj = static_cast<int>(stride % nq);
+  int i, jq, di, dj;
+  divmod_nonneg(first, nq, i, jq);
+  divmod_nonneg(stride, nq, di, dj);
   for (; i < m; i += di, jq += dj) {
     if (jq >= nq) {
       jq -= nq;

@@ -212,6 +212,19 @@ __device__ __forceinline__ void for_each_vblock(const BatchProblem* __restrict__
 }
 
 // ---------------------------------------------------------------- integers
+// q = a / b, r = a % b for a >= 0 and b > 0: an unsigned 32-bit division when a fits,
+// which is several times cheaper than the 64-bit one.
+__device__ __forceinline__ void divmod_nonneg(int64_t a, int b, int& q, int& r) {
+  if (a <= 0x7FFFFFFFll) {
+    const uint32_t ua = static_cast<uint32_t>(a), ub = static_cast<uint32_t>(b);
+    const uint32_t uq = ua / ub;
+    q = static_cast<int>(uq);
+    r = static_cast<int>(ua - uq * ub);
+  } else {
+    q = static_cast<int>(a / b);
+    r = static_cast<int>(a - static_cast<int64_t>(q) * b);
+  }
+}
 // Normalise a value in [-2h, 2(p-1-h)] (a sum of two symmetric residues).
 __device__ __forceinline__ int smod_small(int x, int p, int h) {
   x = (x > p - 1 - h) ? x - p : x;

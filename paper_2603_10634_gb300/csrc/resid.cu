@@ -341,8 +341,9 @@ __device__ __forceinline__ void residues_rows_body(const ResidArgs& a, int N, co
   if (first >= items) return;
   // (row group, k chunk) of the item, advanced by the stride's quotient and remainder
   // instead of a 64-bit division per item (the stride is at most a few grids of warps)
-  int grp = static_cast<int>(first / nkw), chunk = static_cast<int>(first % nkw);
-  const int dgrp = static_cast<int>(stride / nkw), dchunk = static_cast<int>(stride % nkw);
+  int grp, chunk, dgrp, dchunk;
+  divmod_nonneg(first, nkw, grp, chunk);
+  divmod_nonneg(stride, nkw, dgrp, dchunk);
   // every line of X starts on a 16-byte boundary: 16-byte loads
   const bool vec = (reinterpret_cast<uintptr_t>(a.X) & 15u) == 0 && (a.ldx & 1) == 0;
   bool range_err = false;

@@ -365,8 +365,9 @@ __global__ void __launch_bounds__(256) colmax_batch(const BatchProblem* __restri
                                                     int64_t total) {
   for_each_vblock(probs, count, kBkColmax, total, [&](const BatchProblem& P, int64_t v) {
     const int gx = (P.n + 255) / 256;
-    colmax_body(P.B, P.ldb, P.k, P.n, P.colmaxB, P.colbadB, static_cast<int>(v % gx), static_cast<int>(v / gx),
-                kColRows);
+    int by, bx;
+    divmod_nonneg(v, gx, by, bx);
+    colmax_body(P.B, P.ldb, P.k, P.n, P.colmaxB, P.colbadB, bx, by, kColRows);
   });
 }
 
@@ -375,8 +376,10 @@ __global__ void __launch_bounds__(256) scale_cols_batch(const BatchProblem* __re
                                                         int64_t total, uint32_t* flags) {
   for_each_vblock(probs, count, kBkScaleCols, total, [&](const BatchProblem& P, int64_t v) {
     const int gx = (P.n + 255) / 256;
+    int hb, bx;
+    divmod_nonneg(v, gx, hb, bx);
     scale_cols_body<FAST>(P.B, P.ldb, P.k, P.n, P.kp, P.colmaxB, P.colbadB, P.fprime, P.colstat, P.BbarT, P.partB,
-                          flags, static_cast<int>(v % gx), static_cast<int>(v / gx));
+                          flags, bx, hb);
   });
 }
 
