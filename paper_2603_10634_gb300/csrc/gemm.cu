@@ -592,6 +592,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
               for (int z = 0; z < 4; ++z) pr[z] = sp[4 * w + z];
             };
+            // single problems: the pass's slot(s) go back to the MMA thread as soon as the last
+            // chunk has been read from TMEM, before that chunk's arithmetic and stores (in the
+            // grouped kernel the extra live state made it spill, and the release stays at the
+            // end of the pass)
+            auto release = [&]() {
+              tc_fence_before();
+              if (pair) {
+                mbar_arrive(tempty + 0);
+                mbar_arrive(tempty + 1);
+              } else {
+                mbar_arrive(tempty + slot);
+              }
+            };
             auto chunk = [&](int cb, uint32_t* sp) {
               const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
               const bool keep = gi < uc.m;  // this thread's row is inside the matrix
@@ -600,6 +613,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tmem_ld_32cols(tq + cb * 32, vx);
                 tmem_ld_32cols(tq + BN + cb * 32, vz);
                 tmem_ld_wait();
+                if (!GROUPED && cb == BN / 64 - 1) release();
                 // mod(s X + Z, p): X mod p first keeps s (X mod p) + Z below 2^24 (|X| <= 2^24,
                 // |Z| <= 2^23), so every step is exact
 #pragma unroll
@@ -619,6 +633,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               uint32_t v[32];
               tmem_ld_32cols(ts + cb * 32, v);
               tmem_ld_wait();
+              if (!GROUPED && cb == BN / 64 - 1) release();
               if (mod < kNumSquares) {  // square modulus in two passes
                 if (ps == 0) {  // park x = X mod p (|x| < 0.51 p)
 #pragma unroll
@@ -738,14 +753,19 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             }
           }
-          tc_fence_before();
+          if constexpr (MODE != kModeResidue || GROUPED) {  // else the epilogue released the slot(s) itself
+            tc_fence_before();
+            if (pair) {
+              mbar_arrive(tempty + 0);
+              mbar_arrive(tempty + 1);
+            } else {
+              mbar_arrive(tempty + slot);
+            }
+          }
           if (pair) {
-            mbar_arrive(tempty + 0);
-            mbar_arrive(tempty + 1);
             sl.bump(0u);
             sl.bump(1u);
           } else {
-            mbar_arrive(tempty + slot);
             sl.bump(slot);
             sl.next ^= 1u;
           }
