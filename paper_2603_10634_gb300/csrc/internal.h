@@ -225,11 +225,11 @@ struct BatchProblem {
 // (one block per tile in a grouped launch).
 constexpr int kResidTileCols = 64, kResidTileK = 128;
 
-// Items of the row residue kernel: a warp covers 2^s lanes x 8 k of 32 / 2^s rows, s = 5
-// (256 consecutive k of one row) for kp >= 256, else the smallest s with 2^s 8 >= kp
-// (kp is a multiple of 32).
+// Items of the row residue kernel: a warp covers 2^s lanes x 8 k of 32 / 2^s rows, s = 4
+// (128 consecutive k of two rows) for kp > 64, else the smallest s with 2^s 8 >= kp (kp is
+// a multiple of 32): the last item of a row then leaves at most 120 of its k idle.
 __host__ __device__ constexpr int resid_rows_lane_log(int kp) {
-  return kp >= 256 ? 5 : (kp <= 32 ? 2 : (kp <= 64 ? 3 : (kp <= 128 ? 4 : 5)));
+  return kp <= 32 ? 2 : (kp <= 64 ? 3 : 4);
 }
 __host__ __device__ constexpr int64_t resid_rows_items(int lines, int kp) {
   return static_cast<int64_t>((lines + (32 >> resid_rows_lane_log(kp)) - 1) / (32 >> resid_rows_lane_log(kp))) *

@@ -318,10 +318,10 @@ __device__ __forceinline__ void task_planes(int N, const Tables& tb, const f2 (&
   else all_planes<false>(N, tb, c, tp, st, flags);
 }
 
-// Rows of A.  A warp item covers 2^s lanes x 8 k of 32 / 2^s rows: all 32 lanes on 256
-// consecutive k of one row when kp >= 256, else the smallest power of two of lanes that
-// covers the row (kp / 8 elements), so that short rows do not leave lanes idle.  Lane l
-// owns 8 consecutive elements (four 16-byte loads when the row is 16-byte aligned) and
+// Rows of A.  A warp item covers 2^s lanes x 8 k of 32 / 2^s rows (16 lanes on 128
+// consecutive k of two rows, or 4 or 8 lanes per row for rows of at most 64 k; see
+// resid_rows_lane_log), so short rows and the ends of rows leave few lanes idle.  Lane
+// l owns 8 consecutive elements (four 16-byte loads when the row is 16-byte aligned) and
 // writes 8 bytes of each plane.
 static_assert(kElems == 8, "the row kernel's item shapes assume 8 elements per lane");
 
