@@ -220,3 +220,19 @@ def test_epilogue_int16_packing_by_magic_bias():
         b = np.array([np.float32(r) + np.float32(1.5 * 2**23)], dtype=np.float32).view(np.uint32)[0]
         assert np.float32(r) + np.float32(1.5 * 2**23) == np.float32(r + 1.5 * 2**23)
         assert np.int16(np.uint16(int(b) & 0xFFFF)) == r
+
+
+def test_karatsuba_high_digit_one_rounding():
+    # the digit kernels form d1 = sign(r) ceil(|r| / 16) as RN(r / 16 + sign(r) 15/32) through
+    # 1.5 2^23: r / 16 + 15/32 is exact in FP32 and never a half-integer for integer r
+    for p in oz.hybrid_moduli(20):
+        kind, s = oz.modulus_kind(p)
+        if kind == "square":
+            continue
+        for r in _residues(p):
+            r = int(r)
+            off = Fraction(15, 32) if r >= 0 else Fraction(-15, 32)
+            t = Fraction(r, 16) + off
+            assert oz.f32_round_nearest(t) == t  # exact
+            q = Fraction(float(oz.f32_round_nearest(t + MAGIC))) - MAGIC
+            assert int(q) == oz.split_karatsuba(r, s)[0], (p, r)
