@@ -129,10 +129,10 @@ __device__ __forceinline__ void square_digits(f2 r, f2 neg_s, f2 inv_s, f2& d1, 
   d2 = __ffma2_rn(neg_s, d1, r);
 }
 __device__ __forceinline__ void karatsuba_digits(f2 r, f2& d1, f2& d2, f2& d3) {
-  // ceil(|r| / 16) = round((|r| + 7.5) / 16) for integer |r| (never a tie)
-  const f2 a = make_float2(fabsf(r.x), fabsf(r.y));
-  const f2 m1 = round_magic(__fadd2_rn(__ffma2_rn(a, dup(0.0625f), dup(0.46875f)), dup(kMagic)));
-  d1 = make_float2(copysignf(m1.x, r.x), copysignf(m1.y, r.y));
+  // d1 = sign(r) ceil(|r| / 16) = RN(r / 16 + sign(r) 15/32): the sum is exact and never a
+  // half-integer for integer r, and a zero result is +0
+  const f2 off = make_float2(copysignf(0.46875f, r.x), copysignf(0.46875f, r.y));
+  d1 = round_magic(__fadd2_rn(__ffma2_rn(r, dup(0.0625f), off), dup(kMagic)));
   d2 = __ffma2_rn(dup(-16.0f), d1, r);
   d3 = __fadd2_rn(d1, d2);
 }
