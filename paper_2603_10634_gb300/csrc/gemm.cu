@@ -31,15 +31,17 @@
 // unit gives a thread the same row and columns).  The bound and raw products are one single-slot pass per unit.  The wide tile halves the
 // operand bytes each SM pulls per flop compared with 128 x 128.
 //
-// Roles (320 threads, one persistent CTA per SM):
+// Roles (320 threads for single problems, 576 for grouped launches; one persistent CTA
+// per SM):
 //   warp 0      TMA producer: 128-row A and 256-row B^T boxes of 128 bytes along K
 //               (K-major, 128-byte swizzle, zero fill past m, n, k) into a 4-stage
 //               ring of 48 KiB stages, mbarrier complete_tx.
 //   warp 1      TMEM allocation and the single MMA-issuing thread:
 //               tcgen05.mma.cta_group::1.kind::f8f6f4, M = 128, N = 256, K = 32; a pass
 //               starts once the epilogue has released the slot(s) it writes.
-//   warps 2-9   epilogue: warp w reads TMEM lane quadrant w % 4, column half
-//               (w - 2) / 4, with tcgen05.ld; integer math; global stores.
+//   warps 2-9   epilogue (warps 2-17 in grouped launches): warp w reads TMEM lane
+//               quadrant w % 4, column half (quarter) (w - 2) / 4, with tcgen05.ld;
+//               FP32 math; global stores.
 // Every wait is bounded (device.cuh; the limit is a launch parameter); a wait that gives
 // up raises a CTA-wide abort flag and the global timeout flag, drains the copies and
 // products this CTA has in flight, frees TMEM and returns.  Operands are read only with
@@ -54,8 +56,19 @@ namespace {
 constexpr int BM = 128;
 constexpr int BK = 128;  // bytes = FP8 elements per k-step (one 128-byte swizzle row)
 constexpr int kATileBytes = BM * BK;  // 16 KiB
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+// Epilogue warps: 8 for single problems, 16 for grouped launches.  Short reductions in
+// batches of small problems leave the tensor cores waiting for the epilogue (about 40%
+// of the MMA thread's time with 8 warps on the 512-product batch); twice the warps hide
+// more of its TMEM-load and store latency there (batch 14.8 -> 13.7 ms), while for
+// single problems the extra warps slowed the MMA and TMA threads that share their
+// schedulers (8192 x 8192 x 2048: 4.29 -> 4.53 ms).
+template <bool GROUPED>
+struct Epi {
+  static constexpr int kWarps = GROUPED ? 16 : 8;
+  static constexpr int kColGroups = kWarps / 4;  // epilogue warps per TMEM lane quadrant
+  static constexpr int kThreads = 64 + 32 * kWarps;
+  static constexpr int kCW = GROUPED ? 16 : 32;  // columns per TMEM load of the residue epilogue
+};
 constexpr int kChunkKaratsuba = 65536;  // 2^16 * 16 * 16 = 2^24
 constexpr int kChunkSquare = 32768;     // shared accumulator: 2 * 2^15 * 16 * 16 = 2^24
 constexpr int kGroupM = 16;             // tile rasterisation: bands of 16 tile rows (2048 rows of A)
@@ -363,7 +376,7 @@ __device__ __forceinline__ void store_residues8(int16_t* dst, int gc, int n, uin
 
 // GROUPED: the units of all `nprobs` problems of `probs` (tmA, tmB unused).  TN: tile width.
 template <int MODE, bool GROUPED, int TN>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(Epi<GROUPED>::kThreads, 1)
     fp8_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                     const __grid_constant__ GemmParams prm, const GemmProblem* __restrict__ probs, int nprobs) {
   constexpr int BN = TN;
@@ -395,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int j = 0; j < 2; ++j) {
       mbar_init(tfull + j, 1);
-      mbar_init(tempty + j, 32 * kEpiWarps);
+      mbar_init(tempty + j, 32 * Epi<GROUPED>::kWarps);
     }
     mbar_init(done, 1);
     mbar_init(never, 1);
@@ -547,16 +560,19 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else {
     // ------------------------------------------------------------ epilogue
     const int q = warp & 3;                 // TMEM lane quadrant this warp may access
-    const int chalf = (warp - 2) >> 2;      // column half of the tile
+    const int cgrp = (warp - 2) >> 2;       // column group of the tile
+    constexpr int kCols = BN / Epi<GROUPED>::kColGroups;  // columns of this thread
+    constexpr int kCW = Epi<GROUPED>::kCW;
+    constexpr int kChunks = kCols / kCW;
     const int row = q * 32 + lane;
-    const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(chalf * (BN / 2));
+    const uint32_t tq = tmem_base + (static_cast<uint32_t>(q * 32) << 16) + static_cast<uint32_t>(cgrp * kCols);
     // Residues kept between the passes of a unit (Karatsuba d1, then v; the X residue of
-    // a two-pass square modulus), 32 int16 per chunk of 32 columns, two per word.  Every
-    // pass of a unit gives this thread the same row and the same BN / 2 columns, so they
+    // a two-pass square modulus), kCW int16 per chunk of kCW columns, two per word.  Every
+    // pass of a unit gives this thread the same row and the same kCols columns, so they
     // stay in registers (the chunk loop unrolled).  An earlier form parked them in a
     // CTA-private scratch tile in L2; its round trips made short reductions up to 14%
     // slower.
-    uint32_t park[MODE == kModeResidue ? BN / 64 : 1][16];
+    uint32_t park[MODE == kModeResidue ? kChunks : 1][kCW / 2];
     Slots sl;  // the MMA thread's pass sequence, replayed
     bool ok = true;
     UnitCtx uc;
@@ -582,7 +598,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const ModPair mp{dup2(-static_cast<float>(p)), dup2(prm.mod.inv_p[mod]), p == 1024};
             const bool last = ps == up.npasses - 1;
             int16_t* dst = uc.cres + static_cast<int64_t>(mod) * uc.res_stride + static_cast<int64_t>(gi) * uc.ldr;
-            // one chunk of 32 columns; sp: this thread's 32 parked int16 of the chunk, two per
+            // one chunk of kCW columns; sp: this thread's kCW parked int16 of the chunk, two per
             // word (registers: every index below is known at compile time)
             auto store4 = [](uint32_t* sp, int w, const uint32_t (&pk)[4]) {
 #pragma unroll
@@ -606,18 +622,18 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             };
             auto chunk = [&](int cb, uint32_t* sp) {
-              const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
+              const int gc = tn * BN + cgrp * kCols + cb * kCW;
               const bool keep = gi < uc.m;  // this thread's row is inside the matrix
               if (pair) {  // square modulus: X in slot 0, Z in slot 1
-                uint32_t vx[32], vz[32];
-                tmem_ld_32cols(tq + cb * 32, vx);
-                tmem_ld_32cols(tq + BN + cb * 32, vz);
+                uint32_t vx[kCW], vz[kCW];
+                tmem_ld_cols(tq + cb * kCW, vx);
+                tmem_ld_cols(tq + BN + cb * kCW, vz);
                 tmem_ld_wait();
-                if (!GROUPED && cb == BN / 64 - 1) release();
+                if (!GROUPED && cb == kChunks - 1) release();
                 // mod(s X + Z, p): X mod p first keeps s (X mod p) + Z below 2^24 (|X| <= 2^24,
                 // |Z| <= 2^23), so every step is exact
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < kCW / 8; ++w) {
                   uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z) {
@@ -630,14 +646,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 return;
               }
-              uint32_t v[32];
-              tmem_ld_32cols(ts + cb * 32, v);
+              uint32_t v[kCW];
+              tmem_ld_cols(ts + cb * kCW, v);
               tmem_ld_wait();
-              if (!GROUPED && cb == BN / 64 - 1) release();
+              if (!GROUPED && cb == kChunks - 1) release();
               if (mod < kNumSquares) {  // square modulus in two passes
                 if (ps == 0) {  // park x = X mod p (|x| < 0.51 p)
 #pragma unroll
-                  for (int w = 0; w < 4; ++w) {
+                  for (int w = 0; w < kCW / 8; ++w) {
                     uint32_t pk[4];
 #pragma unroll
                     for (int z = 0; z < 4; ++z) pk[z] = pack2(mod_near2(bits2(v[8 * w + 2 * z], v[8 * w + 2 * z + 1]), mp));
@@ -647,7 +663,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 // C' = mod(s x + Z, p), as the one-pass form computes it
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < kCW / 8; ++w) {
                   uint32_t pr[4];
                   load4(sp, w, pr);
                   uint32_t pk[4];
@@ -663,7 +679,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               if (ps == 0) {  // Karatsuba pass 1: park d1 = mod(D1, p)
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < kCW / 8; ++w) {
                   uint32_t pk[4];
 #pragma unroll
                   for (int z = 0; z < 4; ++z) pk[z] = pack2(smod2(bits2(v[8 * w + 2 * z], v[8 * w + 2 * z + 1]), mp));
@@ -674,7 +690,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               if (!last) {  // Karatsuba pass 2: park v = mod(240 d1 - 15 D2, p); D2 mod p first
                             // keeps |240 d1 - 15 (D2 mod p)| below 2^17
 #pragma unroll
-                for (int w = 0; w < 4; ++w) {
+                for (int w = 0; w < kCW / 8; ++w) {
                   uint32_t pr[4];
                   load4(sp, w, pr);
                   uint32_t pk[4];
@@ -691,7 +707,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
               // Karatsuba pass 3: C' = mod(v + 16 D3, p); D3 mod p first (|v + 16 (D3 mod p)| < 2^14)
 #pragma unroll
-              for (int w = 0; w < 4; ++w) {
+              for (int w = 0; w < kCW / 8; ++w) {
                 uint32_t pr[4];
                 load4(sp, w, pr);
                 uint32_t pk[4];
@@ -705,7 +721,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
             };
 #pragma unroll
-            for (int cb = 0; cb < BN / 64; ++cb) chunk(cb, park[cb]);
+            for (int cb = 0; cb < kChunks; ++cb) chunk(cb, park[cb]);
           } else if constexpr (MODE == kModeBound) {
             float rmax = 0.0f;
             // 2^-s for an integer s clamped to [-126, 126] (an upper bound of 2^-s for
@@ -718,11 +734,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float rscale = (GROUPED || !prm.rowshift || gi >= uc.m) ? 1.0f : pow2_neg(prm.rowshift[gi]);
             const bool cshift = !GROUPED && prm.colshift != nullptr;
 #pragma unroll 1
-            for (int cb = 0; cb < BN / 64; ++cb) {
+            for (int cb = 0; cb < kCols / 32; ++cb) {
               uint32_t v0[32];
               tmem_ld_32cols(ts + cb * 32, v0);
               tmem_ld_wait();
-              const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
+              const int gc = tn * BN + cgrp * kCols + cb * 32;
               float cv[32];
 #pragma unroll
               for (int j = 0; j < 32; ++j) {
@@ -740,11 +756,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (gi < uc.m && rmax > 0.0f) atomicMax(reinterpret_cast<int*>(uc.R) + gi, __float_as_int(rmax));
           } else {
 #pragma unroll 1
-            for (int cb = 0; cb < BN / 64; ++cb) {
+            for (int cb = 0; cb < kCols / 32; ++cb) {
               uint32_t v0[32];
               tmem_ld_32cols(ts + cb * 32, v0);
               tmem_ld_wait();
-              const int gc = tn * BN + chalf * (BN / 2) + cb * 32;
+              const int gc = tn * BN + cgrp * kCols + cb * 32;
               if (gi < uc.m) {
                 float* o = prm.D + static_cast<int64_t>(gi) * prm.ldd;
 #pragma unroll
@@ -799,7 +815,7 @@ cudaError_t launch_mode(const GemmParams& prm, const CUtensorMap& ta, const CUte
     if (err != cudaSuccess) return err;
     configured[dev] = true;
   }
-  fp8_gemm_kernel<MODE, GROUPED, TN><<<grid, kThreads, smem, st>>>(ta, tb, prm, probs, nprobs);
+  fp8_gemm_kernel<MODE, GROUPED, TN><<<grid, Epi<GROUPED>::kThreads, smem, st>>>(ta, tb, prm, probs, nprobs);
   return cudaGetLastError();
 }
 
