@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--shapes", default="4096x4096x65536,65536x1024x1024",
                     help="rect: comma-separated m x n x k shapes")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="batched: plan with --moduli and --tile (default 256) instead of the autotuner")
+                    help="batched: plan with --moduli and --tile (default 0: the library's per-problem "
+                         "widths) instead of the autotuner")
     ap.add_argument("--workload", default="dgemm", choices=["dgemm", "autograd", "batched", "sweep", "rect"],
                     help="dgemm: the square product above; autograd: forward + backward of "
                          "C = A B with A 8192 x 4096, B 4096 x 4096 and upstream gradient W ~ N(0, 1); "
@@ -622,6 +623,11 @@ def run_autograd(a, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def tile_label(tile):
+    """Words for a batch plan's tile setting."""
+    return f"tile 128x{tile}" if tile else "tiles 128x256 or 128x128 per problem"
+
+
 def run_batched(a, rank, world):
     """512 uneven products as one batch plan (one launch per phase), against the same
     products issued as 512 single calls and against a CUDA graph of the plan."""
@@ -642,7 +648,7 @@ def run_batched(a, rank, world):
     # tile width of the plan (timed), picked by the autotuner
     t0 = time.perf_counter()
     if a.no_autotune:
-        N, tile, tune_rep = a.moduli, a.tile if a.tile in (128, 256) else 256, {"moduli": [], "plan_ms": {}}
+        N, tile, tune_rep = a.moduli, a.tile if a.tile in (0, 128, 256) else 0, {"moduli": [], "plan_ms": {}}
     else:
         N, tile, tune_rep = ozk.choose_plan(As, Bs, "fp64", mode=a.mode, probes=4)
     reports = tune_rep["moduli"]
@@ -697,7 +703,7 @@ def run_batched(a, rank, world):
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f8e4m3", "emulates": "f64", "data": "synthetic",
             "config": {"workload": f"512 products, m, n, k log-uniform on [64, 2048] (seed 0), phi={a.phi}, "
-                                   f"N={N}, tile 128x{tile} ({'given' if a.no_autotune else 'autotuned'}), {a.mode} mode", "total_flop": flops,
+                                   f"N={N}, {tile_label(tile)} ({'given' if a.no_autotune else 'autotuned'}), {a.mode} mode", "total_flop": flops,
                        "l2": "operands (2.7 GB) larger than L2, no flush"},
             "gpu_launches": launches * a.steps, "clocks": clk.summary(), "device_status": status,
             "plain_calls": {"ms_per_step": plain_ms, "tflops": flops / plain_ms / 1e9, "launches": 512 * single_launches,

@@ -336,14 +336,16 @@ uint64_t ozk2_set_wait_limit(uint64_t ns);
  * this call (and of batch plans created after it): 256 (128 x 256 tiles), 128 (128 x 128
  * tiles, for narrow or ragged products), or 0, the default: the library chooses 128 where
  * a 256-wide tile would pad the product's columns by a quarter or more, else 256 (a batch
- * plan applies that rule to the batch's total padded work).  Results are bit-identical
- * for either width.  Returns the previous setting, or -1 (unchanged) for other values.
- * Process-wide; a tuning knob (the moduli-and-tile tuner measures both widths).
+ * plan applies that rule to each problem's residue products, which then run in up to two
+ * grouped launches, one per width, and to the batch's total padded work for its bound
+ * products).  Results are bit-identical for either width.  Returns the previous setting,
+ * or -1 (unchanged) for other values.  Process-wide; a tuning knob (the moduli-and-tile
+ * tuner measures the settings).
  */
 int ozk2_set_tile_n(int tile_n);
 
-/* ozk2_batch_plan_tile_n - the tile width a batch plan runs its products with (-1 for
- * NULL). */
+/* ozk2_batch_plan_tile_n - the tile width a batch plan runs its residue products with:
+ * 256 or 128, 0 when its problems use both widths, -1 for NULL. */
 int ozk2_batch_plan_tile_n(ozk2_batch_plan plan);
 
 /*

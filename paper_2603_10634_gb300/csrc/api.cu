@@ -1091,9 +1091,14 @@ struct ozk2_batch_plan_st {
   bool owns_ws = false;
   ozk2::BatchLayout L{};
   int64_t totals[ozk2::kBatchKernels] = {};
-  int64_t units_bound = 0, units_res = 0;
+  int64_t units_bound = 0;
+  // The residue products run in up to two grouped launches: the first res_cnt[0]
+  // descriptors in 256-wide tiles, the next res_cnt[1] in 128-wide tiles.
+  int res_cnt[2] = {0, 0};
+  int64_t res_units[2] = {0, 0};
   int num_sms = 0;
-  int tile_n = 256;  // tile width of the plan's FP8 products
+  int tile_n = 256;      // tile width of the residue products (0: both widths)
+  int bound_tile = 256;  // tile width of the bound products
   const void* tab = nullptr;  // ozk2::Tables
   uint8_t* host = nullptr;    // pinned copy of the uploaded descriptors
   size_t host_bytes = 0;
@@ -1296,41 +1301,54 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
     ++j;
   }
   for (int w = 0; w < kBatchKernels; ++w) plan->totals[w] = running[w];
-  std::stable_sort(order.begin(), order.end(), [&probs](int a, int b) { return probs[a].k > probs[b].k; });
-  // one tile width for the whole plan: the setting, else the rule on the batch's total
-  // padded tensor work (sum of m k ceil(n / t) t)
+  // Tile widths.  The setting (ozk2_set_tile_n) fixes one for every product of the plan.
+  // Otherwise each problem's residue products take the rule of single calls (tile_for):
+  // narrow or ragged problems run in 128-wide tiles and the rest in 256-wide ones, in
+  // two grouped launches (wide first), which spends less tensor work on padding than one
+  // width for the whole batch.  The bound products (1-2% of a plan) run in one launch
+  // with the rule applied to the batch's total padded work (sum of m k ceil(n / t) t).
+  const int tset = g_tile_n.load();
   {
     int64_t w256 = 0, w128 = 0;
     for (const BatchProblem& q : probs) {
       w256 += int64_t(q.m) * q.k * padded(q.n, 256) / 64;
       w128 += int64_t(q.m) * q.k * padded(q.n, 128) / 64;
     }
-    const int t = g_tile_n.load();
-    plan->tile_n = t ? t : tile_rule(w256, w128);
+    plan->bound_tile = tset ? tset : tile_rule(w256, w128);
   }
+  std::vector<int> narrow(probs.size());  // 1: the problem's residue products use 128-wide tiles
+  for (size_t i = 0; i < probs.size(); ++i)
+    narrow[i] = (tset ? tset : tile_rule(padded(probs[i].n, 256), padded(probs[i].n, 128))) == 128 ? 1 : 0;
+  // grouped by tile width, longest reductions first within a group
+  std::stable_sort(order.begin(), order.end(), [&probs, &narrow](int a, int b) {
+    return narrow[a] != narrow[b] ? narrow[a] < narrow[b] : probs[a].k > probs[b].k;
+  });
   std::vector<GemmProblem> gres(probs.size()), gbound(fast ? 0 : probs.size());
   const int64_t split_kmax = g_split_kmax.load();
-  int64_t ures = 0, ubound = 0;
+  int64_t ubound = 0;
   for (size_t r = 0; r < order.size(); ++r) {
     const BatchProblem& q = probs[size_t(order[r])];
+    const int grp = narrow[size_t(order[r])];
+    const int tile = grp ? 128 : 256;
     GemmProblem& g = gres[r];
     std::memset(&g, 0, sizeof(g));
-    if (!encode_gemm_problem(&g, q.planesA, q.planesB, q.ldp, tab->mt.num_planes, q.m, q.n, q.k, plan->tile_n)) {
+    if (!encode_gemm_problem(&g, q.planesA, q.planesB, q.ldp, tab->mt.num_planes, q.m, q.n, q.k, tile)) {
       destroy_plan(plan);
       return OZK2_ERR_INTERNAL;
     }
     // the products of one problem are addressed like those of a single call, but the
     // planes of the B operand have n rows: the map was encoded with the packed strides
-    g.unit_start = ures;
+    g.unit_start = plan->res_units[grp];  // units are numbered within each grouped launch
     g.split = q.k <= split_kmax ? 1 : 0;
     g.cres = q.cres;
     g.ldr = q.ldr;
     g.res_stride = int64_t(q.m) * q.ldr;
-    ures += fp8_gemm_units(kModeResidue, q.m, q.n, N, plan->tile_n);
+    plan->res_units[grp] += fp8_gemm_units(kModeResidue, q.m, q.n, N, tile);
+    plan->res_cnt[grp] += 1;
     if (!fast) {
       GemmProblem& b = gbound[r];
       std::memset(&b, 0, sizeof(b));
-      if (!encode_gemm_problem(&b, q.Abar, q.BbarT, q.kp, 1, q.m, q.n, q.k, plan->tile_n)) {
+      if (!encode_gemm_problem(&b, q.Abar, q.BbarT, q.kp, 1, q.m, q.n, q.k, plan->bound_tile)) {
         destroy_plan(plan);
         return OZK2_ERR_INTERNAL;
       }
@@ -1338,13 +1356,13 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
       b.factor = bound_factor_f32(q.k);
       b.R = q.R;
       b.S = q.S;
-      ubound += fp8_gemm_units(kModeBound, q.m, q.n, N, plan->tile_n);
+      ubound += fp8_gemm_units(kModeBound, q.m, q.n, N, plan->bound_tile);
     }
   }
-  plan->units_res = ures;
   plan->units_bound = ubound;
+  plan->tile_n = plan->res_cnt[0] > 0 && plan->res_cnt[1] > 0 ? 0 : (plan->res_cnt[1] > 0 ? 128 : 256);
   if (plan->cnt > 0) {
-    if (ures > 0x7FFFFFFFll) {
+    if (plan->res_units[0] > 0x7FFFFFFFll || plan->res_units[1] > 0x7FFFFFFFll) {
       destroy_plan(plan);
       return OZK2_ERR_UNSUPPORTED;
     }
@@ -1391,7 +1409,7 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
   GemmArgs g{};
   g.num_sms = plan->num_sms;
   g.flags = flags;
-  g.tile_n = plan->tile_n;
+  g.tile_n = plan->bound_tile;
   if (!plan->fast) {
     g.mode = kModeBound;
     if (!launch_controls(g)) return OZK2_ERR_CUDA;
@@ -1404,11 +1422,16 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
                                  flags, st));
   g.mode = kModeResidue;
   g.mt = &tab->mt;
-  if (!launch_controls(g)) return OZK2_ERR_CUDA;
-  OZK2_TRY(launch_fp8_gemm_grouped(g, reinterpret_cast<const GemmProblem*>(ws + L.gres), plan->cnt, plan->units_res,
-                                   st));
+  const GemmProblem* gres = reinterpret_cast<const GemmProblem*>(ws + L.gres);
+  for (int grp = 0, first = 0; grp < 2; first += plan->res_cnt[grp], ++grp) {
+    if (plan->res_cnt[grp] == 0) continue;
+    g.tile_n = grp ? 128 : 256;
+    if (!launch_controls(g)) return OZK2_ERR_CUDA;
+    OZK2_TRY(launch_fp8_gemm_grouped(g, gres + first, plan->res_cnt[grp], plan->res_units[grp], st));
+    t_launches += 1;
+  }
   OZK2_TRY(launch_crt_batch(probs, plan->cnt, plan->totals[kBkCrt], tab->ct, st));
-  t_launches += 5;
+  t_launches += 4;
   return OZK2_OK;
 }
 

@@ -313,7 +313,8 @@ class BatchPlan:
         return self._lib.ozk2_batch_plan_workspace(self._plan)
 
     def tile_n(self):
-        """Tile width the plan's FP8 products run with."""
+        """Tile width the plan's residue products run with (0: both widths, chosen per
+        problem)."""
         return int(self._lib.ozk2_batch_plan_tile_n(self._plan))
 
     def status(self):

@@ -121,11 +121,13 @@ def choose_tile(A, B, num_moduli=12, mode="accurate", reps=3):
 
 
 def choose_plan(As, Bs, target="fp64", mode="accurate", probes=4, reps=3, **kw):
-    """Moduli count for the requested accuracy (choose_moduli_batch) and the faster tile
-    width of the whole batch plan, measured: (N, tile_n, report)."""
+    """Moduli count for the requested accuracy (choose_moduli_batch) and the fastest tile
+    setting of the batch plan, measured: 256 or 128 for every problem, or 0 for the
+    library's per-problem widths (narrow and ragged problems in 128-wide tiles, the rest
+    in 256-wide ones): (N, tile_n, report)."""
     N, reports = choose_moduli_batch(As, Bs, target, mode, probes, **kw)
     times = {}
-    for t in (256, 128):
+    for t in (0, 256, 128):
         plan = ozk2.BatchPlan(As, Bs, num_moduli=N, mode=mode, tile_n=t)
         times[t] = _time(plan.execute, reps)
         plan.close()
