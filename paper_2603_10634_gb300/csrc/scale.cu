@@ -407,11 +407,11 @@ void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nb)[kB
   nb[kBkScaleCols] = gx * (kp / 32);
   nb[kBkSumsq] = fast ? gx : 0;
   nb[kBkExponents] = (static_cast<int64_t>(m) + n + 255) / 256;
-  nb[kBkResidRows] = (resid_rows_items(m, kp) + 31) / 32;  // up to 4 items per warp
+  nb[kBkResidRows] = (resid_rows_items(m, kp) + 127) / 128;  // up to 16 items per warp
   // one block per tile of the column residue kernel
   nb[kBkResidCols] = static_cast<int64_t>((n + kResidTileCols - 1) / kResidTileCols) *
                      ((kp + kResidTileK - 1) / kResidTileK);
-  nb[kBkCrt] = (static_cast<int64_t>(m) * ((n + 1) / 2) + 1023) / 1024;  // up to 4 items per thread
+  nb[kBkCrt] = (static_cast<int64_t>(m) * ((n + 1) / 2) + 4095) / 4096;  // up to 16 items per thread
 }
 
 cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64_t (&total)[kBatchKernels],
