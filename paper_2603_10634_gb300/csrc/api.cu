@@ -1103,6 +1103,10 @@ struct ozk2_batch_plan_st {
   uint8_t* host = nullptr;    // pinned copy of the uploaded descriptors
   size_t host_bytes = 0;
   cudaEvent_t uploaded = nullptr;
+  // B's scaling and residue kernels run on this second stream beside A's (fork and join
+  // through the two events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace ozk2 {
@@ -1207,6 +1211,9 @@ void destroy_plan(ozk2_batch_plan plan) {
     cudaEventDestroy(plan->uploaded);
   }
   if (plan->host) cudaFreeHost(plan->host);
+  if (plan->side) cudaStreamDestroy(plan->side);  // released once its work is done
+  if (plan->fork) cudaEventDestroy(plan->fork);
+  if (plan->join) cudaEventDestroy(plan->join);
   if (plan->owns_ws && plan->ws) cudaFree(plan->ws);
   delete plan;
 }
@@ -1374,6 +1381,13 @@ ozk2_status create_plan(ozk2_batch_plan* out, int count, const int64_t* m, const
       destroy_plan(plan);
       return OZK2_ERR_ALLOC;
     }
+    if (cudaStreamCreateWithFlags(&plan->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&plan->join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      destroy_plan(plan);
+      return OZK2_ERR_CUDA;
+    }
     plan->host_bytes = nb;
     std::memset(plan->host, 0, nb);
     std::memcpy(plan->host, probs.data(), sizeof(BatchProblem) * probs.size());
@@ -1404,7 +1418,21 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
   uint32_t* flags = reinterpret_cast<uint32_t*>(ws + L.flags);
   OZK2_TRY(cudaMemsetAsync(ws + L.flags, 0, 256, st));
   OZK2_TRY(cudaMemsetAsync(ws + L.zero_begin, 0, L.zero_end - L.zero_begin, st));
-  OZK2_TRY(launch_scale_batch(probs, plan->cnt, plan->totals, plan->fast, flags, st));
+  // A's and B's conversions are independent until the bound product and again until the
+  // residue products: B's run on the plan's second stream, forked from and joined back to
+  // `st` by events (a CUDA graph captured from `st` keeps the same dependencies), so each
+  // grouped launch's tail overlaps the other operand's work
+  auto fork = [&]() -> cudaError_t {
+    cudaError_t e = cudaEventRecord(plan->fork, st);
+    return e != cudaSuccess ? e : cudaStreamWaitEvent(plan->side, plan->fork, 0);
+  };
+  auto join = [&]() -> cudaError_t {
+    cudaError_t e = cudaEventRecord(plan->join, plan->side);
+    return e != cudaSuccess ? e : cudaStreamWaitEvent(st, plan->join, 0);
+  };
+  OZK2_TRY(fork());
+  OZK2_TRY(launch_scale_batch(probs, plan->cnt, plan->totals, plan->fast, flags, st, plan->side));
+  OZK2_TRY(join());
   t_launches += plan->fast ? 4 : 3;
   GemmArgs g{};
   g.num_sms = plan->num_sms;
@@ -1418,8 +1446,10 @@ ozk2_status execute_plan(ozk2_batch_plan plan, cudaStream_t st) {
     t_launches += 1;
   }
   OZK2_TRY(launch_exponents_batch(probs, plan->cnt, plan->totals[kBkExponents], tab->pprime, delta_f32(), st));
+  OZK2_TRY(fork());
   OZK2_TRY(launch_residues_batch(probs, plan->cnt, plan->totals[kBkResidRows], plan->totals[kBkResidCols], tab->mt,
-                                 flags, st));
+                                 flags, st, plan->side));
+  OZK2_TRY(join());
   g.mode = kModeResidue;
   g.mt = &tab->mt;
   const GemmProblem* gres = reinterpret_cast<const GemmProblem*>(ws + L.gres);

@@ -250,12 +250,14 @@ inline int grouped_grid(int64_t total, int per_sm) {
 // single-problem launchers use, without their grid caps).
 void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nblocks)[kBatchKernels]);
 
+// The row kernels (A) run on st, the column kernels (B) on st_cols.
 cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64_t (&total)[kBatchKernels],
-                               bool fast, uint32_t* flags, cudaStream_t st);
+                               bool fast, uint32_t* flags, cudaStream_t st, cudaStream_t st_cols);
 cudaError_t launch_exponents_batch(const BatchProblem* probs, int count, int64_t total_blocks, float pprime,
                                    float delta, cudaStream_t st);
 cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t rows_blocks,
-                                  int64_t cols_blocks, const ModTable& mt, uint32_t* flags, cudaStream_t st);
+                                  int64_t cols_blocks, const ModTable& mt, uint32_t* flags, cudaStream_t st,
+                                  cudaStream_t st_cols);
 cudaError_t launch_crt_batch(const BatchProblem* probs, int count, int64_t total_blocks, const CrtTable& ct,
                              cudaStream_t st);
 

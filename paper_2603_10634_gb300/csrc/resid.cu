@@ -700,13 +700,14 @@ cudaError_t launch_residues_cols(const double* B, int64_t ldb, int k, int n, int
 }
 
 cudaError_t launch_residues_batch(const BatchProblem* probs, int count, int64_t rows_blocks, int64_t cols_blocks,
-                                  const ModTable& mt, uint32_t* flags, cudaStream_t st) {
+                                  const ModTable& mt, uint32_t* flags, cudaStream_t st, cudaStream_t st_cols) {
   if (rows_blocks < 1 || cols_blocks < 1 || rows_blocks > 0x7FFFFFFFll || cols_blocks > 0x7FFFFFFFll)
     return cudaErrorInvalidValue;
   static bool done[64] = {};
   allow_cols_smem(residues_cols_batch, done);
   residues_rows_batch<<<grouped_grid(rows_blocks, 3), 256, 0, st>>>(probs, count, rows_blocks, flags, mt);
-  residues_cols_batch<<<grouped_grid(cols_blocks, 3), 256, kColsSmem, st>>>(probs, count, cols_blocks, flags, mt);
+  residues_cols_batch<<<grouped_grid(cols_blocks, 3), 256, kColsSmem, st_cols>>>(probs, count, cols_blocks, flags,
+                                                                                mt);
   return cudaGetLastError();
 }
 

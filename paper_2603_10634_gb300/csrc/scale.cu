@@ -415,7 +415,7 @@ void batch_block_counts(int m, int n, int k, int kp, bool fast, int64_t (&nb)[kB
 }
 
 cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64_t (&total)[kBatchKernels],
-                               bool fast, uint32_t* flags, cudaStream_t st) {
+                               bool fast, uint32_t* flags, cudaStream_t st, cudaStream_t st_cols) {
   for (int w : {int(kBkScaleRows), int(kBkColmax), int(kBkScaleCols), int(kBkExponents)})
     if (!grid_ok(total[w])) return cudaErrorInvalidValue;
   if (fast && !grid_ok(total[kBkSumsq])) return cudaErrorInvalidValue;
@@ -424,12 +424,12 @@ cudaError_t launch_scale_batch(const BatchProblem* probs, int count, const int64
     scale_rows_batch<true><<<grouped_grid(tr, 8), 256, 0, st>>>(probs, count, tr, flags);
   else
     scale_rows_batch<false><<<grouped_grid(tr, 8), 256, 0, st>>>(probs, count, tr, flags);
-  colmax_batch<<<grouped_grid(tm, 8), 256, 0, st>>>(probs, count, tm);
+  colmax_batch<<<grouped_grid(tm, 8), 256, 0, st_cols>>>(probs, count, tm);
   if (fast) {
-    scale_cols_batch<true><<<grouped_grid(tc, 8), 256, 0, st>>>(probs, count, tc, flags);
-    sumsq_batch<<<grouped_grid(total[kBkSumsq], 8), 256, 0, st>>>(probs, count, total[kBkSumsq]);
+    scale_cols_batch<true><<<grouped_grid(tc, 8), 256, 0, st_cols>>>(probs, count, tc, flags);
+    sumsq_batch<<<grouped_grid(total[kBkSumsq], 8), 256, 0, st_cols>>>(probs, count, total[kBkSumsq]);
   } else {
-    scale_cols_batch<false><<<grouped_grid(tc, 8), 256, 0, st>>>(probs, count, tc, flags);
+    scale_cols_batch<false><<<grouped_grid(tc, 8), 256, 0, st_cols>>>(probs, count, tc, flags);
   }
   return cudaGetLastError();
 }
