@@ -68,6 +68,35 @@ def test_tile_setting_and_plans(cuda):
     auto.close()
 
 
+def test_plan_with_both_tile_widths(cuda):
+    """By default a plan gives each problem the tile width of a single call: narrow or
+    ragged problems 128, the rest 256, in one grouped launch per width (the plan reports
+    0).  Outputs are bit-identical to single calls, also inside a CUDA graph and with the
+    tile setting fixed afterwards."""
+    shapes = [(300, 100, 500), (200, 512, 700), (130, 1000, 64), (64, 256, 2000), (257, 384, 129)]
+    As, Bs = workloads.batch_problems(shapes, 1.0, seed=8, device=cuda)
+    singles = [ozk.dgemm(A, B, num_moduli=12) for A, B in zip(As, Bs)]
+    plan = ozk.BatchPlan(As, Bs, num_moduli=12, tile_n=0)
+    assert plan.tile_n() == 0
+    outs = plan.execute()
+    assert plan.status() == "OZK2_OK"
+    assert all(torch.equal(C, D) for C, D in zip(outs, singles))
+    assert ozk.last_launch_count() == 10  # the residue products in two launches
+    for C in outs:
+        C.fill_(float("nan"))
+    side = torch.cuda.Stream(cuda)
+    side.wait_stream(torch.cuda.current_stream(cuda))
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            plan.execute()
+    torch.cuda.current_stream(cuda).wait_stream(side)
+    graph.replay()
+    torch.cuda.synchronize(cuda)
+    assert all(torch.equal(C, D) for C, D in zip(outs, singles))
+    plan.close()
+
+
 def test_tuner_choices(cuda):
     A, B = workloads.problem(512, 200, 700, 1.0, seed=5, device=cuda)
     t, times = ozk.choose_tile(A, B, 12, reps=2)
