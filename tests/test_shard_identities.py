@@ -1,5 +1,6 @@
 """The two ways the method shards over GPUs, checked on CPU ranks (gloo, world size 2)
-with the oracle's steps, since every machine of this build has one GPU.
+with the oracle's steps: the library itself runs one problem on one GPU and has no
+exchange step, so the identities a sharded run relies on are tested here.
 
 * Rows of A (output rows) per rank: the row exponents e_i need only rank-local data;
   the column exponents f_j need max_i cbar_ij over ALL rows, one all-reduce(max) of S.
