@@ -262,8 +262,11 @@ ozk2_status ozk2_batch_plan_create(ozk2_batch_plan *plan, int count,
                                    ozk2_stream_t stream);
 
 /* ozk2_batch_plan_execute - enqueues the whole batch on `stream` (device work only: a
- * few memsets and one launch per phase; capturable into a CUDA graph).  Must be called
- * on the device the plan was created on; executions of one plan must not overlap. */
+ * few memsets and one launch per phase; capturable into a CUDA graph).  B's scaling and
+ * residue kernels run on a second stream that the plan owns, forked from `stream` and
+ * joined back to it by events, so the execution is complete when `stream` reaches its
+ * end, and a graph captured from `stream` holds both branches.  Must be called on the
+ * device the plan was created on; executions of one plan must not overlap. */
 ozk2_status ozk2_batch_plan_execute(ozk2_batch_plan plan, ozk2_stream_t stream);
 
 /* ozk2_batch_plan_workspace - the plan's device workspace (for ozk2_device_status). */
